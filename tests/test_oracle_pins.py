@@ -1,0 +1,289 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test ties an oracle function to something it does not compute itself:
+published known-answer vectors, brute force on tiny inputs, closed forms,
+library routines on special cases, or exact identities the paper states.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+import scipy.stats
+
+from oracle import algorithms as alg
+from oracle import sketch as sk
+from oracle.philox import philox4x32_10
+from paper_2605_09755_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- generator
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors (SC'11 / Random123)."""
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(w, 16) for w in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = philox4x32_10(*r[:6])
+        assert [int(w) for w in out] == r[6:]
+
+
+def test_philox_vectorised_matches_scalar():
+    c = np.arange(37, dtype=np.uint64) * np.uint64(2654435761) & np.uint64(0xFFFFFFFF)
+    vec = philox4x32_10(c, 7, 11, 13, 5, 9)
+    for i in [0, 5, 36]:
+        sc = philox4x32_10(int(c[i]), 7, 11, 13, 5, 9)
+        assert [int(v[i]) for v in vec] == [int(s) for s in sc]
+
+
+# ---------------------------------------------------------------- sketch (Lemma 3.2 item 2)
+@pytest.mark.parametrize("n,r1,s", [(500, 40, 8), (300, 8, 8), (1000, 100, 1), (64, 64, 3)])
+def test_sketch_rows_have_s_distinct_columns(n, r1, s):
+    cols, signs = sk.sketch_entries(n, r1, s, seed=42)
+    assert cols.shape == (n, s) and signs.shape == (n, s)
+    assert cols.min() >= 0 and cols.max() < r1
+    for j in range(n):
+        assert len(set(cols[j].tolist())) == s
+    assert set(np.unique(signs).tolist()) <= {-1, 1}
+    S = sk.Sketch(n, r1, s, 42)
+    D = S.dense()
+    # each row: exactly s non-zeros of magnitude 1/sqrt(s)
+    nz = np.count_nonzero(D, axis=1)
+    assert np.all(nz == s)
+    assert np.allclose(np.abs(D[D != 0]), 1.0 / np.sqrt(s))
+    ptr, rows, sg = S.buckets()
+    assert ptr[-1] == n * s
+    for c in range(r1):
+        rr = rows[ptr[c]:ptr[c + 1]]
+        assert np.all(np.diff(rr) > 0)           # ascending row order inside a bucket
+        assert np.allclose(D[rr, c], sg[ptr[c]:ptr[c + 1]] / np.sqrt(s))
+
+
+def test_sketch_column_and_sign_distribution():
+    """Columns uniform over [0, r1) and signs fair (chi-square / binomial, s = 1)."""
+    n, r1 = 200000, 50
+    cols, signs = sk.sketch_entries(n, r1, 1, seed=7)
+    counts = np.bincount(cols[:, 0], minlength=r1)
+    stat, p = scipy.stats.chisquare(counts)
+    assert p > 1e-4
+    plus = int((signs == 1).sum())
+    assert abs(plus - n / 2) < 5 * np.sqrt(n / 4)
+
+
+def test_sketch_seed_changes_draws_and_is_reproducible():
+    a = sk.sketch_entries(300, 30, 4, seed=1)
+    b = sk.sketch_entries(300, 30, 4, seed=1)
+    c = sk.sketch_entries(300, 30, 4, seed=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert not np.array_equal(a[0], c[0])
+
+
+def test_apply_matches_brute_force():
+    """A S by the definition sum_j A[i,j] S[j,c], looped in pure Python on a tiny case."""
+    rng = np.random.default_rng(3)
+    m, n, r1, s = 5, 17, 6, 3
+    A = rng.standard_normal((m, n))
+    S = sk.Sketch(n, r1, s, seed=99)
+    cols, signs = S.cols, S.signs
+    ref = [[0.0] * r1 for _ in range(m)]
+    for i in range(m):
+        for j in range(n):
+            for t in range(s):
+                ref[i][int(cols[j, t])] += float(signs[j, t]) / np.sqrt(s) * A[i, j]
+    assert np.allclose(sk.apply_right(A, S), np.array(ref), rtol=0, atol=1e-14)
+    X = rng.standard_normal((n, 4))
+    refT = np.zeros((r1, 4))
+    for j in range(n):
+        for t in range(s):
+            refT[int(cols[j, t])] += float(signs[j, t]) / np.sqrt(s) * X[j]
+    assert np.allclose(sk.apply_left_t(S, X), refT, rtol=0, atol=1e-14)
+
+
+def test_identity_sketch():
+    S = sk.Sketch(12, 12, 1, 0, kind=sk.IDENTITY)
+    assert np.array_equal(S.dense(), np.eye(12))
+
+
+def test_gaussian_omega_is_standard_normal():
+    z = sk.gaussian(300, 400, seed=43).reshape(-1)
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 0.02
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-4
+    # neighbouring entries come from one Box-Muller pair: still uncorrelated
+    assert abs(np.corrcoef(z[0::2], z[1::2])[0, 1]) < 0.02
+    assert np.array_equal(sk.gaussian(3, 5, 43), sk.gaussian(300, 400, 43).reshape(-1)[:15].reshape(3, 5))
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def test_orth_is_orthonormal_and_spans():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((80, 12))
+    Q = alg.orth(Y)
+    assert np.linalg.norm(Q.T @ Q - np.eye(12)) < 1e-13
+    assert np.linalg.norm(Q @ (Q.T @ Y) - Y) < 1e-12 * np.linalg.norm(Y)
+
+
+def test_q0_with_identity_omega_spans_AS():
+    """q = 0 and Omega = I_{r1}: Y = A S exactly, so range(Q) = range(A S)."""
+    A, _ = wl.dense_lowrank(60, 40, np.linspace(3, 1, 40), seed=5)
+    S = sk.Sketch(40, 10, 4, seed=11)
+    Q = alg.range_finder(A, S, np.eye(10), q=0)
+    AS = A @ S.dense()
+    assert Q.shape == (60, 10)
+    assert np.linalg.norm(Q @ (Q.T @ AS) - AS) < 1e-12 * np.linalg.norm(AS)
+
+
+def test_identity_sketch_is_subspace_iteration_converging_to_optimum():
+    """S = I recovers the classical range finder (Section 2); with many power steps and a
+    spectral gap, Q spans the top singular subspace, so the residual equals Eckart-Young."""
+    sigma = np.concatenate([np.linspace(10, 5, 8), 0.5 * np.linspace(1, 0.1, 32)])
+    A, _ = wl.dense_lowrank(70, 40, sigma, seed=8)
+    S = sk.Sketch(40, 40, 1, 0, kind=sk.IDENTITY)
+    Om = sk.gaussian(40, 8, seed=3)
+    Q = alg.range_finder(A, S, Om, q=25)
+    res = alg.residual_fro(A, Q)
+    opt = alg.optimal_fro(sigma, 8)
+    assert abs(res - opt) < 1e-9 * opt
+    # and the projection matches the truncated SVD (library routine)
+    U, s, Vt = np.linalg.svd(A)
+    P_true = U[:, :8] @ U[:, :8].T
+    assert np.linalg.norm(Q @ Q.T - P_true) < 1e-8
+
+
+def test_reorth_does_not_change_output_in_exact_arithmetic():
+    """Section 2: intermediate re-orthonormalisation leaves range(Y) unchanged."""
+    A, _ = wl.dense_lowrank(50, 30, np.linspace(2, 1, 30), seed=9)
+    S = sk.Sketch(30, 15, 3, seed=1)
+    Om = sk.gaussian(15, 5, seed=2)
+    Q1 = alg.range_finder(A, S, Om, q=2, reorth=True)
+    Q2 = alg.range_finder(A, S, Om, q=2, reorth=False)
+    assert np.linalg.norm(Q1 @ Q1.T - Q2 @ Q2.T) < 1e-10
+
+
+def test_power_step_direction():
+    """One power step uses A~ A~^T (not A~^T A~): compare with the definition on a tiny case."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((9, 7))
+    S = sk.Sketch(7, 5, 2, seed=6)
+    Om = rng.standard_normal((5, 3))
+    At = A @ S.dense()
+    Y = At @ At.T @ At @ Om
+    Q = alg.range_finder(A, S, Om, q=1)
+    assert np.linalg.norm(Q @ (Q.T @ Y) - Y) < 1e-12 * np.linalg.norm(Y)
+
+
+def test_exact_low_rank_is_recovered():
+    sigma = np.array([5.0, 3.0, 2.0, 1.0, 0.5])
+    A, _ = wl.dense_lowrank(90, 60, sigma, seed=12)
+    S = sk.Sketch(60, 20, 4, seed=3)
+    Q = alg.range_finder(A, S, sk.gaussian(20, 8, 4), q=1)
+    assert alg.residual_fro(A, Q) < 1e-13 * np.linalg.norm(A)
+
+
+def test_eckart_young_lower_bound_and_cfg1_closed_form():
+    """Residual never beats Eckart-Young; the 2000 x 1000, sigma_i = 1/i optimum at k = 50
+    is sqrt(sum_{i=51}^{1000} i^-2) = sqrt(psi1(51) - psi1(1001))."""
+    closed = np.sqrt(scipy.special.polygamma(1, 51) - scipy.special.polygamma(1, 1001))
+    sig = 1.0 / np.arange(1, 1001)
+    assert abs(alg.optimal_fro(sig, 50) - closed) < 1e-14
+    assert abs(closed - 0.1371197763272333) < 1e-12
+    A, sigma = wl.plain_fp64(200, 100, seed=1001)
+    assert np.allclose(np.linalg.svd(A, compute_uv=False), sigma, atol=1e-13)
+    for seed in range(3):
+        S = sk.Sketch(100, 20, 8, seed=seed)
+        Q = alg.range_finder(A, S, sk.gaussian(20, 10, seed + 50), q=2)
+        assert alg.residual_fro(A, Q) >= alg.optimal_fro(sigma, 10) * (1 - 1e-12)
+
+
+def test_sketched_power_improves_then_plateau_falls_with_sketch_size():
+    """Theorem 2.1 and Section 4, qualitatively: error drops with q, and the level it
+    settles at is lower for a larger sketch (averaged over seeds)."""
+    A, sigma = wl.plain_fp64(400, 300, seed=21)
+    k = 10
+    opt = alg.optimal_fro(sigma, k)
+
+    def err(r1, q):
+        e = []
+        for sd in range(6):
+            S = sk.Sketch(300, r1, 4, seed=100 + sd)
+            Q = alg.range_finder(A, S, sk.gaussian(r1, k, 200 + sd), q=q)
+            e.append(alg.residual_fro(A, Q) / opt)
+        return float(np.mean(e))
+
+    assert err(40, 3) < err(40, 0)
+    assert err(160, 6) < err(40, 6)
+
+
+# ---------------------------------------------------------------- Randomized SVD finish
+def test_rsvd_factors_reproduce_projection():
+    A, sigma = wl.plain_fp64(120, 80, seed=31)
+    S = sk.Sketch(80, 30, 8, seed=42)
+    U, s, Vt, Q = alg.rsvd(A, S, sk.gaussian(30, 12, 43), q=2, k=12)
+    assert np.linalg.norm(U.T @ U - np.eye(12)) < 1e-13
+    assert np.linalg.norm(Vt @ Vt.T - np.eye(12)) < 1e-13
+    assert np.all(np.diff(s) <= 0)
+    # U S V^T equals Q Q^T A (k = r2) and s are the singular values of Q Q^T A
+    P = Q @ (Q.T @ A)
+    assert np.linalg.norm((U * s) @ Vt - P) < 1e-12 * np.linalg.norm(A)
+    assert np.allclose(s, np.linalg.svd(P, compute_uv=False)[:12], rtol=1e-12)
+    # sign convention: largest-magnitude entry of each u_i is positive
+    idx = np.argmax(np.abs(U), axis=0)
+    assert np.all(U[idx, np.arange(12)] > 0)
+
+
+# ---------------------------------------------------------------- Algorithm 2
+def test_lowrank_with_identity_S2_is_projection():
+    """S2 = I: X = Y^+ A, so Y X = Q Q^T A."""
+    A, _ = wl.plain_fp64(70, 50, seed=41)
+    S1 = sk.Sketch(50, 20, 4, seed=1)
+    S2 = sk.Sketch(70, 70, 1, 0, kind=sk.IDENTITY)
+    Om = sk.gaussian(20, 8, 2)
+    Y, X = alg.lowrank(A, S1, S2, Om, q=1)
+    Q = alg.range_finder(A, S1, Om, q=1)
+    assert np.linalg.norm(Y @ X - Q @ (Q.T @ A)) < 1e-12 * np.linalg.norm(A)
+
+
+def test_lowrank_exact_on_low_rank_input():
+    sigma = np.array([4.0, 2.0, 1.0])
+    A, _ = wl.dense_lowrank(80, 60, sigma, seed=43)
+    Y, X = alg.lowrank(A, sk.Sketch(60, 20, 4, 1), sk.Sketch(80, 20, 4, 2), sk.gaussian(20, 6, 3), q=1)
+    assert np.linalg.norm(Y @ X - A) < 1e-12 * np.linalg.norm(A)
+
+
+# ---------------------------------------------------------------- Algorithm 3
+def test_nystrom_identity_with_range_finder_on_sqrt():
+    """Proof of Theorem 2.3: C W^+ C^T = A^{1/2} Q Q^T A^{1/2} with Q from Algorithm 1
+    applied to A^{1/2} with the same S and Omega."""
+    n = 60
+    sigma = np.linspace(4.0, 0.01, n) ** 2
+    A = wl.psd_lowrank(n, sigma, seed=51)
+    lam, V = np.linalg.eigh(A)
+    Ah = (V * np.sqrt(np.maximum(lam, 0))) @ V.T
+    S = sk.Sketch(n, 25, 4, seed=5)
+    Om = sk.gaussian(25, 8, 6)
+    for q in (0, 1, 2):
+        C, W = alg.nystrom(A, S, Om, q)
+        Ahat = alg.nystrom_apply(C, W)
+        Q = alg.range_finder(Ah, S, Om, q)
+        ref = Ah @ Q @ Q.T @ Ah
+        assert np.linalg.norm(Ahat - ref) < 1e-9 * np.linalg.norm(A)
+        # A - A_hat is psd
+        assert np.linalg.eigvalsh(A - Ahat).min() > -1e-9 * np.linalg.norm(A)
+
+
+def test_nystrom_exact_on_low_rank_psd():
+    A = wl.psd_lowrank(50, np.array([3.0, 2.0, 1.0, 0.5]), seed=52)
+    C, W = alg.nystrom(A, sk.Sketch(50, 20, 4, 1), sk.gaussian(20, 6, 2), q=1)
+    assert np.linalg.norm(alg.nystrom_apply(C, W) - A) < 1e-11 * np.linalg.norm(A)
+
+
+def test_gmm_kernel_is_psd_with_unit_diagonal():
+    K, h, X = wl.gmm_kernel(200, seed=3)
+    assert np.allclose(np.diag(K), 1.0)
+    assert np.linalg.eigvalsh(K).min() > -1e-10
+    assert h > 0

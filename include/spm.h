@@ -1,0 +1,204 @@
+/*
+ * spm.h -- C ABI of the sketch-powered power method library (libspm.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the data-parallel hot
+ * path of "Accelerating Power Method with Fast Sketching for Stronger Low-Rank
+ * Approximation" (Chenakkod & Derezinski):
+ *
+ *   - the sparse sign sketch S (Lemma 3.2, item 2) and its products A S, S^T X;
+ *   - the Sketch-Powered Range Finder (Algorithm 1): Q = orth((A~ A~^T)^q A~ Omega),
+ *     A~ = A S, with re-orthonormalisation between power steps (Section 2);
+ *   - the Randomized SVD finish (Section 2): B = Q^T A, B = U~ Sigma V^T, U = Q U~;
+ *   - the Sketch-Powered Low-Rank Factorization (Algorithm 2);
+ *   - the Sketch-Powered Nystrom Approximation (Algorithm 3).
+ *
+ * Conventions shared by every entry point
+ *   - Dense matrices are row-major: element (i, j) of a matrix with leading
+ *     dimension ld sits at ptr[i * ld + j]; ld >= number of columns.
+ *   - Matrix pointers are DEVICE pointers unless a parameter says "host".  The
+ *     caller owns every input and output buffer.  The library allocates its
+ *     own workspace stream-ordered (cudaMallocAsync on the given stream) and
+ *     frees it before the call returns (or in spm_sketch_destroy for sketch
+ *     tables).
+ *   - Every call is stream-ordered on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  A call returns after its kernels are enqueued; it
+ *     synchronises only when an `info` pointer is passed (it then reads the
+ *     device status word back) or when timing is requested through `info`.
+ *   - dtype is SPM_F32 or SPM_F64 and applies to A and to every floating-point
+ *     output of the call.
+ *   - Return value: SPM_OK (0) or one of the SPM_E* codes below.  Nothing is
+ *     launched when argument checking fails.
+ *   - There is no CPU fallback: without a usable sm_103a device every compute
+ *     entry point returns SPM_ECUDA.
+ */
+#ifndef SPM_H_
+#define SPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPM_OK 0
+#define SPM_EINVAL 1        /* bad shape, null pointer, ld too small, bad enum   */
+#define SPM_ENOMEM 2        /* stream-ordered workspace allocation failed        */
+#define SPM_ECUDA 3         /* kernel launch / runtime error, or no usable GPU   */
+#define SPM_EBREAKDOWN 4    /* Cholesky breakdown inside CholeskyQR after shift  */
+#define SPM_ENONFINITE 5    /* NaN/Inf met in an input or produced in an output  */
+#define SPM_ETIMEOUT 6      /* a bounded device-side wait gave up                */
+#define SPM_EUNSUPPORTED 7  /* valid request this build does not implement       */
+
+/* ---- enums ------------------------------------------------------------- */
+#define SPM_F32 0
+#define SPM_F64 1
+
+#define SPM_SKETCH_SPARSE_SIGN 0 /* s non-zeros +-1/sqrt(s) per row (Lemma 3.2 item 2) */
+#define SPM_SKETCH_IDENTITY 1    /* S = I (r1 = n): the classical power method (Section 2) */
+
+#define SPM_PREC_FP64 0   /* every product and factorisation in FP64 (CUDA cores)        */
+#define SPM_PREC_MIXED 1  /* BF16 tensor-core products (FP32 accumulate), split-precision
+                             (hi+lo BF16) products where accuracy is needed, FP32/FP64
+                             small factorisations; A may be SPM_F32 or SPM_F64            */
+
+#define SPM_NSTAGES 8     /* stage timers reported through spm_info                       */
+/* stage indices of spm_info.stage_ms */
+#define SPM_STAGE_SKETCH 0   /* sketch generation (a1) + Omega (a2)                 */
+#define SPM_STAGE_APPLY 1    /* A~ = A S (a3)                                       */
+#define SPM_STAGE_POWER 2    /* power products A~ Z, A~^T Y (a4)                    */
+#define SPM_STAGE_ORTH 3     /* re-orthonormalisation and final orth (a5)           */
+#define SPM_STAGE_PROJECT 4  /* B = Q^T A, S2^T A or C~ Y (a6/a7/a8 big product)    */
+#define SPM_STAGE_SMALL 5    /* small core factorisation (eig / least squares)     */
+#define SPM_STAGE_FINISH 6   /* U = Q U~, V^T, X, C, W outputs                     */
+#define SPM_STAGE_OTHER 7
+
+typedef struct spm_sketch spm_sketch; /* opaque: device tables of one sketch S */
+
+typedef struct spm_opts {
+  int32_t precision;    /* SPM_PREC_FP64 (default when opts == NULL) or SPM_PREC_MIXED      */
+  int32_t reorth;       /* 1 (default): re-orthonormalise after each A~^T product; 0: none  */
+  int32_t final_passes; /* MIXED only: BF16 passes for the final projection Q^T A: 1 or 3
+                           (hi*hi + hi*lo + lo*hi); 0 selects the default 3                 */
+  int32_t small_fp64;   /* MIXED only: 1 = FP64 Cholesky / eigensolver, 0 (default) = FP32   */
+  const void* omega;    /* optional caller-supplied Omega: device, r1 x r2 row-major, ld r2,
+                           dtype of A.  NULL: generated from omega_seed (a2).               */
+} spm_opts;
+
+typedef struct spm_info {
+  /* inputs */
+  int32_t want_timing;  /* 1: record CUDA events around stages (forces a final sync)       */
+  int32_t reserved0;
+  /* outputs (written when info != NULL; the call synchronises its stream) */
+  int32_t device_status;    /* SPM_OK or the first device-side error code                */
+  int32_t cholqr_passes;    /* CholeskyQR passes executed on the final basis              */
+  double resid_est;         /* a-posteriori estimate sqrt(max(|A|_F^2 - |B|_F^2, 0)) where
+                               B = Q^T A is formed (rsvd); -1 when not available          */
+  double fro_a;             /* |A|_F accumulated while A streams through the sketch pass  */
+  float stage_ms[SPM_NSTAGES];
+} spm_info;
+
+/* ---- library ----------------------------------------------------------- */
+/* Version number (major * 10000 + minor * 100 + patch). */
+int spm_version(void);
+/* Static string naming a status code. */
+const char* spm_status_string(int status);
+/* 1 if the current CUDA device is sm_103 and the kernels loaded, else 0. */
+int spm_device_ok(void);
+
+/* ---- a1: sketch generation ---------------------------------------------
+ * Lemma 3.2 item 2 (CountSketch-type S in R^{n x r1}, s non-zeros of the form
+ * +-1/sqrt(s) per row) and Section 4 (s = 1 is CountSketch).  Row j draws s
+ * distinct columns uniformly (rejection of repeats) from Philox4x32-10 keyed by
+ * `seed`; column = floor(u * r1 / 2^32).  The tables are built on the device in
+ * stream order and are bit-identical to the CPU oracle's for the same seed.
+ * kind = SPM_SKETCH_IDENTITY needs r1 == n and s == 1 (S = I).
+ * Errors: SPM_EINVAL if n < 1, r1 < 1, s < 1, s > r1, s > 64, n > 2^31 - 1,
+ * r1 > 2^31 - 1, or out == NULL.
+ * Ownership: *out is owned by the caller and released with spm_sketch_destroy. */
+int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64_t seed,
+                      int32_t kind, void* stream);
+/* Frees the device tables (stream-ordered on the stream given at creation). */
+int spm_sketch_destroy(spm_sketch* S);
+/* Host query of the sketch shape; any output pointer may be NULL. */
+int spm_sketch_shape(const spm_sketch* S, int64_t* n, int64_t* r1, int32_t* s, int32_t* kind);
+/* Copies the tables into caller DEVICE buffers (any may be NULL):
+ *   cols[n*s]  int32, column of entry t of row j at [j*s + t] (draw order)
+ *   signs[n*s] int8,  +1 / -1
+ *   bucket_ptr[r1+1] int64, bucket_rows[n*s] int32: CSC form of S, rows of each
+ *   column in ascending order; bucket_signs[n*s] int8. */
+int spm_sketch_tables(const spm_sketch* S, int32_t* cols, int8_t* signs, int64_t* bucket_ptr,
+                      int32_t* bucket_rows, int8_t* bucket_signs, void* stream);
+
+/* ---- a2: Gaussian start block Omega (Algorithm 1 input, Theorem 2.1) --------
+ * out[i*ld + j] = N(0,1) draw for row-major element e = i*cols + j: Box-Muller on
+ * the Philox4x32-10 block with counter (e/2 lo, e/2 hi, 0, 2), two 53-bit
+ * uniforms, cos for even e and sin for odd e.  Errors: SPM_EINVAL on bad sizes. */
+int spm_gaussian(void* out, int32_t dtype, int64_t rows, int64_t cols, int64_t ld,
+                 uint64_t seed, void* stream);
+
+/* ---- a3: sketch products ----------------------------------------------------
+ * out (m x r1, ld ldo) = A (m x n, ld lda) * S  (Algorithm 1 line 1, A~ = A S;
+ * Algorithm 3 line 1, C~ = A S).  Sums run over the column buckets of S. */
+int spm_sketch_apply(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                     void* out, int64_t ldo, void* stream);
+/* out (r1 x p, ld ldo) = S^T X with X (n x p, ld ldx)  (Algorithm 2 line 2: S2^T Y,
+ * S2^T A; Algorithm 3 line 1: W~ = S^T C~). */
+int spm_sketch_apply_t(const spm_sketch* S, const void* X, int32_t dtype, int64_t p, int64_t ldx,
+                       void* out, int64_t ldo, void* stream);
+
+/* ---- a4 + a5: Algorithm 1, Sketch-Powered Range Finder ----------------------
+ * Q (m x r2, ld ldq) with orthonormal columns spanning (A~ A~^T)^q A~ Omega,
+ * A~ = A S, A (m x n, ld lda), S from spm_sketch_create with S.n == n.
+ * Omega is r1 x r2 Gaussian from omega_seed unless opts->omega is set.
+ * Requires 1 <= r2 <= r1 and r2 <= m.  q >= 0. */
+int spm_range_finder(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                     int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts,
+                     void* Q, int64_t ldq, spm_info* info, void* stream);
+
+/* ---- a6: Randomized SVD on Algorithm 1 (Section 2) --------------------------
+ * U (m x k, ld ldu), sigma (k, descending), Vt (k x n, ld ldvt) with
+ * A ~ U diag(sigma) Vt, from B = Q^T A = U~ Sigma V^T, U = Q U~.  1 <= k <= r2.
+ * Sign convention: the entry of largest magnitude of each column of U is > 0. */
+int spm_rsvd(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+             int64_t r2, int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts,
+             void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, spm_info* info,
+             void* stream);
+
+/* ---- a7: Algorithm 2, Sketch-Powered Low-Rank Factorization ------------------
+ * Y (m x r2, ld ldy) and X (r2 x n, ld ldx) with A ~ Y X, X = (S2^T Y)^+ (S2^T A).
+ * Y is returned orthonormal (the product Y X does not depend on the basis).
+ * S1: n -> r1 column sketch; S2: m -> r1' row sketch (S2.n == m, S2.r1 >= r2). */
+int spm_lowrank(const spm_sketch* S1, const spm_sketch* S2, const void* A, int32_t dtype,
+                int64_t m, int64_t lda, int64_t r2, int32_t q, uint64_t omega_seed,
+                const spm_opts* opts, void* Y, int64_t ldy, void* X, int64_t ldx,
+                spm_info* info, void* stream);
+
+/* ---- a8: Algorithm 3, Sketch-Powered Nystrom Approximation -------------------
+ * For symmetric psd A (n x n, ld lda): C (n x r2, ld ldc) and W (r2 x r2, ld ldw)
+ * with A ~ C W^+ C^T: C~ = A S, W~ = S^T A S, Y = W~^q Omega, C = C~ Y,
+ * W = Y^T W~ Y.  Y is re-orthonormalised between its q products (this leaves
+ * C W^+ C^T unchanged). */
+int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, int64_t lda,
+                int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts,
+                void* C, int64_t ldc, void* W, int64_t ldw, spm_info* info, void* stream);
+
+/* ---- tensor-core building block --------------------------------------------
+ * D (M x N, FP32, row stride ldd) = sum_{q < npass} A_q (M x K) * B_q (N x K)^T on
+ * tcgen05 tensor cores, BF16 operands, FP32 accumulation: the tall-skinny
+ * contractions of Algorithm 1 line 1 (A~ Z, A~^T Y) and of the Randomized SVD
+ * finish (Q^T A).  A and B are HOST arrays of npass DEVICE pointers (npass 1..3).
+ * Operand q of A is stored row-major with leading dimension lda (elements,
+ * multiple of 8, base 16-byte aligned): a_mn = 0 -> stored M x K (K contiguous);
+ * a_mn = 1 -> stored K x M.  Same for B with N.  splitk >= 1 splits K; partial
+ * sums are reduced in a fixed order (deterministic).
+ * Errors: SPM_EINVAL on bad sizes/alignment, SPM_ECUDA without an sm_103 device. */
+int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
+                  int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
+                  float* D, int64_t ldd, int32_t splitk, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPM_H_ */

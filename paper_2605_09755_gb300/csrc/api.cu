@@ -1,0 +1,640 @@
+// C ABI entry points: Algorithm 1 (Sketch-Powered Range Finder), the
+// Randomized SVD finish, Algorithm 2 (Sketch-Powered Low-Rank Factorization)
+// and Algorithm 3 (Sketch-Powered Nystrom Approximation).
+//
+// Two precision modes share one schedule:
+//   SPM_PREC_FP64  -- every product on CUDA cores in FP64 (the plain form);
+//   SPM_PREC_MIXED -- A~ in BF16, power products on tcgen05 tensor cores with
+//                     FP32 accumulation; the products whose accuracy reaches the
+//                     output (CholeskyQR Gram and triangular products, Q^T A,
+//                     B B^T, U~^T B, Q U~) use split-precision hi*hi + hi*lo +
+//                     lo*hi BF16 passes; small factorisations in FP32 (or FP64
+//                     with opts->small_fp64).
+// Re-orthonormalisation (Section 2): Z = orth(A~^T Y) after every A~^T product;
+// the final basis is orth(Y).  In exact arithmetic this equals Algorithm 1.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace spm {
+
+struct Call {
+  cudaStream_t st;
+  Arena ar;
+  int prec = SPM_PREC_FP64;
+  int adt = DT_F64;
+  bool small64 = false;
+  int final_passes = 3;
+  bool reorth = true;
+  const void* omega = nullptr;
+  int* status = nullptr;
+  double* acc = nullptr;  // [0] = |A|_F^2, [1] = |B|_F^2
+  StageTimer timer;
+  int cholqr_passes = 0;
+  explicit Call(cudaStream_t s) : st(s), ar(s) { timer.stream = s; }
+};
+
+static int64_t pad8(int64_t x) { return round_up(x, 8); }
+
+static int auto_splitk(int64_t M, int64_t N, int64_t K) {
+  const int BN = (N >= 192) ? 256 : 128;
+  const int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
+  const int64_t kt = cdiv(K, 64);
+  int64_t sk = cdiv(2 * 152, tiles);
+  sk = min64(sk, max64(kt / 4, 1));
+  return (int)max64(sk, 1);
+}
+
+// Split-precision tensor-core product: D = sum of npass terms over (hi, lo) pairs.
+static int tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* Ahi,
+                    const __nv_bfloat16* Alo, int64_t lda, bool a_mn, const __nv_bfloat16* Bhi,
+                    const __nv_bfloat16* Blo, int64_t ldb, bool b_mn, int npass, float* D,
+                    int64_t d_rs, int64_t d_cs, cudaStream_t st) {
+  TcOp A[3] = {{Ahi, lda, a_mn}, {Ahi, lda, a_mn}, {Alo, lda, a_mn}};
+  TcOp B[3] = {{Bhi, ldb, b_mn}, {Blo, ldb, b_mn}, {Bhi, ldb, b_mn}};
+  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K), st);
+}
+
+// ------------------------------------------------------------------ CholeskyQR
+// Relative diagonal shift of the first CholeskyQR pass (shifted CholeskyQR3).
+// FP64 Gram: 11 (rows c + c (c + 1)) u, the bound of Fukaya et al. (2020);
+// Gram formed from FP32 / split-BF16 data (relative error about 1e-5): 1e-4.
+static double shift_coef(bool fp64_gram, int64_t rows, int64_t c) {
+  if (fp64_gram) return 11.0 * ((double)rows * c + (double)c * (c + 1)) * 1.1102230246251565e-16;
+  return 1e-4;
+}
+
+// Shifted CholeskyQR3 in FP64 on CUDA cores: X (rows x c, ld ldx) <- orth(X).
+// The first pass adds a small multiple of trace(G) to the Gram diagonal, so a
+// rank-deficient or ill-conditioned X never breaks the Cholesky factorisation;
+// the next passes restore orthonormality to working precision.
+static int orth_f64(Call& C, double* X, int64_t rows, int64_t c, int64_t ldx, int passes) {
+  SPM_ALLOC(C.ar, double, G, c * c);
+  SPM_ALLOC(C.ar, double, Li, c * c);
+  SPM_ALLOC(C.ar, double, Xn, rows * c);
+  for (int ps = 0; ps < passes; ++ps) {
+    SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F64, ldx)),
+                      rowmajor(X, DT_F64, ldx), 0.0, mrowmajor(G, DT_F64, c), C.st));
+    if (ps == 0 && passes > 2)
+      SPM_TRY(add_trace_shift(c, G, c, DT_F64, shift_coef(true, rows, c), C.st));
+    SPM_TRY(cholesky_inv(c, G, c, Li, c, DT_F64, C.status, C.st));
+    SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F64, ldx), transpose(rowmajor(Li, DT_F64, c)),
+                      0.0, mrowmajor(Xn, DT_F64, c), C.st));
+    SPM_TRY(convert2d(rows, c, rowmajor(Xn, DT_F64, c), mrowmajor(X, DT_F64, ldx), C.st));
+  }
+  return SPM_OK;
+}
+
+// Shifted CholeskyQR on an FP32 matrix with the small factorisation in FP32 or
+// FP64 and the Gram / triangular products on CUDA cores (used for the r1 x r2
+// iterate Z and other small bases).  First pass shifted, then `passes - 1` plain.
+static int orth_small_f32(Call& C, float* X, int64_t rows, int64_t c, int64_t ldx, int passes) {
+  const int sdt = C.small64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(sdt);
+  void* G = C.ar.alloc<unsigned char>(c * c * es);
+  void* Li = C.ar.alloc<unsigned char>(c * c * es);
+  float* Xn = C.ar.alloc<float>(rows * c);
+  if (!G || !Li || !Xn) return SPM_ENOMEM;
+  for (int ps = 0; ps < passes; ++ps) {
+    SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F32, ldx)),
+                      rowmajor(X, DT_F32, ldx), 0.0, mrowmajor(G, sdt, c), C.st));
+    if (ps == 0 && passes > 2) SPM_TRY(add_trace_shift(c, G, c, sdt, shift_coef(false, rows, c), C.st));
+    SPM_TRY(cholesky_inv(c, G, c, Li, c, sdt, C.status, C.st));
+    SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F32, ldx), transpose(rowmajor(Li, sdt, c)), 0.0,
+                      mrowmajor(Xn, DT_F32, c), C.st));
+    SPM_TRY(convert2d(rows, c, rowmajor(Xn, DT_F32, c), mrowmajor(X, DT_F32, ldx), C.st));
+  }
+  return SPM_OK;
+}
+
+// Shifted CholeskyQR3 of the tall m x c FP32 basis Y on tensor cores: Gram and
+// Y R^{-1} as split-precision (3-pass) BF16 products.  On return Y holds Q and
+// (Qhi, Qlo) its BF16 split (row-major, ld pad8(c)).
+static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
+                          __nv_bfloat16* Qhi, __nv_bfloat16* Qlo) {
+  const int sdt = C.small64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(sdt);
+  const int64_t cp = pad8(c);
+  SPM_ALLOC(C.ar, float, G, c * c);
+  void* Gs = C.ar.alloc<unsigned char>(c * c * es);
+  void* Li = C.ar.alloc<unsigned char>(c * c * es);
+  if (!Gs || !Li) return SPM_ENOMEM;
+  SPM_ALLOC(C.ar, __nv_bfloat16, Lhi, c * cp);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Llo, c * cp);
+  const int passes = 3;
+  for (int ps = 0; ps < passes; ++ps) {
+    SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
+                       mrowmajor(Qlo, DT_BF16, cp), C.st));
+    // G = Y^T Y: A-op Y^T (M = c, K = m) and B-op (N = c, K = m) both MN-major
+    SPM_TRY(tc_split(c, c, m, Qhi, Qlo, cp, true, Qhi, Qlo, cp, true, 3, G, c, 1, C.st));
+    if (sdt == DT_F64)
+      SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F64, c), C.st));
+    else
+      SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F32, c), C.st));
+    if (ps == 0) SPM_TRY(add_trace_shift(c, Gs, c, sdt, shift_coef(false, m, c), C.st));
+    SPM_TRY(cholesky_inv(c, Gs, c, Li, c, sdt, C.status, C.st));
+    // Y <- Y L^{-T}: A-op Y (M = m, K = c) K-major; B-op (N = c, K = c) element
+    // (n, k) = Linv[n][k], i.e. Linv row-major is K-major.
+    SPM_TRY(split_bf16(c, c, rowmajor(Li, sdt, c), mrowmajor(Lhi, DT_BF16, cp),
+                       mrowmajor(Llo, DT_BF16, cp), C.st));
+    SPM_TRY(tc_split(m, c, c, Qhi, Qlo, cp, false, Lhi, Llo, cp, false, 3, Y, ldy, 1, C.st));
+    C.cholqr_passes++;
+  }
+  SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
+                     mrowmajor(Qlo, DT_BF16, cp), C.st));
+  return SPM_OK;
+}
+
+// ------------------------------------------------------------------ Algorithm 1
+// Result of the range finder, kept on the device for the finishing steps.
+struct RF {
+  int64_t m = 0, r2 = 0;
+  double* Q64 = nullptr;       // FP64 mode: m x r2 (ld r2)
+  float* Q32 = nullptr;        // MIXED: m x r2 (ld r2)
+  __nv_bfloat16* Qhi = nullptr;  // MIXED: BF16 split of Q (ld pad8(r2))
+  __nv_bfloat16* Qlo = nullptr;
+};
+
+static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_t m, int64_t lda,
+                             int64_t r2, int q, uint64_t seed, RF& out) {
+  const int64_t n = S->n, r1 = S->r1;
+  out.m = m;
+  out.r2 = r2;
+  if (C.prec == SPM_PREC_FP64) {
+    SPM_ALLOC(C.ar, double, At, m * r1);
+    SPM_ALLOC(C.ar, double, Om, r1 * r2);
+    SPM_ALLOC(C.ar, double, Y, m * r2);
+    SPM_ALLOC(C.ar, double, Z, r1 * r2);
+    {
+      StageScope sc(C.timer, SPM_STAGE_SKETCH);
+      if (C.omega)
+        SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Om, DT_F64, r2), C.st));
+      else
+        SPM_TRY(gaussian_dev(Om, DT_F64, r1, r2, r2, seed, C.st));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_APPLY);
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_F64, r1, C.acc, C.st));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, DT_F64, r1), rowmajor(Om, DT_F64, r2), 0.0,
+                        mrowmajor(Y, DT_F64, r2), C.st));
+    }
+    for (int t = 0; t < q; ++t) {
+      {
+        StageScope sc(C.timer, SPM_STAGE_POWER);
+        SPM_TRY(gemm_simt(r1, r2, m, 1.0, transpose(rowmajor(At, DT_F64, r1)),
+                          rowmajor(Y, DT_F64, r2), 0.0, mrowmajor(Z, DT_F64, r2), C.st));
+      }
+      if (C.reorth) {
+        StageScope sc(C.timer, SPM_STAGE_ORTH);
+        SPM_TRY(orth_f64(C, Z, r1, r2, r2, 3));
+      }
+      {
+        StageScope sc(C.timer, SPM_STAGE_POWER);
+        SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, DT_F64, r1), rowmajor(Z, DT_F64, r2), 0.0,
+                          mrowmajor(Y, DT_F64, r2), C.st));
+      }
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_ORTH);
+      SPM_TRY(orth_f64(C, Y, m, r2, r2, 3));
+      C.cholqr_passes = 3;
+    }
+    out.Q64 = Y;
+    return SPM_OK;
+  }
+  // ---------------- mixed precision
+  const int64_t r1p = pad8(r1), r2p = pad8(r2);
+  SPM_ALLOC(C.ar, __nv_bfloat16, At, m * r1p);
+  SPM_ALLOC(C.ar, float, Om32, r1 * r2);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Zb, r1 * r2p);
+  SPM_ALLOC(C.ar, float, Y, m * r2);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Yb, m * r2p);
+  SPM_ALLOC(C.ar, float, Z, r1 * r2);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Qhi, m * r2p);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Qlo, m * r2p);
+  {
+    StageScope sc(C.timer, SPM_STAGE_SKETCH);
+    if (C.omega)
+      SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Om32, DT_F32, r2), C.st));
+    else
+      SPM_TRY(gaussian_dev(Om32, DT_F32, r1, r2, r2, seed, C.st));
+    SPM_TRY(convert2d(r1, r2, rowmajor(Om32, DT_F32, r2), mrowmajor(Zb, DT_BF16, r2p), C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_APPLY);
+    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st));
+  }
+  TcOp opAt_k{At, r1p, false};   // A~ as A-operand, K = r1
+  TcOp opAt_mn{At, r1p, true};   // A~^T as A-operand, K = m
+  TcOp opZ{Zb, r2p, true};       // Z (r1 x r2 row-major) as B-operand, K = r1
+  TcOp opY{Yb, r2p, true};       // Y (m x r2 row-major) as B-operand, K = m
+  {
+    StageScope sc(C.timer, SPM_STAGE_POWER);
+    SPM_TRY(gemm_tc(m, r2, r1, 1, &opAt_k, &opZ, 1.0f, Y, r2, 1, 1, C.st));
+  }
+  for (int t = 0; t < q; ++t) {
+    {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      SPM_TRY(convert2d(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Yb, DT_BF16, r2p), C.st));
+      SPM_TRY(gemm_tc(r1, r2, m, 1, &opAt_mn, &opY, 1.0f, Z, r2, 1, auto_splitk(r1, r2, m), C.st));
+    }
+    if (C.reorth) {
+      StageScope sc(C.timer, SPM_STAGE_ORTH);
+      SPM_TRY(orth_small_f32(C, Z, r1, r2, r2, 3));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      SPM_TRY(convert2d(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zb, DT_BF16, r2p), C.st));
+      SPM_TRY(gemm_tc(m, r2, r1, 1, &opAt_k, &opZ, 1.0f, Y, r2, 1, 1, C.st));
+    }
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_ORTH);
+    SPM_TRY(orth_big_mixed(C, Y, m, r2, r2, Qhi, Qlo));
+  }
+  out.Q32 = Y;
+  out.Qhi = Qhi;
+  out.Qlo = Qlo;
+  return SPM_OK;
+}
+
+// ------------------------------------------------------------------ argument checks
+static int check_common(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                        int64_t r2, int32_t q, const spm_opts* o) {
+  if (!S || !A) return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  if (m < 1 || lda < S->n || r2 < 1 || r2 > S->r1 || r2 > m || q < 0) return SPM_EINVAL;
+  if (o) {
+    if (o->precision != SPM_PREC_FP64 && o->precision != SPM_PREC_MIXED) return SPM_EINVAL;
+    if (o->final_passes != 0 && o->final_passes != 1 && o->final_passes != 3) return SPM_EINVAL;
+  }
+  return SPM_OK;
+}
+
+static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info) {
+  C.adt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  if (o) {
+    C.prec = o->precision;
+    C.reorth = o->reorth != 0;
+    C.final_passes = o->final_passes == 0 ? 3 : o->final_passes;
+    C.small64 = o->small_fp64 != 0;
+    C.omega = o->omega;
+  }
+  if (info && info->want_timing) C.timer.on = true;
+}
+
+static int prepare(Call& C) {
+  C.status = C.ar.alloc<int>(1);
+  C.acc = C.ar.alloc<double>(2);
+  if (!C.status || !C.acc) return SPM_ENOMEM;
+  SPM_CUDA_TRY(cudaMemsetAsync(C.status, 0, sizeof(int), C.st));
+  SPM_CUDA_TRY(cudaMemsetAsync(C.acc, 0, 2 * sizeof(double), C.st));
+  if (C.prec == SPM_PREC_MIXED && !tc_available()) return SPM_ECUDA;
+  return SPM_OK;
+}
+
+static int finish(Call& C, spm_info* info, int rc, bool has_b) {
+  if (rc != SPM_OK) return rc;
+  if (!info) return SPM_OK;
+  int dst = 0;
+  double acc[2] = {0.0, 0.0};
+  SPM_CUDA_TRY(cudaMemcpyAsync(&dst, C.status, sizeof(int), cudaMemcpyDeviceToHost, C.st));
+  SPM_CUDA_TRY(cudaMemcpyAsync(acc, C.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, C.st));
+  SPM_CUDA_TRY(cudaStreamSynchronize(C.st));
+  for (int i = 0; i < SPM_NSTAGES; ++i) info->stage_ms[i] = 0.f;
+  C.timer.collect(info->stage_ms);
+  info->device_status = dst;
+  info->cholqr_passes = C.cholqr_passes;
+  info->fro_a = sqrt(acc[0]);
+  info->resid_est = has_b ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
+  return dst == 0 ? SPM_OK : dst;
+}
+
+// Write an FP32 or FP64 device matrix into the caller's buffer of dtype adt.
+static int store_out(int64_t rows, int64_t cols, View src, void* dst, int adt, int64_t ld,
+                     cudaStream_t st) {
+  return convert2d(rows, cols, src, mrowmajor(dst, adt, ld), st);
+}
+
+// ------------------------------------------------------------------ RandSVD finish
+static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda, const RF& rf,
+                       int64_t k, void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt) {
+  const int64_t r2 = rf.r2;
+  const int edt = C.adt;
+  if (C.prec == SPM_PREC_FP64) {
+    SPM_ALLOC(C.ar, double, B, r2 * n);
+    SPM_ALLOC(C.ar, double, G, r2 * r2);
+    SPM_ALLOC(C.ar, double, Ut, r2 * r2);
+    SPM_ALLOC(C.ar, double, lam, r2);
+    SPM_ALLOC(C.ar, double, W, r2 * n);
+    SPM_ALLOC(C.ar, double, sig, r2);
+    SPM_ALLOC(C.ar, double, Uo, m * k);
+    {
+      StageScope sc(C.timer, SPM_STAGE_PROJECT);
+      SPM_TRY(gemm_simt(r2, n, m, 1.0, transpose(rowmajor(rf.Q64, DT_F64, r2)),
+                        rowmajor(A, edt, lda), 0.0, mrowmajor(B, DT_F64, n), C.st));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_SMALL);
+      SPM_TRY(sumsq(r2, n, rowmajor(B, DT_F64, n), C.acc + 1, C.st));
+      SPM_TRY(gemm_simt(r2, r2, n, 1.0, rowmajor(B, DT_F64, n), transpose(rowmajor(B, DT_F64, n)),
+                        0.0, mrowmajor(G, DT_F64, r2), C.st));
+      SPM_TRY(symmetrize(r2, G, r2, DT_F64, C.st));
+      SPM_TRY(sym_eig(r2, G, r2, Ut, r2, lam, DT_F64, C.status, C.st));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_FINISH);
+      SPM_TRY(gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(Ut, DT_F64, r2)),
+                        rowmajor(B, DT_F64, n), 0.0, mrowmajor(W, DT_F64, n), C.st));
+      SPM_TRY(norms(r2, n, rowmajor(W, DT_F64, n), false, sig, C.st));
+      SPM_TRY(scale_lines(k, n, mrowmajor(W, DT_F64, n), true, sig, true, C.st));
+      SPM_TRY(gemm_simt(m, k, r2, 1.0, rowmajor(rf.Q64, DT_F64, r2), rowmajor(Ut, DT_F64, r2), 0.0,
+                        mrowmajor(Uo, DT_F64, k), C.st));
+      SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F64, k), mrowmajor(W, DT_F64, n), C.st));
+      SPM_TRY(store_out(m, k, rowmajor(Uo, DT_F64, k), U, edt, ldu, C.st));
+      SPM_TRY(store_out(k, n, rowmajor(W, DT_F64, n), Vt, edt, ldvt, C.st));
+      SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
+    }
+    return SPM_OK;
+  }
+  // ---------------- mixed precision
+  const int64_t np_ = pad8(n), r2p = pad8(r2);
+  const int sdt = C.small64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(sdt);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Ahi, m * np_);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Alo, m * np_);
+  SPM_ALLOC(C.ar, float, B, r2 * n);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Bhi, r2 * np_);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Blo, r2 * np_);
+  SPM_ALLOC(C.ar, float, G, r2 * r2);
+  void* Gs = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  void* Ut = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  void* lam = C.ar.alloc<unsigned char>(r2 * es);
+  if (!Gs || !Ut || !lam) return SPM_ENOMEM;
+  SPM_ALLOC(C.ar, __nv_bfloat16, Uhi, r2 * r2p);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Ulo, r2 * r2p);
+  SPM_ALLOC(C.ar, float, W, r2 * n);
+  SPM_ALLOC(C.ar, double, sig, r2);
+  SPM_ALLOC(C.ar, float, Uo, m * k);
+  {
+    StageScope sc(C.timer, SPM_STAGE_PROJECT);
+    SPM_TRY(split_bf16(m, n, rowmajor(A, edt, lda), mrowmajor(Ahi, DT_BF16, np_),
+                       mrowmajor(Alo, DT_BF16, np_), C.st));
+    // B = Q^T A: A-op Q^T (M = r2, K = m) MN-major; B-op A (N = n, K = m) MN-major
+    SPM_TRY(tc_split(r2, n, m, rf.Qhi, rf.Qlo, r2p, true, Ahi, Alo, np_, true, C.final_passes, B,
+                     n, 1, C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_SMALL);
+    SPM_TRY(sumsq(r2, n, rowmajor(B, DT_F32, n), C.acc + 1, C.st));
+    SPM_TRY(split_bf16(r2, n, rowmajor(B, DT_F32, n), mrowmajor(Bhi, DT_BF16, np_),
+                       mrowmajor(Blo, DT_BF16, np_), C.st));
+    // G = B B^T: both operands B (r2 x n), K-major
+    SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st));
+    SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Gs, sdt, r2), C.st));
+    SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
+    SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st));
+    SPM_TRY(split_bf16(r2, r2, rowmajor(Ut, sdt, r2), mrowmajor(Uhi, DT_BF16, r2p),
+                       mrowmajor(Ulo, DT_BF16, r2p), C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_FINISH);
+    // W = U~^T B: A-op U~^T (M = r2, K = r2) MN-major; B-op B (N = n, K = r2) MN-major
+    SPM_TRY(tc_split(r2, n, r2, Uhi, Ulo, r2p, true, Bhi, Blo, np_, true, 3, W, n, 1, C.st));
+    SPM_TRY(norms(r2, n, rowmajor(W, DT_F32, n), false, sig, C.st));
+    SPM_TRY(scale_lines(k, n, mrowmajor(W, DT_F32, n), true, sig, true, C.st));
+    // U = Q U~[:, :k]: A-op Q (M = m, K = r2) K-major; B-op U~ (N = k, K = r2) MN-major
+    SPM_TRY(tc_split(m, k, r2, rf.Qhi, rf.Qlo, r2p, false, Uhi, Ulo, r2p, true, 3, Uo, k, 1, C.st));
+    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F32, k), mrowmajor(W, DT_F32, n), C.st));
+    SPM_TRY(store_out(m, k, rowmajor(Uo, DT_F32, k), U, edt, ldu, C.st));
+    SPM_TRY(store_out(k, n, rowmajor(W, DT_F32, n), Vt, edt, ldvt, C.st));
+    SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
+  }
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+int spm_version(void) { return 100; }
+
+const char* spm_status_string(int s) {
+  switch (s) {
+    case SPM_OK: return "ok";
+    case SPM_EINVAL: return "invalid argument";
+    case SPM_ENOMEM: return "out of device memory";
+    case SPM_ECUDA: return "CUDA error or no usable sm_103 device";
+    case SPM_EBREAKDOWN: return "Cholesky breakdown";
+    case SPM_ENONFINITE: return "non-finite value";
+    case SPM_ETIMEOUT: return "bounded device wait expired";
+    case SPM_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+int spm_device_ok(void) { return tc_available() ? 1 : 0; }
+
+int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
+                  int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
+                  float* D, int64_t ldd, int32_t splitk, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || npass < 1 || npass > 3 || !A || !B || !D || ldd < N || splitk < 1)
+    return SPM_EINVAL;
+  if (!tc_available()) return SPM_ECUDA;
+  TcOp a[3], b[3];
+  for (int q = 0; q < npass; ++q) {
+    if (!A[q] || !B[q]) return SPM_EINVAL;
+    a[q] = TcOp{(const __nv_bfloat16*)A[q], lda, a_mn != 0};
+    b[q] = TcOp{(const __nv_bfloat16*)B[q], ldb, b_mn != 0};
+  }
+  if (lda < (a_mn ? M : K) || ldb < (b_mn ? N : K)) return SPM_EINVAL;
+  return gemm_tc(M, N, K, npass, a, b, 1.0f, D, ldd, 1, splitk, as_stream(stream));
+}
+
+int spm_range_finder(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                     int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* Q,
+                     int64_t ldq, spm_info* info, void* stream) {
+  SPM_TRY(check_common(S, A, dtype, m, lda, r2, q, opts));
+  if (!Q || ldq < r2) return SPM_EINVAL;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  RF rf;
+  int rc = range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf);
+  if (rc == SPM_OK) {
+    if (C.prec == SPM_PREC_FP64)
+      rc = store_out(m, r2, rowmajor(rf.Q64, DT_F64, r2), Q, C.adt, ldq, C.st);
+    else
+      rc = store_out(m, r2, rowmajor(rf.Q32, DT_F32, r2), Q, C.adt, ldq, C.st);
+  }
+  return finish(C, info, rc, false);
+}
+
+int spm_rsvd(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda, int64_t r2,
+             int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts, void* U, int64_t ldu,
+             void* sigma, void* Vt, int64_t ldvt, spm_info* info, void* stream) {
+  SPM_TRY(check_common(S, A, dtype, m, lda, r2, q, opts));
+  if (!U || !sigma || !Vt || k < 1 || k > r2 || ldu < k || ldvt < S->n) return SPM_EINVAL;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  RF rf;
+  int rc = range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf);
+  if (rc == SPM_OK) rc = rsvd_finish(C, A, m, S->n, lda, rf, k, U, ldu, sigma, Vt, ldvt);
+  return finish(C, info, rc, true);
+}
+
+int spm_lowrank(const spm_sketch* S1, const spm_sketch* S2, const void* A, int32_t dtype,
+                int64_t m, int64_t lda, int64_t r2, int32_t q, uint64_t omega_seed,
+                const spm_opts* opts, void* Y, int64_t ldy, void* X, int64_t ldx, spm_info* info,
+                void* stream) {
+  SPM_TRY(check_common(S1, A, dtype, m, lda, r2, q, opts));
+  if (!S2 || S2->n != m || S2->r1 < r2 || !Y || !X || ldy < r2 || ldx < S1->n) return SPM_EINVAL;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  const int64_t n = S1->n, r1b = S2->r1;
+  RF rf;
+  int rc = range_finder_core(C, S1, A, m, lda, r2, q, omega_seed, rf);
+  if (rc != SPM_OK) return finish(C, info, rc, false);
+  // X = (S2^T Q)^+ (S2^T A) via CholeskyQR2 of M = S2^T Q: M = QM R, X = R^{-1} QM^T N
+  const bool f64 = C.prec == SPM_PREC_FP64;
+  const int wdt = f64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(wdt);
+  void* M = C.ar.alloc<unsigned char>(r1b * r2 * es);
+  void* N = C.ar.alloc<unsigned char>(r1b * n * es);
+  void* T1 = C.ar.alloc<unsigned char>(r2 * n * es);
+  void* T2 = C.ar.alloc<unsigned char>(r2 * n * es);
+  void* G = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  void* L1 = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  void* L2 = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  void* Mn = C.ar.alloc<unsigned char>(r1b * r2 * es);
+  if (!M || !N || !T1 || !T2 || !G || !L1 || !L2 || !Mn) return finish(C, info, SPM_ENOMEM, false);
+  do {
+    {
+      StageScope sc(C.timer, SPM_STAGE_PROJECT);
+      const void* Qp = f64 ? (const void*)rf.Q64 : (const void*)rf.Q32;
+      rc = sketch_apply_t_dev(S2, Qp, wdt, r2, r2, M, wdt, r2, C.st);
+      if (rc) break;
+      rc = sketch_apply_t_dev(S2, A, C.adt, n, lda, N, wdt, n, C.st);
+      if (rc) break;
+    }
+    StageScope sc(C.timer, SPM_STAGE_SMALL);
+    void* Ls[2] = {L1, L2};
+    for (int ps = 0; ps < 2 && rc == SPM_OK; ++ps) {
+      rc = gemm_simt(r2, r2, r1b, 1.0, transpose(rowmajor(M, wdt, r2)), rowmajor(M, wdt, r2), 0.0,
+                     mrowmajor(G, wdt, r2), C.st);
+      if (rc) break;
+      rc = cholesky_inv(r2, G, r2, Ls[ps], r2, wdt, C.status, C.st);
+      if (rc) break;
+      rc = gemm_simt(r1b, r2, r2, 1.0, rowmajor(M, wdt, r2), transpose(rowmajor(Ls[ps], wdt, r2)),
+                     0.0, mrowmajor(Mn, wdt, r2), C.st);
+      if (rc) break;
+      rc = convert2d(r1b, r2, rowmajor(Mn, wdt, r2), mrowmajor(M, wdt, r2), C.st);
+    }
+    if (rc) break;
+    // T1 = QM^T N ; T2 = L2^{-T} T1 ; T1 = L1^{-T} T2
+    rc = gemm_simt(r2, n, r1b, 1.0, transpose(rowmajor(M, wdt, r2)), rowmajor(N, wdt, n), 0.0,
+                   mrowmajor(T1, wdt, n), C.st);
+    if (rc) break;
+    rc = gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(L2, wdt, r2)), rowmajor(T1, wdt, n), 0.0,
+                   mrowmajor(T2, wdt, n), C.st);
+    if (rc) break;
+    rc = gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(L1, wdt, r2)), rowmajor(T2, wdt, n), 0.0,
+                   mrowmajor(T1, wdt, n), C.st);
+    if (rc) break;
+    StageScope sc2(C.timer, SPM_STAGE_FINISH);
+    rc = store_out(r2, n, rowmajor(T1, wdt, n), X, C.adt, ldx, C.st);
+    if (rc) break;
+    if (f64)
+      rc = store_out(m, r2, rowmajor(rf.Q64, DT_F64, r2), Y, C.adt, ldy, C.st);
+    else
+      rc = store_out(m, r2, rowmajor(rf.Q32, DT_F32, r2), Y, C.adt, ldy, C.st);
+  } while (0);
+  return finish(C, info, rc, false);
+}
+
+int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, int64_t lda,
+                int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* Cout,
+                int64_t ldc, void* Wout, int64_t ldw, spm_info* info, void* stream) {
+  SPM_TRY(check_common(S, A, dtype, n, lda, r2, q, opts));
+  if (S->n != n || !Cout || !Wout || ldc < r2 || ldw < r2) return SPM_EINVAL;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  const int64_t r1 = S->r1;
+  const bool f64 = C.prec == SPM_PREC_FP64;
+  const int wdt = f64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(wdt);
+  void* Ct = C.ar.alloc<unsigned char>(n * r1 * es);
+  void* Wt = C.ar.alloc<unsigned char>(r1 * r1 * es);
+  void* Y = C.ar.alloc<unsigned char>(r1 * r2 * es);
+  void* Yn = C.ar.alloc<unsigned char>(r1 * r2 * es);
+  void* Cw = C.ar.alloc<unsigned char>(n * r2 * es);
+  void* T = C.ar.alloc<unsigned char>(r1 * r2 * es);
+  void* Ww = C.ar.alloc<unsigned char>(r2 * r2 * es);
+  if (!Ct || !Wt || !Y || !Yn || !Cw || !T || !Ww) return SPM_ENOMEM;
+  int rc = SPM_OK;
+  do {
+    {
+      StageScope sc(C.timer, SPM_STAGE_SKETCH);
+      if (C.omega)
+        rc = convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Y, wdt, r2), C.st);
+      else
+        rc = gaussian_dev(Y, wdt, r1, r2, r2, omega_seed, C.st);
+      if (rc) break;
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_APPLY);
+      rc = sketch_apply_dev(S, A, C.adt, n, lda, Ct, wdt, r1, C.acc, C.st);  // C~ = A S
+      if (rc) break;
+      rc = sketch_apply_t_dev(S, Ct, wdt, r1, r1, Wt, wdt, r1, C.st);       // W~ = S^T C~
+      if (rc) break;
+      rc = symmetrize(r1, Wt, r1, wdt, C.st);
+      if (rc) break;
+    }
+    for (int t = 0; t < q && rc == SPM_OK; ++t) {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      rc = gemm_simt(r1, r2, r1, 1.0, rowmajor(Wt, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
+                     mrowmajor(Yn, wdt, r2), C.st);
+      if (rc) break;
+      rc = convert2d(r1, r2, rowmajor(Yn, wdt, r2), mrowmajor(Y, wdt, r2), C.st);
+      if (rc) break;
+      if (C.reorth) {
+        if (f64)
+          rc = orth_f64(C, (double*)Y, r1, r2, r2, 3);
+        else
+          rc = orth_small_f32(C, (float*)Y, r1, r2, r2, 3);
+      }
+    }
+    if (rc) break;
+    {
+      StageScope sc(C.timer, SPM_STAGE_PROJECT);
+      rc = gemm_simt(n, r2, r1, 1.0, rowmajor(Ct, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
+                     mrowmajor(Cw, wdt, r2), C.st);  // C = C~ Y
+      if (rc) break;
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_FINISH);
+      rc = gemm_simt(r1, r2, r1, 1.0, rowmajor(Wt, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
+                     mrowmajor(T, wdt, r2), C.st);
+      if (rc) break;
+      rc = gemm_simt(r2, r2, r1, 1.0, transpose(rowmajor(Y, wdt, r2)), rowmajor(T, wdt, r2), 0.0,
+                     mrowmajor(Ww, wdt, r2), C.st);  // W = Y^T W~ Y
+      if (rc) break;
+      rc = symmetrize(r2, Ww, r2, wdt, C.st);
+      if (rc) break;
+      rc = store_out(n, r2, rowmajor(Cw, wdt, r2), Cout, C.adt, ldc, C.st);
+      if (rc) break;
+      rc = store_out(r2, r2, rowmajor(Ww, wdt, r2), Wout, C.adt, ldw, C.st);
+    }
+  } while (0);
+  return finish(C, info, rc, false);
+}
+
+}  // extern "C"

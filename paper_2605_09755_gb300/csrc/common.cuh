@@ -1,0 +1,146 @@
+// Shared host/device helpers of libspm: status plumbing, stream-ordered
+// workspace, device status word, small math helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/spm.h"
+
+namespace spm {
+
+// Device-side error codes written into the status word (first error wins).
+enum DevStatus : int {
+  DEV_OK = 0,
+  DEV_BREAKDOWN = SPM_EBREAKDOWN,
+  DEV_NONFINITE = SPM_ENONFINITE,
+  DEV_TIMEOUT = SPM_ETIMEOUT,
+};
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+#define SPM_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t _e = (expr);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      if (_e == cudaErrorMemoryAllocation) return SPM_ENOMEM;                \
+      return SPM_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+#define SPM_TRY(expr)               \
+  do {                              \
+    int _s = (expr);                \
+    if (_s != SPM_OK) return _s;    \
+  } while (0)
+
+#define SPM_LAUNCH_CHECK() SPM_CUDA_TRY(cudaGetLastError())
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Stream-ordered scratch arena: every buffer is cudaMallocAsync'ed on the
+// call's stream and released by cudaFreeAsync when the arena dies.
+struct Arena {
+  cudaStream_t stream;
+  void* ptrs[64];
+  int count = 0;
+  bool failed = false;
+  explicit Arena(cudaStream_t s) : stream(s) {}
+  ~Arena() {
+    for (int i = count - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], stream);
+  }
+  template <typename T>
+  T* alloc(int64_t elems) {
+    if (elems <= 0) elems = 1;
+    if (count >= 64) { failed = true; return nullptr; }
+    void* p = nullptr;
+    // round to 256 B so that every TMA base is aligned
+    size_t bytes = (size_t)round_up(elems * (int64_t)sizeof(T), 256);
+    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs[count++] = p;
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+#define SPM_ALLOC(arena, T, name, elems)          \
+  T* name = (arena).template alloc<T>(elems);     \
+  if (!name) return SPM_ENOMEM
+
+// Event-based stage timer, used only when the caller asks for timing.
+struct StageTimer {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev[2 * SPM_NSTAGES * 8];
+  int stage_of[SPM_NSTAGES * 8];
+  int n = 0;
+  int cur = -1;
+  void begin(int stage) {
+    if (!on) return;
+    if (cur >= 0) end();  // a nested stage closes the enclosing one
+    if (n >= SPM_NSTAGES * 8) return;
+    cudaEventCreate(&ev[2 * n]);
+    cudaEventCreate(&ev[2 * n + 1]);
+    cudaEventRecord(ev[2 * n], stream);
+    stage_of[n] = stage;
+    cur = n;
+  }
+  void end() {
+    if (!on || cur < 0) return;
+    cudaEventRecord(ev[2 * cur + 1], stream);
+    ++n;
+    cur = -1;
+  }
+  void collect(float* out) {
+    if (!on) return;
+    cudaStreamSynchronize(stream);
+    for (int i = 0; i < n; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      out[stage_of[i]] += ms;
+      cudaEventDestroy(ev[2 * i]);
+      cudaEventDestroy(ev[2 * i + 1]);
+    }
+    n = 0;
+  }
+  ~StageTimer() {
+    for (int i = 0; i < n; ++i) {
+      cudaEventDestroy(ev[2 * i]);
+      cudaEventDestroy(ev[2 * i + 1]);
+    }
+  }
+};
+
+struct StageScope {
+  StageTimer& t;
+  StageScope(StageTimer& tt, int stage) : t(tt) { t.begin(stage); }
+  ~StageScope() { t.end(); }
+};
+
+}  // namespace spm
+
+// The sketch handle (opaque to C callers).
+struct spm_sketch {
+  int64_t n;
+  int64_t r1;
+  int32_t s;
+  int32_t kind;
+  uint64_t seed;
+  cudaStream_t stream;
+  int32_t* cols;          // n*s, draw order
+  int8_t* signs;          // n*s
+  int64_t* bucket_ptr;    // r1+1
+  uint32_t* bucket_ent;   // n*s: row index j in bits 0..30, sign (1 = minus) in bit 31
+};

@@ -1,0 +1,96 @@
+// Internal (C++) interfaces shared by the libspm translation units.
+#pragma once
+#include "common.cuh"
+
+namespace spm {
+
+// Element types used inside the library.
+enum Dt : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
+
+inline size_t dt_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+
+// A strided matrix view: element (i, j) at p[i*rs + j*cs] (in elements).
+struct View {
+  const void* p;
+  int dt;
+  int64_t rs, cs;
+};
+struct MView {
+  void* p;
+  int dt;
+  int64_t rs, cs;
+};
+inline View rowmajor(const void* p, int dt, int64_t ld) { return View{p, dt, ld, 1}; }
+inline View colmajor(const void* p, int dt, int64_t ld) { return View{p, dt, 1, ld}; }
+inline View transpose(View v) { return View{v.p, v.dt, v.cs, v.rs}; }
+inline MView mrowmajor(void* p, int dt, int64_t ld) { return MView{p, dt, ld, 1}; }
+inline View cview(MView v) { return View{v.p, v.dt, v.rs, v.cs}; }
+
+// ---------------------------------------------------------------- sketch.cu
+// out (m x r1) = A (m x n) S ; out_dt in {F32, F64, BF16}; accumulates |A|_F^2
+// into *fro2 (device double) when fro2 != nullptr.
+int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
+                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st);
+// out (r1 x p) = S^T X, X (n x p, row stride ldx)
+int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
+                       void* out, int out_dt, int64_t ldo, cudaStream_t st);
+int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                 cudaStream_t st);
+
+// ---------------------------------------------------------------- gemm_simt.cu
+// C = alpha * A(MxK) * B(KxN) + beta * C  on CUDA cores.  Accumulates in FP64 if
+// any operand is FP64, else FP32.  batch > 1: pointers advance by the strides.
+int gemm_simt(int64_t M, int64_t N, int64_t K, double alpha, View A, View B, double beta, MView C,
+              cudaStream_t st, int batch = 1, int64_t sA = 0, int64_t sB = 0, int64_t sC = 0);
+
+// ---------------------------------------------------------------- gemm_tc.cu
+// One BF16 operand of a tcgen05 product.  `p` points at a row-major array with
+// leading dimension `ld` (elements, multiple of 8).  For the A operand (M x K):
+// mn_major = false -> array is M x K (K contiguous); true -> array is K x M.
+// For the B operand (N x K): mn_major = false -> array is N x K; true -> K x N.
+struct TcOp {
+  const __nv_bfloat16* p;
+  int64_t ld;
+  bool mn_major;
+};
+// D(M x N, fp32) = alpha * sum_{q < npass} A[q] * B[q]^T, written at
+// D[i*d_rs + j*d_cs].  splitk > 1 splits K in equal chunks; partial sums are
+// reduced deterministically (fixed order) before D is written.
+int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
+            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st);
+bool tc_available();
+
+// ---------------------------------------------------------------- dense.cu
+// y = convert(x) elementwise on a strided 2-D view (rows x cols).
+int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st);
+// hi = bf16(x), lo = bf16(x - hi)  (split-precision operands)
+int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStream_t st);
+// Cholesky G = L L^T of an r x r SPD matrix (row-major, ld), lower L in place,
+// and Linv = L^{-1} (row-major, ldi).  dt: F32 or F64.  Breakdown -> status.
+int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* status,
+                 cudaStream_t st);
+// Add shift * I to the diagonal, where shift = coef * (sum of diag) (device-computed).
+int add_trace_shift(int64_t r, void* G, int64_t ldg, int dt, double coef, cudaStream_t st);
+// Symmetric eigendecomposition by parallel cyclic Jacobi: A (r x r, row-major,
+// overwritten), V (r x r row-major eigenvectors in columns), lam (r) sorted
+// descending, V columns permuted accordingly.  dt F32 or F64.
+int sym_eig(int64_t r, void* A, int64_t lda, void* V, int64_t ldv, void* lam, int dt, int* status,
+            cudaStream_t st);
+// out[j] = sqrt(sum_i X[i,j]^2) for columns (col = true) or rows (col = false), in FP64.
+int norms(int64_t rows, int64_t cols, View X, bool by_col, double* out, cudaStream_t st);
+// Scale rows (or columns) of X by s[i] (or 1/s[i] when inv).
+int scale_lines(int64_t rows, int64_t cols, MView X, bool rows_not_cols, const double* s, bool inv,
+                cudaStream_t st);
+// Sum of squares of a strided view into *acc (device double, accumulated).
+int sumsq(int64_t rows, int64_t cols, View X, double* acc, cudaStream_t st);
+// Sign convention: for each column j < k of U (m x k), flip column j of U and
+// row j of Vt (k x n) so that the largest-magnitude entry of U[:, j] is > 0.
+int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st);
+// Copy sigma (FP64 device) to the output dtype.
+int copy_vec(int64_t n, const double* src, void* dst, int dt, cudaStream_t st);
+// Symmetrise in place: A = (A + A^T) / 2.
+int symmetrize(int64_t r, void* A, int64_t lda, int dt, cudaStream_t st);
+// Scan a strided view for NaN/Inf; sets *status to SPM_ENONFINITE.
+int check_finite(int64_t rows, int64_t cols, View X, int* status, cudaStream_t st);
+
+}  // namespace spm

@@ -1,0 +1,596 @@
+// Sparse sign sketch S (Lemma 3.2 item 2), Gaussian Omega (Algorithm 1 input)
+// and the sketch products A S (Algorithm 1 line 1, Algorithm 3 line 1) and
+// S^T X (Algorithm 2 line 2, Algorithm 3 line 1).
+//
+// Layout of a sketch on the device
+//   cols[n*s], signs[n*s]: entry t of row j in draw order (bit-exact with the
+//     CPU oracle for the same seed).
+//   Chunked CSC: rows j are grouped into chunks of CHUNK = 512; inside a chunk,
+//   entries are sorted by column c and, within a column, by ascending j.
+//   cptr[k*r1 + c] is the start of the (chunk k, column c) segment in ent[];
+//   ent[] packs j (bits 0..30) and the sign (bit 31 set = minus).
+//   The segments of chunk k form the contiguous range [k*CHUNK*s, ...).
+#include <math.h>
+
+#include "internal.cuh"
+#include "rng.cuh"
+
+namespace spm {
+
+static constexpr int CHUNK = 512;          // rows of S (columns of A) per tile
+static constexpr int APPLY_ROWS = 32;      // rows of A per CTA (one per lane)
+static constexpr int APPLY_WARPS = 16;
+static constexpr int APPLY_THREADS = APPLY_WARPS * 32;
+static constexpr int APPLY_TILE_LD = APPLY_ROWS + 1;   // padded: conflict-free
+static constexpr uint32_t SIGN_BIT = 0x80000000u;
+
+// ------------------------------------------------------------------ a1: generation
+__global__ void k_sketch_gen(int64_t n, uint32_t r1, int s, uint32_t k0, uint32_t k1,
+                             int32_t* __restrict__ cols, int8_t* __restrict__ signs,
+                             int* __restrict__ status) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
+  int32_t chosen[64];
+  uint32_t u = 0, blk = 0xFFFFFFFFu;
+  u32x4 w = {0, 0, 0, 0};
+  for (int t = 0; t < s; ++t) {
+    for (;;) {
+      const uint32_t b = u >> 2;
+      if (b != blk) {
+        w = philox4x32_10(jlo, jhi, b, 0u, k0, k1);
+        blk = b;
+      }
+      const uint32_t word = pick(w, u & 3u);
+      ++u;
+      const int32_t cand = (int32_t)(((uint64_t)word * r1) >> 32);
+      bool dup = false;
+      for (int q = 0; q < t; ++q) dup |= (chosen[q] == cand);
+      if (!dup) {
+        chosen[t] = cand;
+        break;
+      }
+      if (u > (1u << 26)) {  // cannot happen for s <= r1; bounded anyway
+        set_status(status, DEV_TIMEOUT);
+        chosen[t] = 0;
+        break;
+      }
+    }
+  }
+  uint32_t sblk = 0xFFFFFFFFu;
+  u32x4 sw = {0, 0, 0, 0};
+  for (int t = 0; t < s; ++t) {
+    const uint32_t b = (uint32_t)(t >> 7);
+    if (b != sblk) {
+      sw = philox4x32_10(jlo, jhi, b, 1u, k0, k1);
+      sblk = b;
+    }
+    const uint32_t word = pick(sw, (uint32_t)((t >> 5) & 3));
+    const uint32_t bit = (word >> (t & 31)) & 1u;
+    cols[j * s + t] = chosen[t];
+    signs[j * s + t] = bit ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+__global__ void k_sketch_identity(int64_t n, int32_t* cols, int8_t* signs, uint32_t* ent,
+                                  int64_t* cptr, int nchunks) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) {
+    cols[j] = (int32_t)j;
+    signs[j] = 1;
+    ent[j] = (uint32_t)j;
+  }
+  // cptr[k*n + c]: column c lives only in chunk c / CHUNK
+  const int64_t total = (int64_t)nchunks * n;
+  for (int64_t q = j; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = q / n, c = q % n;
+    const int64_t base = k * CHUNK;
+    const int64_t len = min64(CHUNK, n - base);
+    // segment (k, c) holds entry c only when c lies in chunk k
+    cptr[q] = base + min64(max64(c - base, 0), len);
+  }
+  if (j == 0) cptr[total] = n;
+}
+
+// Stable counting sort of one chunk's entries by column (one CTA per chunk).
+__global__ void k_chunk_sort(int64_t n, int r1, int s, const int32_t* __restrict__ cols,
+                             const int8_t* __restrict__ signs, int64_t* __restrict__ cptr,
+                             uint32_t* __restrict__ ent) {
+  extern __shared__ int hist[];  // r1 + 1 ints
+  const int k = blockIdx.x;
+  const int64_t j0 = (int64_t)k * CHUNK;
+  const int64_t j1 = min(n, j0 + CHUNK);
+  const int64_t e0 = j0 * s, e1 = j1 * s;
+  for (int c = threadIdx.x; c <= r1; c += blockDim.x) hist[c] = 0;
+  __syncthreads();
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&hist[cols[e]], 1);
+  __syncthreads();
+  // exclusive scan over r1 bins by thread 0 of each warp-sized slice (simple, r1 small)
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int c = 0; c < r1; ++c) {
+      const int v = hist[c];
+      hist[c] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < r1; c += blockDim.x) cptr[(int64_t)k * r1 + c] = e0 + hist[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = e0; base < e1; base += 32) {
+      const int64_t e = base + lane;
+      const bool valid = e < e1;
+      const int c = valid ? cols[e] : -1 - lane;
+      const unsigned mask = __match_any_sync(0xFFFFFFFFu, c);
+      const int rank = __popc(mask & lt);
+      const int leader = __ffs(mask) - 1;
+      int pos = 0;
+      if (valid) pos = hist[c] + rank;
+      __syncwarp();
+      if (valid && lane == leader) hist[c] += __popc(mask);
+      __syncwarp();
+      if (valid) {
+        const uint32_t j = (uint32_t)(e / s);
+        ent[e0 + pos] = j | (signs[e] < 0 ? SIGN_BIT : 0u);
+      }
+    }
+  }
+}
+
+__global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
+
+// Plain CSC view for spm_sketch_tables: count per column over all chunks.
+__global__ void k_bucket_counts(int r1, int nchunks, const int64_t* __restrict__ cptr,
+                                int64_t* __restrict__ cnt) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= r1) return;
+  int64_t tot = 0;
+  for (int k = 0; k < nchunks; ++k) {
+    const int64_t b = cptr[(int64_t)k * r1 + c];
+    const int64_t e = cptr[(int64_t)k * r1 + c + 1];
+    tot += e - b;
+  }
+  cnt[c] = tot;
+}
+
+__global__ void k_exclusive_scan_small(int64_t count, const int64_t* __restrict__ in,
+                                       int64_t* __restrict__ out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int64_t i = 0; i < count; ++i) {
+      out[i] = run;
+      run += in[i];
+    }
+    out[count] = run;
+  }
+}
+
+__global__ void k_bucket_fill(int r1, int nchunks, const int64_t* __restrict__ cptr,
+                              const uint32_t* __restrict__ ent, const int64_t* __restrict__ bptr,
+                              int32_t* __restrict__ rows, int8_t* __restrict__ sg) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= r1) return;
+  int64_t o = bptr[c];
+  for (int k = 0; k < nchunks; ++k) {
+    const int64_t b = cptr[(int64_t)k * r1 + c];
+    const int64_t e = cptr[(int64_t)k * r1 + c + 1];
+    for (int64_t p = b; p < e; ++p, ++o) {
+      const uint32_t v = ent[p];
+      if (rows) rows[o] = (int32_t)(v & ~SIGN_BIT);
+      if (sg) sg[o] = (v & SIGN_BIT) ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ a2: Omega
+template <typename T>
+__global__ void k_gaussian(int64_t rows, int64_t cols, int64_t ld, uint32_t k0, uint32_t k1,
+                           T* __restrict__ out) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = (uint64_t)e >> 1;
+    const u32x4 w = philox4x32_10((uint32_t)p, (uint32_t)(p >> 32), 0u, 2u, k0, k1);
+    const uint64_t x1 = ((uint64_t)w.y << 21) | (uint64_t)(w.x >> 11);
+    const uint64_t x2 = ((uint64_t)w.w << 21) | (uint64_t)(w.z >> 11);
+    const double u1 = (double)(x1 + 1ull) * 0x1.0p-53;
+    const double u2 = (double)x2 * 0x1.0p-53;
+    const double rad = sqrt(-2.0 * log(u1));
+    const double ang = 6.283185307179586 * u2;
+    const double z = (e & 1) ? rad * sin(ang) : rad * cos(ang);
+    const int64_t i = e / cols, j = e % cols;
+    out[i * ld + j] = (T)z;
+  }
+}
+
+// ------------------------------------------------------------------ a3: A S
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename TO>
+__device__ __forceinline__ TO to_out(double v);
+template <>
+__device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ double to_out<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
+// One CTA: 32 rows of A (lane = row) x a group of CG = 16 warps * CPW output
+// columns.  The A tile (32 rows x CHUNK columns) is staged transposed in shared
+// memory ([jj][row], row stride 33) so that one warp-wide read of a column jj
+// hits 32 distinct banks; every bucket entry then costs one conflict-free
+// shared load and one FMA per lane.  Accumulators stay in registers across
+// all chunks.  NBUF = 2 double-buffers the tile with 4/8-byte cp.async.
+template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
+__global__ void __launch_bounds__(APPLY_THREADS)
+    k_sketch_apply(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, int r1,
+                   int nchunks, const int64_t* __restrict__ cptr,
+                   const uint32_t* __restrict__ ent, TO* __restrict__ out, int64_t ldo,
+                   int col_groups, double scale, double* __restrict__ fro2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* tile = reinterpret_cast<TA*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rb = blockIdx.x / col_groups;
+  const int cg = blockIdx.x % col_groups;
+  const int64_t row0 = rb * APPLY_ROWS;
+  const int nrows = (int)min64(APPLY_ROWS, m - row0);
+  const int cbeg = cg * (APPLY_WARPS * CPW) + warp * CPW;
+  const bool do_fro = (fro2 != nullptr) && (cg == 0);
+  TACC acc[CPW];
+#pragma unroll
+  for (int i = 0; i < CPW; ++i) acc[i] = (TACC)0;
+  double fro_local = 0.0;
+
+  // stage chunk k into buffer b: thread tid owns column jj = tid (+512 ...)
+  auto stage = [&](int k, int b) {
+    TA* t = tile + (size_t)b * CHUNK * APPLY_TILE_LD;
+    const int64_t j0 = (int64_t)k * CHUNK;
+    const int wcnt = (int)min64(CHUNK, n - j0);
+    for (int jj = tid; jj < CHUNK; jj += APPLY_THREADS) {
+#pragma unroll 8
+      for (int r = 0; r < APPLY_ROWS; ++r) {
+        TA* dst = t + jj * APPLY_TILE_LD + r;
+        if (r < nrows && jj < wcnt)
+          cp_async_elem(dst, A + (row0 + r) * lda + j0 + jj);
+        else
+          *dst = (TA)0;
+      }
+    }
+    cp_async_commit();
+  };
+
+  if (NBUF == 2) stage(0, 0);
+  for (int k = 0; k < nchunks; ++k) {
+    const int b = (NBUF == 2) ? (k & 1) : 0;
+    if (NBUF == 2) {
+      if (k + 1 < nchunks) {
+        stage(k + 1, b ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      stage(k, 0);
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const TA* t = tile + (size_t)b * CHUNK * APPLY_TILE_LD;
+    if (do_fro) {
+      for (int jj = tid; jj < CHUNK; jj += APPLY_THREADS) {
+#pragma unroll 8
+        for (int r = 0; r < APPLY_ROWS; ++r) {
+          const double v = (double)t[jj * APPLY_TILE_LD + r];
+          fro_local += v * v;
+        }
+      }
+    }
+    const uint32_t j0 = (uint32_t)k * CHUNK;
+    const int64_t* cp = cptr + (int64_t)k * r1;
+#pragma unroll
+    for (int i = 0; i < CPW; ++i) {
+      const int c = cbeg + i;
+      if (c < r1) {
+        int64_t p = __ldg(cp + c);
+        const int64_t pe = __ldg(cp + c + 1);
+        for (; p < pe; ++p) {
+          const uint32_t e = __ldg(ent + p);
+          const uint32_t jj = (e & ~SIGN_BIT) - j0;
+          if (jj >= (uint32_t)CHUNK) continue;  // cannot happen with consistent tables
+          const TACC v = (TACC)t[jj * APPLY_TILE_LD + lane];
+          acc[i] += (e & SIGN_BIT) ? -v : v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: transpose the 32 x CPW accumulator block of each warp through
+  // shared memory so that stores are row-contiguous.
+  TACC* st = reinterpret_cast<TACC*>(smem_raw) + (size_t)warp * APPLY_ROWS * (CPW + 1);
+#pragma unroll
+  for (int i = 0; i < CPW; ++i) st[lane * (CPW + 1) + i] = acc[i];
+  __syncwarp();
+  for (int r = 0; r < nrows; ++r) {
+    for (int i = lane; i < CPW; i += 32) {
+      const int c = cbeg + i;
+      if (c < r1) out[(row0 + r) * ldo + c] = to_out<TO>((double)st[r * (CPW + 1) + i] * scale);
+    }
+  }
+  if (do_fro) {
+    // block reduction of fro_local
+    for (int o = 16; o > 0; o >>= 1) fro_local += __shfl_xor_sync(0xFFFFFFFFu, fro_local, o);
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem_raw);
+    if (lane == 0) red[warp] = fro_local;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < APPLY_WARPS; ++w) s += red[w];
+      atomicAdd(fro2, s);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ S^T X
+// One CTA per (output row c, strip of 256 columns of X); c varies fastest so
+// that all CTAs of one strip run together and re-reads of X rows hit L2.
+template <typename TX, typename TACC, typename TO>
+__global__ void __launch_bounds__(256)
+    k_sketch_apply_t(const TX* __restrict__ X, int64_t p, int64_t ldx, int r1, int nchunks,
+                     const int64_t* __restrict__ cptr, const uint32_t* __restrict__ ent,
+                     TO* __restrict__ out, int64_t ldo, double scale) {
+  const int c = blockIdx.x % r1;
+  const int64_t strip = blockIdx.x / r1;
+  const int64_t col = strip * 256 + threadIdx.x;
+  TACC acc = 0;
+  if (col < p) {
+    for (int k = 0; k < nchunks; ++k) {
+      const int64_t b = __ldg(cptr + (int64_t)k * r1 + c);
+      const int64_t e = __ldg(cptr + (int64_t)k * r1 + c + 1);
+      for (int64_t q = b; q < e; ++q) {
+        const uint32_t v = __ldg(ent + q);
+        const int64_t j = (int64_t)(v & ~SIGN_BIT);
+        const TACC x = (TACC)X[j * ldx + col];
+        acc += (v & SIGN_BIT) ? -x : x;
+      }
+    }
+    out[(int64_t)c * ldo + col] = to_out<TO>((double)acc * scale);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static int64_t nchunks_of(int64_t n) { return cdiv(n, CHUNK); }
+
+int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                 cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return SPM_OK;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int64_t total = rows * cols;
+  const int blocks = (int)min64(cdiv(total, 256), 152 * 16);
+  if (dt == DT_F64)
+    k_gaussian<double><<<blocks, 256, 0, st>>>(rows, cols, ld, k0, k1, (double*)out);
+  else if (dt == DT_F32)
+    k_gaussian<float><<<blocks, 256, 0, st>>>(rows, cols, ld, k0, k1, (float*)out);
+  else
+    return SPM_EINVAL;
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
+static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda, TO* out,
+                        int64_t ldo, double* fro2, cudaStream_t st) {
+  const int64_t nch = nchunks_of(S->n);
+  const int cgsz = APPLY_WARPS * CPW;
+  const int col_groups = (int)cdiv(S->r1, cgsz);
+  const int64_t row_blocks = cdiv(m, APPLY_ROWS);
+  const int64_t grid = row_blocks * col_groups;
+  if (grid > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  size_t tile_bytes = (size_t)NBUF * CHUNK * APPLY_TILE_LD * sizeof(TA);
+  size_t epi_bytes = (size_t)APPLY_WARPS * APPLY_ROWS * (CPW + 1) * sizeof(TACC);
+  size_t smem = tile_bytes > epi_bytes ? tile_bytes : epi_bytes;
+  auto kern = k_sketch_apply<TA, TACC, TO, CPW, NBUF>;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double scale = (S->kind == SPM_SKETCH_IDENTITY) ? 1.0 : 1.0 / sqrt((double)S->s);
+  kern<<<(unsigned)grid, APPLY_THREADS, smem, st>>>(A, m, S->n, lda, (int)S->r1, (int)nch,
+                                                   S->bucket_ptr, S->bucket_ent, out, ldo,
+                                                   col_groups, scale, fro2);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
+                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st) {
+  if (m <= 0) return SPM_OK;
+  if (a_dt == DT_F32) {
+    const float* a = (const float*)A;
+    if (out_dt == DT_F32) return launch_apply<float, float, float, 32, 2>(S, a, m, lda, (float*)out, ldo, fro2, st);
+    if (out_dt == DT_BF16)
+      return launch_apply<float, float, __nv_bfloat16, 32, 2>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st);
+    if (out_dt == DT_F64) return launch_apply<float, double, double, 16, 2>(S, a, m, lda, (double*)out, ldo, fro2, st);
+  } else if (a_dt == DT_F64) {
+    const double* a = (const double*)A;
+    if (out_dt == DT_F64) return launch_apply<double, double, double, 16, 1>(S, a, m, lda, (double*)out, ldo, fro2, st);
+    if (out_dt == DT_F32) return launch_apply<double, double, float, 16, 1>(S, a, m, lda, (float*)out, ldo, fro2, st);
+    if (out_dt == DT_BF16)
+      return launch_apply<double, double, __nv_bfloat16, 16, 1>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st);
+  }
+  return SPM_EINVAL;
+}
+
+int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
+                       void* out, int out_dt, int64_t ldo, cudaStream_t st) {
+  if (p <= 0) return SPM_OK;
+  const int64_t strips = cdiv(p, 256);
+  const int64_t grid = strips * S->r1;
+  if (grid > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  const double scale = (S->kind == SPM_SKETCH_IDENTITY) ? 1.0 : 1.0 / sqrt((double)S->s);
+  const int nch = (int)nchunks_of(S->n);
+  const int r1 = (int)S->r1;
+#define SPM_APT(TX, TACC, TO)                                                                 \
+  k_sketch_apply_t<TX, TACC, TO><<<(unsigned)grid, 256, 0, st>>>((const TX*)X, p, ldx, r1, nch, \
+                                                                 S->bucket_ptr, S->bucket_ent, \
+                                                                 (TO*)out, ldo, scale)
+  if (x_dt == DT_F32 && out_dt == DT_F32) SPM_APT(float, float, float);
+  else if (x_dt == DT_F32 && out_dt == DT_F64) SPM_APT(float, double, double);
+  else if (x_dt == DT_F64 && out_dt == DT_F64) SPM_APT(double, double, double);
+  else if (x_dt == DT_F64 && out_dt == DT_F32) SPM_APT(double, double, float);
+  else if (x_dt == DT_F32 && out_dt == DT_BF16) SPM_APT(float, float, __nv_bfloat16);
+  else if (x_dt == DT_BF16 && out_dt == DT_F32) SPM_APT(__nv_bfloat16, float, float);
+  else return SPM_EINVAL;
+#undef SPM_APT
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64_t seed,
+                      int32_t kind, void* stream) {
+  if (!out) return SPM_EINVAL;
+  *out = nullptr;
+  if (n < 1 || r1 < 1 || s < 1 || n > 0x7FFFFFFF || r1 > 0x7FFFFFFF) return SPM_EINVAL;
+  if (kind == SPM_SKETCH_SPARSE_SIGN) {
+    if (s > r1 || s > 64) return SPM_EINVAL;
+    if (r1 > 48 * 1024) return SPM_EUNSUPPORTED;  // per-chunk histogram lives in shared memory
+  } else if (kind == SPM_SKETCH_IDENTITY) {
+    if (r1 != n || s != 1) return SPM_EINVAL;
+  } else {
+    return SPM_EINVAL;
+  }
+  if (n * (int64_t)s > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  spm_sketch* S = new spm_sketch();
+  S->n = n;
+  S->r1 = r1;
+  S->s = s;
+  S->kind = kind;
+  S->seed = seed;
+  S->stream = st;
+  const int64_t nnz = n * s;
+  const int64_t nch = nchunks_of(n);
+  auto fail = [&](int code) {
+    spm_sketch_destroy(S);
+    return code;
+  };
+  if (cudaMallocAsync((void**)&S->cols, nnz * sizeof(int32_t), st) != cudaSuccess) return fail(SPM_ENOMEM);
+  if (cudaMallocAsync((void**)&S->signs, nnz * sizeof(int8_t), st) != cudaSuccess) return fail(SPM_ENOMEM);
+  if (cudaMallocAsync((void**)&S->bucket_ent, nnz * sizeof(uint32_t), st) != cudaSuccess) return fail(SPM_ENOMEM);
+  if (cudaMallocAsync((void**)&S->bucket_ptr, (nch * r1 + 1) * sizeof(int64_t), st) != cudaSuccess)
+    return fail(SPM_ENOMEM);
+  if (kind == SPM_SKETCH_IDENTITY) {
+    const int64_t blocks = cdiv(max64(n, 1), 256);
+    k_sketch_identity<<<(unsigned)min64(blocks, 65535 * 16), 256, 0, st>>>(
+        n, S->cols, S->signs, S->bucket_ent, S->bucket_ptr, (int)nch);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+  } else {
+    k_sketch_gen<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(n, (uint32_t)r1, s, (uint32_t)seed,
+                                                         (uint32_t)(seed >> 32), S->cols,
+                                                         S->signs, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+    const size_t hist_bytes = (size_t)(r1 + 1) * sizeof(int);
+    if (cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hist_bytes) != cudaSuccess)
+      return fail(SPM_ECUDA);
+    k_chunk_sort<<<(unsigned)nch, 256, hist_bytes, st>>>(n, (int)r1, s, S->cols, S->signs,
+                                                         S->bucket_ptr, S->bucket_ent);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+    k_set_i64<<<1, 1, 0, st>>>(S->bucket_ptr + nch * r1, nnz);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+  }
+  *out = S;
+  return SPM_OK;
+}
+
+int spm_sketch_destroy(spm_sketch* S) {
+  if (!S) return SPM_EINVAL;
+  if (S->cols) cudaFreeAsync(S->cols, S->stream);
+  if (S->signs) cudaFreeAsync(S->signs, S->stream);
+  if (S->bucket_ent) cudaFreeAsync(S->bucket_ent, S->stream);
+  if (S->bucket_ptr) cudaFreeAsync(S->bucket_ptr, S->stream);
+  delete S;
+  return SPM_OK;
+}
+
+int spm_sketch_shape(const spm_sketch* S, int64_t* n, int64_t* r1, int32_t* s, int32_t* kind) {
+  if (!S) return SPM_EINVAL;
+  if (n) *n = S->n;
+  if (r1) *r1 = S->r1;
+  if (s) *s = S->s;
+  if (kind) *kind = S->kind;
+  return SPM_OK;
+}
+
+int spm_sketch_tables(const spm_sketch* S, int32_t* cols, int8_t* signs, int64_t* bucket_ptr,
+                      int32_t* bucket_rows, int8_t* bucket_signs, void* stream) {
+  if (!S) return SPM_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const int64_t nnz = S->n * S->s;
+  if (cols) SPM_CUDA_TRY(cudaMemcpyAsync(cols, S->cols, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  if (signs) SPM_CUDA_TRY(cudaMemcpyAsync(signs, S->signs, nnz, cudaMemcpyDeviceToDevice, st));
+  if (bucket_ptr || bucket_rows || bucket_signs) {
+    Arena ar(st);
+    const int nch = (int)nchunks_of(S->n);
+    const int r1 = (int)S->r1;
+    SPM_ALLOC(ar, int64_t, cnt, r1);
+    SPM_ALLOC(ar, int64_t, bptr, r1 + 1);
+    k_bucket_counts<<<(unsigned)cdiv(r1, 256), 256, 0, st>>>(r1, nch, S->bucket_ptr, cnt);
+    SPM_LAUNCH_CHECK();
+    k_exclusive_scan_small<<<1, 1, 0, st>>>(r1, cnt, bptr);
+    SPM_LAUNCH_CHECK();
+    if (bucket_ptr)
+      SPM_CUDA_TRY(cudaMemcpyAsync(bucket_ptr, bptr, (r1 + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    if (bucket_rows || bucket_signs) {
+      k_bucket_fill<<<(unsigned)cdiv(r1, 128), 128, 0, st>>>(r1, nch, S->bucket_ptr, S->bucket_ent,
+                                                              bptr, bucket_rows, bucket_signs);
+      SPM_LAUNCH_CHECK();
+    }
+  }
+  return SPM_OK;
+}
+
+int spm_gaussian(void* out, int32_t dtype, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                 void* stream) {
+  if (!out || rows < 1 || cols < 1 || ld < cols) return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  return gaussian_dev(out, dtype == SPM_F64 ? DT_F64 : DT_F32, rows, cols, ld, seed,
+                      as_stream(stream));
+}
+
+int spm_sketch_apply(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                     void* out, int64_t ldo, void* stream) {
+  if (!S || !A || !out || m < 1 || lda < S->n || ldo < S->r1) return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  const int dt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  return sketch_apply_dev(S, A, dt, m, lda, out, dt, ldo, nullptr, as_stream(stream));
+}
+
+int spm_sketch_apply_t(const spm_sketch* S, const void* X, int32_t dtype, int64_t p, int64_t ldx,
+                       void* out, int64_t ldo, void* stream) {
+  if (!S || !X || !out || p < 1 || ldx < p || ldo < p) return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  const int dt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  return sketch_apply_t_dev(S, X, dt, p, ldx, out, dt, ldo, as_stream(stream));
+}
+
+}  // extern "C"

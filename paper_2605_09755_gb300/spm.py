@@ -1,0 +1,263 @@
+"""Thin Python binding of libspm (C ABI in include/spm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device buffers are torch CUDA tensors; the current torch stream is passed to
+each call.  There is no CPU fallback: if libspm.so is missing or no sm_103
+device is present, calls raise.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+F32, F64 = 0, 1
+SPARSE_SIGN, IDENTITY = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+STAGES = ("sketch", "apply", "power", "orth", "project", "small", "finish", "other")
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+           4: "Cholesky breakdown", 5: "non-finite value", 6: "device wait timed out",
+           7: "unsupported"}
+
+
+class SpmError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {_STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reorth", ctypes.c_int32),
+                ("final_passes", ctypes.c_int32), ("small_fp64", ctypes.c_int32),
+                ("omega", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("want_timing", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("device_status", ctypes.c_int32), ("cholqr_passes", ctypes.c_int32),
+                ("resid_est", ctypes.c_double), ("fro_a", ctypes.c_double),
+                ("stage_ms", ctypes.c_float * 8)]
+
+    def as_dict(self):
+        return {"device_status": self.device_status, "cholqr_passes": self.cholqr_passes,
+                "resid_est": self.resid_est, "fro_a": self.fro_a,
+                "stage_ms": {k: float(v) for k, v in zip(STAGES, self.stage_ms)}}
+
+
+_LIB = None
+I64, I32, U64, VP = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p
+
+_SIGS = {
+    "spm_version": ([], I32),
+    "spm_status_string": ([I32], ctypes.c_char_p),
+    "spm_device_ok": ([], I32),
+    "spm_sketch_create": ([ctypes.POINTER(VP), I64, I64, I32, U64, I32, VP], I32),
+    "spm_sketch_destroy": ([VP], I32),
+    "spm_sketch_shape": ([VP, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                          ctypes.POINTER(I32)], I32),
+    "spm_sketch_tables": ([VP, VP, VP, VP, VP, VP, VP], I32),
+    "spm_gaussian": ([VP, I32, I64, I64, I64, U64, VP], I32),
+    "spm_sketch_apply": ([VP, VP, I32, I64, I64, VP, I64, VP], I32),
+    "spm_sketch_apply_t": ([VP, VP, I32, I64, I64, VP, I64, VP], I32),
+    "spm_range_finder": ([VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64,
+                          ctypes.POINTER(Info), VP], I32),
+    "spm_rsvd": ([VP, VP, I32, I64, I64, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64, VP,
+                  VP, I64, ctypes.POINTER(Info), VP], I32),
+    "spm_lowrank": ([VP, VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64, VP,
+                     I64, ctypes.POINTER(Info), VP], I32),
+    "spm_gemm_bf16": ([I64, I64, I64, I32, ctypes.POINTER(VP), I64, I32, ctypes.POINTER(VP), I64,
+                       I32, VP, I64, I32, VP], I32),
+    "spm_nystrom": ([VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64, VP, I64,
+                     ctypes.POINTER(Info), VP], I32),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libspm.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libspm.so not built at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SpmError(rc, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dt(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("only float32 / float64 matrices")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("device (CUDA) tensors required")
+        if t.dim() == 2 and t.stride(1) != 1:
+            raise ValueError("row-major (last-dim contiguous) matrices required")
+
+
+class Sketch:
+    """Device tables of one sparse sign sketch S in R^{n x r1} (or the identity)."""
+
+    def __init__(self, n, r1, s=8, seed=42, kind=SPARSE_SIGN):
+        h = ctypes.c_void_p()
+        _check(lib().spm_sketch_create(ctypes.byref(h), int(n), int(r1), int(s), int(seed),
+                                       int(kind), _stream()), "spm_sketch_create")
+        self.handle = h
+        self.n, self.r1, self.s, self.seed, self.kind = int(n), int(r1), int(s), int(seed), kind
+
+    def close(self):
+        if self.handle:
+            lib().spm_sketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tables(self):
+        """Draw-order (cols, signs) and column buckets (ptr, rows, signs) as device tensors."""
+        dev = torch.device("cuda")
+        nnz = self.n * (self.s if self.kind == SPARSE_SIGN else 1)
+        cols = torch.empty(nnz, dtype=torch.int32, device=dev)
+        signs = torch.empty(nnz, dtype=torch.int8, device=dev)
+        bptr = torch.empty(self.r1 + 1, dtype=torch.int64, device=dev)
+        brows = torch.empty(nnz, dtype=torch.int32, device=dev)
+        bsg = torch.empty(nnz, dtype=torch.int8, device=dev)
+        _check(lib().spm_sketch_tables(self.handle, _ptr(cols), _ptr(signs), _ptr(bptr),
+                                       _ptr(brows), _ptr(bsg), _stream()), "spm_sketch_tables")
+        return cols, signs, bptr, brows, bsg
+
+
+def gaussian(rows, cols, seed, dtype=torch.float64):
+    out = torch.empty(rows, cols, dtype=dtype, device="cuda")
+    _check(lib().spm_gaussian(_ptr(out), _dt(out), rows, cols, cols, int(seed), _stream()),
+           "spm_gaussian")
+    return out
+
+
+def sketch_apply(S, A):
+    _require_cuda(A)
+    out = torch.empty(A.shape[0], S.r1, dtype=A.dtype, device=A.device)
+    _check(lib().spm_sketch_apply(S.handle, _ptr(A), _dt(A), A.shape[0], A.stride(0), _ptr(out),
+                                  out.stride(0), _stream()), "spm_sketch_apply")
+    return out
+
+
+def sketch_apply_t(S, X):
+    _require_cuda(X)
+    out = torch.empty(S.r1, X.shape[1], dtype=X.dtype, device=X.device)
+    _check(lib().spm_sketch_apply_t(S.handle, _ptr(X), _dt(X), X.shape[1], X.stride(0), _ptr(out),
+                                    out.stride(0), _stream()), "spm_sketch_apply_t")
+    return out
+
+
+def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False, omega=None):
+    o = Opts(int(precision), int(bool(reorth)), int(final_passes), int(bool(small_fp64)), None)
+    if omega is not None:
+        o.omega = omega.data_ptr()
+    return o
+
+
+def _info(timing):
+    inf = Info()
+    inf.want_timing = 1 if timing else 0
+    return inf
+
+
+def range_finder(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    _require_cuda(A)
+    o = make_opts(precision, **kw)
+    Q = torch.empty(A.shape[0], r2, dtype=A.dtype, device=A.device)
+    inf = _info(timing)
+    _check(lib().spm_range_finder(S.handle, _ptr(A), _dt(A), A.shape[0], A.stride(0), r2, q,
+                                  int(omega_seed), ctypes.byref(o), _ptr(Q), Q.stride(0),
+                                  ctypes.byref(inf), _stream()), "spm_range_finder")
+    return Q, inf.as_dict()
+
+
+def rsvd(S, A, r2, q, k, omega_seed=43, precision=PREC_FP64, timing=False, out=None, info=True,
+         **kw):
+    """Randomized SVD on the sketch-powered range finder: (U, sigma, Vt, info)."""
+    _require_cuda(A)
+    o = make_opts(precision, **kw)
+    m, n = A.shape
+    if out is None:
+        U = torch.empty(m, k, dtype=A.dtype, device=A.device)
+        sig = torch.empty(k, dtype=A.dtype, device=A.device)
+        Vt = torch.empty(k, n, dtype=A.dtype, device=A.device)
+    else:
+        U, sig, Vt = out
+    inf = _info(timing) if info else None
+    rc = lib().spm_rsvd(S.handle, _ptr(A), _dt(A), m, A.stride(0), r2, q, int(omega_seed), k,
+                        ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sig), _ptr(Vt), Vt.stride(0),
+                        ctypes.byref(inf) if inf is not None else None, _stream())
+    _check(rc, "spm_rsvd")
+    return U, sig, Vt, (inf.as_dict() if inf is not None else None)
+
+
+def lowrank(S1, S2, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    _require_cuda(A)
+    o = make_opts(precision, **kw)
+    m, n = A.shape
+    Y = torch.empty(m, r2, dtype=A.dtype, device=A.device)
+    X = torch.empty(r2, n, dtype=A.dtype, device=A.device)
+    inf = _info(timing)
+    _check(lib().spm_lowrank(S1.handle, S2.handle, _ptr(A), _dt(A), m, A.stride(0), r2, q,
+                             int(omega_seed), ctypes.byref(o), _ptr(Y), Y.stride(0), _ptr(X),
+                             X.stride(0), ctypes.byref(inf), _stream()), "spm_lowrank")
+    return Y, X, inf.as_dict()
+
+
+def nystrom(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    _require_cuda(A)
+    o = make_opts(precision, **kw)
+    n = A.shape[0]
+    Cm = torch.empty(n, r2, dtype=A.dtype, device=A.device)
+    W = torch.empty(r2, r2, dtype=A.dtype, device=A.device)
+    inf = _info(timing)
+    _check(lib().spm_nystrom(S.handle, _ptr(A), _dt(A), n, A.stride(0), r2, q, int(omega_seed),
+                             ctypes.byref(o), _ptr(Cm), Cm.stride(0), _ptr(W), W.stride(0),
+                             ctypes.byref(inf), _stream()), "spm_nystrom")
+    return Cm, W, inf.as_dict()
+
+
+def gemm_bf16(A_list, B_list, M, N, K, a_mn=False, b_mn=False, splitk=1):
+    """D (M x N, fp32) = sum_q A_q B_q^T with bf16 operand tensors (see spm.h)."""
+    npass = len(A_list)
+    D = torch.empty(M, N, dtype=torch.float32, device="cuda")
+    Ap = (VP * npass)(*[a.data_ptr() for a in A_list])
+    Bp = (VP * npass)(*[b.data_ptr() for b in B_list])
+    _check(lib().spm_gemm_bf16(M, N, K, npass, Ap, A_list[0].stride(0), int(a_mn), Bp,
+                               B_list[0].stride(0), int(b_mn), _ptr(D), D.stride(0), int(splitk),
+                               _stream()), "spm_gemm_bf16")
+    return D

@@ -1,0 +1,58 @@
+"""The C ABI library builds, loads and exports every symbol declared in include/spm.h (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "spm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libspm():
+    from paper_2605_09755_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["spm_sketch_create", "spm_sketch_destroy", "spm_sketch_apply", "spm_sketch_apply_t",
+                 "spm_gaussian", "spm_range_finder", "spm_rsvd", "spm_lowrank", "spm_nystrom",
+                 "spm_gemm_bf16"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(libspm):
+    missing = [s for s in declared_symbols() if not hasattr(libspm, s)]
+    assert not missing, missing
+
+
+def test_host_only_calls(libspm):
+    libspm.spm_version.restype = ctypes.c_int
+    assert libspm.spm_version() >= 100
+    libspm.spm_status_string.restype = ctypes.c_char_p
+    assert libspm.spm_status_string(1) == b"invalid argument"
+    # argument checking happens before any device work
+    h = ctypes.c_void_p()
+    f = libspm.spm_sketch_create
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                  ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p]
+    assert f(ctypes.byref(h), 100, 10, 11, 1, 0, None) == 1      # s > r1
+    assert f(ctypes.byref(h), 0, 10, 1, 1, 0, None) == 1         # n < 1
+    assert f(ctypes.byref(h), 100, 50, 1, 1, 1, None) == 1       # identity needs r1 == n
+    assert f(None, 100, 10, 1, 1, 0, None) == 1
+
+
+def test_binding_has_no_cpu_path():
+    src = open(os.path.join(ROOT, "paper_2605_09755_gb300", "spm.py")).read()
+    assert "oracle" not in src
+    for f in os.listdir(os.path.join(ROOT, "paper_2605_09755_gb300")):
+        if f.endswith(".py"):
+            assert "import oracle" not in open(os.path.join(ROOT, "paper_2605_09755_gb300", f)).read()

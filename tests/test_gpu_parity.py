@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Inputs come from the shared seeded generators; expected values come from the
+oracle only.  Tolerances:
+  * sketch tables: bit-exact (integer work);
+  * Omega: a few ulp (libm vs CUDA log/sin/cos), |diff| <= 1e-13;
+  * FP64 path: elementwise products <= 1e-12 relative to the operand scale;
+    relative Frobenius residual of the range finder / RandSVD within 1e-10 of
+    the oracle's at the same seed;
+  * mixed path: residual <= 1.01 x the oracle's, top-k singular values within
+    1e-4 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithms as alg
+from oracle import sketch as osk
+from paper_2605_09755_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spm():
+    from paper_2605_09755_gb300 import _build, spm as _spm
+    _build.build()
+    _spm.lib()
+    assert torch.cuda.is_available()
+    return _spm
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+# ------------------------------------------------------------------ a1 sketch tables
+@pytest.mark.parametrize("n,r1,s,seed", [(1000, 100, 8, 42), (1537, 700, 8, 7), (513, 40, 1, 3),
+                                         (64, 64, 64, 5), (16384, 2000, 8, 42), (3, 2, 2, 9)])
+def test_sketch_tables_bit_exact(spm, n, r1, s, seed):
+    S = spm.Sketch(n, r1, s, seed)
+    cols, signs, bptr, brows, bsg = (t.cpu().numpy() for t in S.tables())
+    So = osk.Sketch(n, r1, s, seed)
+    assert np.array_equal(cols.reshape(n, s), So.cols)
+    assert np.array_equal(signs.reshape(n, s).astype(np.int64), So.signs)
+    ptr, rows, sg = So.buckets()
+    assert np.array_equal(bptr, ptr)
+    assert np.array_equal(brows, rows)
+    assert np.array_equal(bsg.astype(np.int64), sg)
+
+
+def test_identity_sketch_tables(spm):
+    S = spm.Sketch(700, 700, 1, 0, kind=spm.IDENTITY)
+    cols, signs, bptr, brows, bsg = (t.cpu().numpy() for t in S.tables())
+    assert np.array_equal(cols, np.arange(700)) and np.all(signs == 1)
+    assert np.array_equal(bptr, np.arange(701)) and np.array_equal(brows, np.arange(700))
+
+
+# ------------------------------------------------------------------ a2 Omega
+@pytest.mark.parametrize("rows,cols", [(100, 50), (7, 3), (2000, 1000)])
+def test_gaussian_matches_oracle(spm, rows, cols):
+    g = host(spm.gaussian(rows, cols, 43, torch.float64))
+    o = osk.gaussian(rows, cols, 43)
+    assert np.max(np.abs(g - o)) <= 1e-13
+    g32 = spm.gaussian(rows, cols, 43, torch.float32).cpu().numpy()
+    assert np.array_equal(g32, o.astype(np.float32)) or np.max(np.abs(g32 - o)) < 1e-6
+
+
+# ------------------------------------------------------------------ a3 A S and S^T X
+@pytest.mark.parametrize("m,n,r1,s", [(100, 1100, 700, 8), (33, 513, 1025, 3), (1, 5, 4, 2),
+                                      (257, 2048, 2000, 8)])
+def test_sketch_apply_parity(spm, m, n, r1, s):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    So = osk.Sketch(n, r1, s, 42)
+    ref = osk.apply_right(A, So)
+    S = spm.Sketch(n, r1, s, 42)
+    out64 = host(spm.sketch_apply(S, dev(A)))
+    scale = np.sqrt(s) * np.abs(A).max()
+    assert np.max(np.abs(out64 - ref)) <= 1e-13 * scale
+    out32 = host(spm.sketch_apply(S, dev(A, torch.float32)))
+    assert np.max(np.abs(out32 - ref)) <= 1e-5 * scale
+    X = rng.standard_normal((n, 37))
+    refT = osk.apply_left_t(So, X)
+    outT = host(spm.sketch_apply_t(S, dev(X)))
+    assert np.max(np.abs(outT - refT)) <= 1e-13 * np.sqrt(s) * np.abs(X).max() * n / r1 * 4
+
+
+def test_sketch_apply_identity_is_copy(spm):
+    A = np.random.default_rng(1).standard_normal((70, 600))
+    S = spm.Sketch(600, 600, 1, 0, kind=spm.IDENTITY)
+    assert np.array_equal(host(spm.sketch_apply(S, dev(A))), A)
+
+
+# ------------------------------------------------------------------ tcgen05 product
+@pytest.mark.parametrize("a_mn,b_mn", [(False, False), (False, True), (True, False), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(300, 200, 500), (128, 256, 64), (1000, 77, 130)])
+def test_gemm_bf16_layouts(spm, a_mn, b_mn, M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M * N + K)
+    Am = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    Bm = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    ref = Am.double() @ Bm.double().T
+    Ast = Am.t().contiguous() if a_mn else Am.contiguous()
+    Bst = Bm.t().contiguous() if b_mn else Bm.contiguous()
+    # the ABI wants leading dimensions that are multiples of 8
+    def pad(t):
+        c = t.shape[1]
+        cp = (c + 7) // 8 * 8
+        out = torch.zeros(t.shape[0], cp, dtype=t.dtype, device=t.device)
+        out[:, :c] = t
+        return out
+    D = spm.gemm_bf16([pad(Ast)], [pad(Bst)], M, N, K, a_mn=a_mn, b_mn=b_mn)
+    err = (D.double() - ref).abs().max().item()
+    assert err <= 1e-4 * (K ** 0.5) * 4, err
+    D2 = spm.gemm_bf16([pad(Ast)], [pad(Bst)], M, N, K, a_mn=a_mn, b_mn=b_mn, splitk=3)
+    assert (D2.double() - ref).abs().max().item() <= 1e-4 * (K ** 0.5) * 4
+
+
+def test_gemm_bf16_split_precision(spm):
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn(700, 300, device="cuda", generator=g, dtype=torch.float64)
+    Y = torch.randn(150, 300, device="cuda", generator=g, dtype=torch.float64)
+    def split(t):
+        hi = t.float().to(torch.bfloat16)
+        lo = (t.float() - hi.float()).to(torch.bfloat16)
+        return hi.contiguous(), lo.contiguous()
+    xh, xl = split(X)
+    yh, yl = split(Y)
+    D = spm.gemm_bf16([xh, xh, xl], [yh, yl, yh], 700, 150, 300)
+    ref = X @ Y.T
+    rel = ((D.double() - ref).abs().max() / ref.abs().max()).item()
+    assert rel < 2e-5, rel
+
+
+# ------------------------------------------------------------------ Algorithm 1 / RandSVD, FP64
+def _oracle_rsvd(A, n, r1, s, r2, q, k, sseed=42, oseed=43, kind=osk.SPARSE_SIGN):
+    So = osk.Sketch(n, r1, s, sseed, kind=kind)
+    Om = osk.gaussian(r1, r2, oseed)
+    return alg.rsvd(A, So, Om, q, k)
+
+
+@pytest.mark.parametrize("m,n,r1,r2,q,s", [(2000, 1000, 100, 50, 2, 8), (777, 513, 130, 40, 1, 4),
+                                           (300, 200, 60, 60, 0, 8), (129, 65, 65, 33, 3, 1)])
+def test_rsvd_fp64_parity(spm, m, n, r1, r2, q, s):
+    A, sigma = wl.plain_fp64(m, n, seed=1001)
+    k = r2
+    U_o, s_o, Vt_o, Q_o = _oracle_rsvd(A, n, r1, s, r2, q, k)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(n, r1, s, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A), r2, q, k, omega_seed=43, precision=spm.PREC_FP64)
+    U, sg, Vt = host(U), host(sg), host(Vt)
+    res = np.linalg.norm(A - (U * sg) @ Vt)
+    opt = alg.optimal_fro(sigma, k)
+    assert abs(res / opt - res_o / opt) <= 1e-10 * (res_o / opt)
+    assert np.max(np.abs(sg - s_o) / s_o) <= 1e-10
+    assert np.linalg.norm(U.T @ U - np.eye(k)) <= 1e-12
+    # singular vectors agree up to the shared sign convention where the gaps allow
+    gap = np.min(np.abs(np.diff(s_o))) / s_o[0]
+    if gap > 1e-6:
+        assert np.max(np.abs(U - U_o)) <= 1e-7
+    assert info["device_status"] == 0
+
+
+def test_range_finder_fp64_identity_sketch_is_classical(spm):
+    """S = I: the CUDA path reproduces the classical range finder of the oracle."""
+    A, sigma = wl.plain_fp64(400, 200, seed=3)
+    So = osk.Sketch(200, 200, 1, 0, kind=osk.IDENTITY)
+    Q_o = alg.range_finder(A, So, osk.gaussian(200, 20, 43), q=3)
+    S = spm.Sketch(200, 200, 1, 0, kind=spm.IDENTITY)
+    Q, info = spm.range_finder(S, dev(A), 20, 3, omega_seed=43)
+    Q = host(Q)
+    assert np.linalg.norm(Q @ Q.T - Q_o @ Q_o.T) <= 1e-9
+    assert abs(alg.residual_fro(A, Q) / alg.residual_fro(A, Q_o) - 1) <= 1e-10
+
+
+def test_range_finder_caller_omega(spm):
+    A, _ = wl.plain_fp64(300, 150, seed=4)
+    Om = np.random.default_rng(2).standard_normal((50, 10))
+    Q_o = alg.range_finder(A, osk.Sketch(150, 50, 8, 42), Om, q=2)
+    S = spm.Sketch(150, 50, 8, 42)
+    Q, _ = spm.range_finder(S, dev(A), 10, 2, omega=dev(Om))
+    Q = host(Q)
+    assert np.linalg.norm(Q @ Q.T - Q_o @ Q_o.T) <= 1e-9
+
+
+def test_range_finder_exact_low_rank(spm):
+    A, _ = wl.dense_lowrank(500, 300, np.array([5.0, 4.0, 3.0, 2.0, 1.0]), seed=8)
+    S = spm.Sketch(300, 40, 8, 42)
+    for prec, dt, tol in [(spm.PREC_FP64, torch.float64, 1e-12), (spm.PREC_MIXED, torch.float32, 1e-4)]:
+        Q, _ = spm.range_finder(S, dev(A, dt), 10, 1, precision=prec)
+        assert alg.residual_fro(A, host(Q)) <= tol * np.linalg.norm(A)
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("m,n,r1,r2,q", [(4096, 2048, 256, 128, 2), (3000, 1500, 300, 100, 0),
+                                         (2000, 1000, 100, 50, 2)])
+def test_rsvd_mixed_parity(spm, m, n, r1, r2, q):
+    if m == 2000:
+        A, sigma = wl.plain_fp64(m, n, seed=1001)
+    else:
+        A, sigma = wl.noisy_exp_numpy(m, n, seed=1002, noise=1e-3 / np.sqrt(n))
+    k = r2
+    U_o, s_o, Vt_o, _ = _oracle_rsvd(A, n, r1, 8, r2, q, k)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(n, r1, 8, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A, torch.float32), r2, q, k, precision=spm.PREC_MIXED)
+    U, sg, Vt = host(U), host(sg), host(Vt)
+    res = np.linalg.norm(A - (U * sg) @ Vt)
+    assert res <= 1.01 * res_o, (res, res_o)
+    assert np.max(np.abs(sg - s_o) / s_o) <= 1e-4, np.max(np.abs(sg - s_o) / s_o)
+    assert np.linalg.norm(U.T @ U - np.eye(k)) <= 1e-3
+    assert info["device_status"] == 0
+
+
+def test_rsvd_mixed_small_fp64_option(spm):
+    A, sigma = wl.plain_fp64(1500, 700, seed=11)
+    U_o, s_o, Vt_o, _ = _oracle_rsvd(A, 700, 120, 8, 40, 2, 40)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(700, 120, 8, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A, torch.float32), 40, 2, 40, precision=spm.PREC_MIXED,
+                               small_fp64=True)
+    res = np.linalg.norm(A - (host(U) * host(sg)) @ host(Vt))
+    assert res <= 1.01 * res_o
+    assert np.max(np.abs(host(sg) - s_o) / s_o) <= 1e-4
+
+
+# ------------------------------------------------------------------ Algorithm 2
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lowrank_parity(spm, prec):
+    m, n, r1, r2, q = 900, 600, 120, 30, 2
+    A, sigma = wl.plain_fp64(m, n, seed=21)
+    S1o, S2o = osk.Sketch(n, r1, 8, 42), osk.Sketch(m, r1, 8, 44)
+    Y_o, X_o = alg.lowrank(A, S1o, S2o, osk.gaussian(r1, r2, 43), q)
+    ref = Y_o @ X_o
+    S1, S2 = spm.Sketch(n, r1, 8, 42), spm.Sketch(m, r1, 8, 44)
+    if prec == "fp64":
+        Y, X, _ = spm.lowrank(S1, S2, dev(A), r2, q)
+        assert np.linalg.norm(host(Y) @ host(X) - ref) <= 1e-9 * np.linalg.norm(A)
+    else:
+        Y, X, _ = spm.lowrank(S1, S2, dev(A, torch.float32), r2, q, precision=spm.PREC_MIXED)
+        e = np.linalg.norm(A - host(Y) @ host(X))
+        assert e <= 1.01 * np.linalg.norm(A - ref)
+
+
+# ------------------------------------------------------------------ Algorithm 3
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_nystrom_parity(spm, prec):
+    K, h, X = wl.gmm_kernel(800, seed=1004)
+    r1, r2, q = 200, 50, 1
+    So = osk.Sketch(800, r1, 8, 42)
+    C_o, W_o = alg.nystrom(K, So, osk.gaussian(r1, r2, 43), q)
+    Ah_o = alg.nystrom_apply(C_o, W_o)
+    S = spm.Sketch(800, r1, 8, 42)
+    if prec == "fp64":
+        Cm, W, _ = spm.nystrom(S, dev(K), r2, q)
+        Ah = alg.nystrom_apply(host(Cm), host(W))
+        assert np.linalg.norm(Ah - Ah_o) <= 1e-8 * np.linalg.norm(K)
+    else:
+        Cm, W, _ = spm.nystrom(S, dev(K, torch.float32), r2, q, precision=spm.PREC_MIXED)
+        Ah = alg.nystrom_apply(host(Cm), host(W))
+        assert np.linalg.norm(K - Ah) <= 1.01 * np.linalg.norm(K - Ah_o)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_invalid_arguments_are_rejected(spm):
+    A = torch.zeros(10, 20, device="cuda", dtype=torch.float64)
+    S = spm.Sketch(20, 8, 2, 1)
+    with pytest.raises(spm.SpmError):
+        spm.range_finder(S, A, 9, 1)          # r2 > r1
+    with pytest.raises(spm.SpmError):
+        spm.range_finder(S, A, 11, 1)         # r2 > m
+    with pytest.raises(spm.SpmError):
+        spm.rsvd(S, A, 4, 1, 5)               # k > r2
+    S2 = spm.Sketch(21, 8, 2, 1)
+    with pytest.raises(spm.SpmError):
+        spm.range_finder(S2, A, 4, 1)         # sketch rows != columns of A

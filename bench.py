@@ -1,0 +1,346 @@
+"""Benchmark: time to a rank-k approximation on one GB300 (and the CPU oracle beside it).
+
+Workload (noisy exponential decay): dense A 65536 x 16384 float32,
+sigma_i = exp(-i/200) between Haar factors plus 1e-3 N(0,1) noise, target rank
+k = 1000, sparse sign sketch of size r1 = 2000 with s = 8 non-zeros per row,
+q = 2 power steps.  One step = one full Randomized SVD through the C ABI
+(sketch apply, power iteration, re-orthonormalisation, Q^T A, core SVD,
+U and V^T) in the mixed-precision mode; the sketch tables are built once.
+
+Printed: one JSON line with the metric, the plain-FP64 GPU form's time and
+residual at the same q (the accuracy target), the stage breakdown, the
+roofline of the dominant kernel, an end-to-end number with host buffers, and
+the CPU oracle timed on a bounded row sample.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rank-k approx at fixed rel. residual vs plain FP64 GPU; HBM GB/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=65536)
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--r1", type=int, default=2000)
+    p.add_argument("--k", type=int, default=1000)
+    p.add_argument("--s", type=int, default=8)
+    p.add_argument("--q", type=int, default=2)
+    p.add_argument("--noise", type=float, default=1e-3)
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU reference run")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--final-passes", type=int, default=3)
+    p.add_argument("--power-passes", type=int, default=3)
+    p.add_argument("--cpu-rows", type=int, default=2048)
+    return p.parse_args()
+
+
+def workload_name(a):
+    return (f"dense {a.m}x{a.n} f32, sigma_i=exp(-i/200) + {a.noise:g}*N(0,1) noise, "
+            f"k={a.k}, sketch r1={a.r1} s={a.s}, q={a.q}, RandSVD")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", os.environ.get("LOCAL_RANK", "0"), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if sm:
+            busy = [v for v in sm if v > 0.5 * max(sm)] or sm
+            out = {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def cpu_oracle_ms(A_rows, a, seed_s=42, seed_o=43):
+    """Oracle Randomized SVD on a row sample; returns (ms for the sample, scale factor)."""
+    from oracle import algorithms as alg
+    from oracle import sketch as osk
+    n = A_rows.shape[1]
+    So = osk.Sketch(n, a.r1, a.s, seed_s)
+    Om = osk.gaussian(a.r1, a.k, seed_o)
+    t0 = time.perf_counter()
+    alg.rsvd(A_rows, So, Om, a.q, a.k)
+    return (time.perf_counter() - t0) * 1e3
+
+
+def reference_main(a):
+    """--impl reference: the CPU oracle, as it stands, on bounded row samples."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rows = max(a.cpu_rows, a.k)
+    rng = np.random.default_rng(7)
+    # a row sample of the same workload family, generated on the host
+    from paper_2605_09755_gb300 import workloads as wl
+    A, _ = wl.noisy_exp_numpy(rows, a.n, seed=1002, noise=a.noise)
+    scale = a.m / rows
+    for _ in range(a.warmup):
+        cpu_oracle_ms(A, a)
+    times = [cpu_oracle_ms(A, a) for _ in range(a.steps)]
+    v = statistics.mean(times) * scale
+    del rng
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{rows} of {a.m} rows, time scaled by {scale:g}"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def residual(A, U, sg, Vt, chunk=4096):
+    import torch
+    tot = 0.0
+    Vs = (Vt.float() * 1.0)
+    Us = U.float() * sg.float()
+    for i in range(0, A.shape[0], chunk):
+        R = A[i:i + chunk] - Us[i:i + chunk] @ Vs
+        tot += float((R.double() ** 2).sum())
+    return tot ** 0.5
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_main(a)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import workloads as wl
+    _build.build()
+    spm.lib()
+
+    m, n, r1, k = a.m, a.n, a.r1, a.k
+    A, sigma = wl.noisy_exp_torch(m, n, seed=1002 + rank * 0, noise=a.noise)
+    torch.cuda.synchronize()
+    S = spm.Sketch(n, r1, a.s, seed=42)
+    U = torch.empty(m, k, device="cuda")
+    sg = torch.empty(k, device="cuda")
+    Vt = torch.empty(k, n, device="cuda")
+    out = (U, sg, Vt)
+    mixed = dict(precision=spm.PREC_MIXED, final_passes=a.final_passes,
+                 power_passes=a.power_passes)
+
+    def step(info=False, timing=False):
+        return spm.rsvd(S, A, k, a.q, k, omega_seed=43, out=out, info=info, timing=timing, **mixed)
+
+    # plain FP64 GPU form at the same q: the accuracy target (run once, untimed loop)
+    fp64 = {}
+    if not a.no_fp64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U64, s64, V64, inf64 = spm.rsvd(S, A, k, a.q, k, omega_seed=43, precision=spm.PREC_FP64,
+                                        timing=True)
+        torch.cuda.synchronize()
+        fp64 = {"ms": (time.perf_counter() - t0) * 1e3,
+                "residual": residual(A, U64, s64, V64),
+                "stage_ms": inf64["stage_ms"]}
+        del U64, s64, V64
+        torch.cuda.empty_cache()
+
+    # warm-up, then the timed region (inputs are 4.3 GB >> 129 MB L2, no flush needed)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(a.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = ms_total / (a.steps * world)   # ms per rank-k approximation, whole job
+
+    # stage breakdown (events recorded by the library on the launching stream)
+    _, _, _, inf = step(info=True, timing=True)
+    stages = inf["stage_ms"]
+    res_mixed = residual(A, U, sg, Vt)
+    launches = None
+    try:
+        lib = spm.lib()
+        c0 = lib.spm_launch_count()
+        step()
+        torch.cuda.synchronize()
+        launches = int(lib.spm_launch_count() - c0) * a.steps
+    except Exception:
+        pass
+
+    # roofline of the dominant kernel: the split-precision projection B = Q^T A
+    # (3 BF16 passes of 2 m n k flops) or the sketch apply (HBM) if that dominates
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    proj_ms = stages.get("project", 0.0)
+    apply_ms = stages.get("apply", 0.0)
+    proj_flops = a.final_passes * 2.0 * m * n * k
+    apply_bytes = 4.0 * m * n + 2.0 * m * r1
+    if proj_ms >= apply_ms:
+        ach = proj_flops / (proj_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_gemm_tc (B = Q^T A, %d BF16 passes)" % a.final_passes,
+                "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": ach / bf16_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    else:
+        ach = apply_bytes / (apply_ms * 1e-3) / 1e9
+        roof = {"kernel": "k_sketch_apply", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    sketch_roof = {"achieved_gbs": apply_bytes / (apply_ms * 1e-3) / 1e9 if apply_ms else None,
+                   "frac": (apply_bytes / (apply_ms * 1e-3) / 1e9) / hbm_peak if apply_ms else None}
+
+    # end to end through the public call with host buffers
+    e2e = None
+    if not a.no_e2e:
+        Ah = A.cpu().pin_memory()
+        Uh = torch.empty(m, k).pin_memory()
+        sh = torch.empty(k).pin_memory()
+        Vh = torch.empty(k, n).pin_memory()
+        def e2e_step():
+            A.copy_(Ah, non_blocking=True)
+            step()
+            Uh.copy_(U, non_blocking=True)
+            sh.copy_(sg, non_blocking=True)
+            Vh.copy_(Vt, non_blocking=True)
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e = {"value": e0.elapsed_time(e1) / a.steps, "unit": "ms",
+               "h2d_bytes_per_step": int(Ah.numel() * 4),
+               "d2h_bytes_per_step": int((Uh.numel() + sh.numel() + Vh.numel()) * 4)}
+        del Ah
+
+    cpu = None
+    if not a.no_cpu and rank == 0 and world == 1:
+        rows = max(a.cpu_rows, k)
+        Ar = A[:rows].double().cpu().numpy()
+        cpu_oracle_ms(Ar[:min(rows, 1024)], argparse.Namespace(**{**vars(a), "k": min(k, 256),
+                                                                 "r1": min(r1, 512)}))
+        t = cpu_oracle_ms(Ar, a)
+        cpu = {"value": t * a.m / rows, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle RandSVD on the first {rows} of {a.m} rows (same n, r1, k, q), "
+                         f"time scaled by {a.m / rows:g}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32",
+            "data": "synthetic (seeded, generated on device)",
+            "config": {"workload": workload_name(a), "precision": "mixed",
+                       "final_passes": a.final_passes, "power_passes": a.power_passes, "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs (4.3 GB) larger than L2; no flush"},
+            "accuracy": {"residual_mixed": res_mixed, "residual_fp64": fp64.get("residual"),
+                         "ratio": (res_mixed / fp64["residual"]) if fp64 else None,
+                         "fro_a": inf["fro_a"], "resid_est": inf["resid_est"]},
+            "fp64_gpu_ms": fp64.get("ms"), "fp64_stage_ms": fp64.get("stage_ms"),
+            "speedup_vs_fp64_gpu": (fp64["ms"] / value) if fp64 else None,
+            "stage_ms": stages, "sketch_apply": sketch_roof,
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

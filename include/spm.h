@@ -82,6 +82,10 @@ typedef struct spm_opts {
   int32_t final_passes; /* MIXED only: BF16 passes for the final projection Q^T A: 1 or 3
                            (hi*hi + hi*lo + lo*hi); 0 selects the default 3                 */
   int32_t small_fp64;   /* MIXED only: 1 = FP64 Cholesky / eigensolver, 0 (default) = FP32   */
+  int32_t power_passes; /* MIXED only: BF16 passes of the power products A~ Z, A~^T Y: 1
+                           (plain BF16, fastest) or 3 (hi/lo split, FP32-level subspace);
+                           0 selects the default 3                                        */
+  int32_t reserved;
   const void* omega;    /* optional caller-supplied Omega: device, r1 x r2 row-major, ld r2,
                            dtype of A.  NULL: generated from omega_seed (a2).               */
 } spm_opts;
@@ -106,6 +110,9 @@ int spm_version(void);
 const char* spm_status_string(int status);
 /* 1 if the current CUDA device is sm_103 and the kernels loaded, else 0. */
 int spm_device_ok(void);
+/* Number of kernels this library has launched in the process so far (host-side
+ * counter, all threads).  Used to report launches per step. */
+uint64_t spm_launch_count(void);
 
 /* ---- a1: sketch generation ---------------------------------------------
  * Lemma 3.2 item 2 (CountSketch-type S in R^{n x r1}, s non-zeros of the form

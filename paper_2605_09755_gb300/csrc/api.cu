@@ -18,6 +18,8 @@
 
 namespace spm {
 
+std::atomic<unsigned long long> g_launches{0};
+
 struct Call {
   cudaStream_t st;
   Arena ar;
@@ -25,6 +27,7 @@ struct Call {
   int adt = DT_F64;
   bool small64 = false;
   int final_passes = 3;
+  int power_passes = 3;
   bool reorth = true;
   const void* omega = nullptr;
   int* status = nullptr;
@@ -72,14 +75,16 @@ static int orth_f64(Call& C, double* X, int64_t rows, int64_t c, int64_t ldx, in
   SPM_ALLOC(C.ar, double, G, c * c);
   SPM_ALLOC(C.ar, double, Li, c * c);
   SPM_ALLOC(C.ar, double, Xn, rows * c);
+  SPM_ALLOC(C.ar, int, defl, c);
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F64, ldx)),
                       rowmajor(X, DT_F64, ldx), 0.0, mrowmajor(G, DT_F64, c), C.st));
     if (ps == 0 && passes > 2)
       SPM_TRY(add_trace_shift(c, G, c, DT_F64, shift_coef(true, rows, c), C.st));
-    SPM_TRY(cholesky_inv(c, G, c, Li, c, DT_F64, C.status, C.st));
+    SPM_TRY(cholesky_inv(c, G, c, Li, c, DT_F64, defl, C.status, C.st));
     SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F64, ldx), transpose(rowmajor(Li, DT_F64, c)),
                       0.0, mrowmajor(Xn, DT_F64, c), C.st));
+    SPM_TRY(fill_deflated(rows, c, Xn, c, DT_F64, defl, 0x5EED0000u + ps, C.st));
     SPM_TRY(convert2d(rows, c, rowmajor(Xn, DT_F64, c), mrowmajor(X, DT_F64, ldx), C.st));
   }
   return SPM_OK;
@@ -94,14 +99,16 @@ static int orth_small_f32(Call& C, float* X, int64_t rows, int64_t c, int64_t ld
   void* G = C.ar.alloc<unsigned char>(c * c * es);
   void* Li = C.ar.alloc<unsigned char>(c * c * es);
   float* Xn = C.ar.alloc<float>(rows * c);
-  if (!G || !Li || !Xn) return SPM_ENOMEM;
+  int* defl = C.ar.alloc<int>(c);
+  if (!G || !Li || !Xn || !defl) return SPM_ENOMEM;
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F32, ldx)),
                       rowmajor(X, DT_F32, ldx), 0.0, mrowmajor(G, sdt, c), C.st));
     if (ps == 0 && passes > 2) SPM_TRY(add_trace_shift(c, G, c, sdt, shift_coef(false, rows, c), C.st));
-    SPM_TRY(cholesky_inv(c, G, c, Li, c, sdt, C.status, C.st));
+    SPM_TRY(cholesky_inv(c, G, c, Li, c, sdt, defl, C.status, C.st));
     SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F32, ldx), transpose(rowmajor(Li, sdt, c)), 0.0,
                       mrowmajor(Xn, DT_F32, c), C.st));
+    SPM_TRY(fill_deflated(rows, c, Xn, c, DT_F32, defl, 0x5EED0100u + ps, C.st));
     SPM_TRY(convert2d(rows, c, rowmajor(Xn, DT_F32, c), mrowmajor(X, DT_F32, ldx), C.st));
   }
   return SPM_OK;
@@ -121,6 +128,7 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
   if (!Gs || !Li) return SPM_ENOMEM;
   SPM_ALLOC(C.ar, __nv_bfloat16, Lhi, c * cp);
   SPM_ALLOC(C.ar, __nv_bfloat16, Llo, c * cp);
+  SPM_ALLOC(C.ar, int, defl, c);
   const int passes = 3;
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
@@ -132,12 +140,13 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
     else
       SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F32, c), C.st));
     if (ps == 0) SPM_TRY(add_trace_shift(c, Gs, c, sdt, shift_coef(false, m, c), C.st));
-    SPM_TRY(cholesky_inv(c, Gs, c, Li, c, sdt, C.status, C.st));
+    SPM_TRY(cholesky_inv(c, Gs, c, Li, c, sdt, defl, C.status, C.st));
     // Y <- Y L^{-T}: A-op Y (M = m, K = c) K-major; B-op (N = c, K = c) element
     // (n, k) = Linv[n][k], i.e. Linv row-major is K-major.
     SPM_TRY(split_bf16(c, c, rowmajor(Li, sdt, c), mrowmajor(Lhi, DT_BF16, cp),
                        mrowmajor(Llo, DT_BF16, cp), C.st));
     SPM_TRY(tc_split(m, c, c, Qhi, Qlo, cp, false, Lhi, Llo, cp, false, 3, Y, ldy, 1, C.st));
+    SPM_TRY(fill_deflated(m, c, Y, ldy, DT_F32, defl, 0x5EED0200u + ps, C.st));
     C.cholqr_passes++;
   }
   SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
@@ -207,13 +216,19 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
   }
   // ---------------- mixed precision
   const int64_t r1p = pad8(r1), r2p = pad8(r2);
+  const int pp = C.power_passes;
   SPM_ALLOC(C.ar, __nv_bfloat16, At, m * r1p);
+  __nv_bfloat16* Atlo = nullptr;
+  if (pp > 1) {
+    Atlo = C.ar.alloc<__nv_bfloat16>(m * r1p);
+    if (!Atlo) return SPM_ENOMEM;
+  }
   SPM_ALLOC(C.ar, float, Om32, r1 * r2);
-  SPM_ALLOC(C.ar, __nv_bfloat16, Zb, r1 * r2p);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Zhi, r1 * r2p);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Zlo, r1 * r2p);
   SPM_ALLOC(C.ar, float, Y, m * r2);
-  SPM_ALLOC(C.ar, __nv_bfloat16, Yb, m * r2p);
   SPM_ALLOC(C.ar, float, Z, r1 * r2);
-  SPM_ALLOC(C.ar, __nv_bfloat16, Qhi, m * r2p);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Qhi, m * r2p);   // also the BF16 split of Y between steps
   SPM_ALLOC(C.ar, __nv_bfloat16, Qlo, m * r2p);
   {
     StageScope sc(C.timer, SPM_STAGE_SKETCH);
@@ -221,25 +236,26 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
       SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Om32, DT_F32, r2), C.st));
     else
       SPM_TRY(gaussian_dev(Om32, DT_F32, r1, r2, r2, seed, C.st));
-    SPM_TRY(convert2d(r1, r2, rowmajor(Om32, DT_F32, r2), mrowmajor(Zb, DT_BF16, r2p), C.st));
+    SPM_TRY(split_bf16(r1, r2, rowmajor(Om32, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
+                       mrowmajor(Zlo, DT_BF16, r2p), C.st));
   }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st));
+    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st, Atlo));
   }
-  TcOp opAt_k{At, r1p, false};   // A~ as A-operand, K = r1
-  TcOp opAt_mn{At, r1p, true};   // A~^T as A-operand, K = m
-  TcOp opZ{Zb, r2p, true};       // Z (r1 x r2 row-major) as B-operand, K = r1
-  TcOp opY{Yb, r2p, true};       // Y (m x r2 row-major) as B-operand, K = m
+  const __nv_bfloat16* Alo = Atlo ? Atlo : At;
   {
+    // Y = A~ Omega: A-op A~ (M = m, K = r1) K-major; B-op Omega (N = r2, K = r1) MN-major
     StageScope sc(C.timer, SPM_STAGE_POWER);
-    SPM_TRY(gemm_tc(m, r2, r1, 1, &opAt_k, &opZ, 1.0f, Y, r2, 1, 1, C.st));
+    SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
   }
   for (int t = 0; t < q; ++t) {
     {
+      // Z = A~^T Y: A-op A~^T (M = r1, K = m) MN-major; B-op Y (N = r2, K = m) MN-major
       StageScope sc(C.timer, SPM_STAGE_POWER);
-      SPM_TRY(convert2d(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Yb, DT_BF16, r2p), C.st));
-      SPM_TRY(gemm_tc(r1, r2, m, 1, &opAt_mn, &opY, 1.0f, Z, r2, 1, auto_splitk(r1, r2, m), C.st));
+      SPM_TRY(split_bf16(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Qhi, DT_BF16, r2p),
+                         mrowmajor(Qlo, DT_BF16, r2p), C.st));
+      SPM_TRY(tc_split(r1, r2, m, At, Alo, r1p, true, Qhi, Qlo, r2p, true, pp, Z, r2, 1, C.st));
     }
     if (C.reorth) {
       StageScope sc(C.timer, SPM_STAGE_ORTH);
@@ -247,8 +263,9 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
     }
     {
       StageScope sc(C.timer, SPM_STAGE_POWER);
-      SPM_TRY(convert2d(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zb, DT_BF16, r2p), C.st));
-      SPM_TRY(gemm_tc(m, r2, r1, 1, &opAt_k, &opZ, 1.0f, Y, r2, 1, 1, C.st));
+      SPM_TRY(split_bf16(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
+                         mrowmajor(Zlo, DT_BF16, r2p), C.st));
+      SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
     }
   }
   {
@@ -270,6 +287,7 @@ static int check_common(const spm_sketch* S, const void* A, int32_t dtype, int64
   if (o) {
     if (o->precision != SPM_PREC_FP64 && o->precision != SPM_PREC_MIXED) return SPM_EINVAL;
     if (o->final_passes != 0 && o->final_passes != 1 && o->final_passes != 3) return SPM_EINVAL;
+    if (o->power_passes != 0 && o->power_passes != 1 && o->power_passes != 3) return SPM_EINVAL;
   }
   return SPM_OK;
 }
@@ -280,6 +298,7 @@ static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info
     C.prec = o->precision;
     C.reorth = o->reorth != 0;
     C.final_passes = o->final_passes == 0 ? 3 : o->final_passes;
+    C.power_passes = o->power_passes == 0 ? 3 : o->power_passes;
     C.small64 = o->small_fp64 != 0;
     C.omega = o->omega;
   }
@@ -440,6 +459,8 @@ const char* spm_status_string(int s) {
 
 int spm_device_ok(void) { return tc_available() ? 1 : 0; }
 
+uint64_t spm_launch_count(void) { return (uint64_t)g_launches.load(); }
+
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream) {
@@ -530,7 +551,7 @@ int spm_lowrank(const spm_sketch* S1, const spm_sketch* S2, const void* A, int32
       rc = gemm_simt(r2, r2, r1b, 1.0, transpose(rowmajor(M, wdt, r2)), rowmajor(M, wdt, r2), 0.0,
                      mrowmajor(G, wdt, r2), C.st);
       if (rc) break;
-      rc = cholesky_inv(r2, G, r2, Ls[ps], r2, wdt, C.status, C.st);
+      rc = cholesky_inv(r2, G, r2, Ls[ps], r2, wdt, nullptr, C.status, C.st);
       if (rc) break;
       rc = gemm_simt(r1b, r2, r2, 1.0, rowmajor(M, wdt, r2), transpose(rowmajor(Ls[ps], wdt, r2)),
                      0.0, mrowmajor(Mn, wdt, r2), C.st);

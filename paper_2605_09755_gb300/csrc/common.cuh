@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "../../include/spm.h"
 
 namespace spm {
@@ -38,7 +40,15 @@ __device__ __forceinline__ void set_status(int* st, int code) {
     if (_s != SPM_OK) return _s;    \
   } while (0)
 
-#define SPM_LAUNCH_CHECK() SPM_CUDA_TRY(cudaGetLastError())
+// Host-side count of kernel launches issued by the library (spm_launch_count).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+#define SPM_LAUNCH_CHECK()          \
+  do {                              \
+    ::spm::count_launch();          \
+    SPM_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "rng.cuh"
 
 namespace spm {
 
@@ -110,16 +111,23 @@ static constexpr int CH_NB = 64;
 
 // Factor one diagonal block G_kk = L L^T in shared memory (right-looking), write
 // L (lower, zeros above) back in place and L^{-1} into Linv.
+// Deflation: a pivot at or below tol * max(diag G) means that column is, to
+// working precision, in the span of the earlier ones (the Gram matrix of a
+// rank-deficient basis).  Its L column becomes e_j, defl[j] is set, and the
+// caller replaces that column of the orthonormalised basis by a fresh random
+// direction which the next CholeskyQR pass orthonormalises.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_chol_diag(int b, T* __restrict__ G, int64_t ldg, T* __restrict__ Li, int64_t ldi,
+                const T* __restrict__ maxd, T tol, int* __restrict__ defl,
                 int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char ch_smem[];
   T(*a)[CH_NB + 1] = reinterpret_cast<T(*)[CH_NB + 1]>(ch_smem);
   T(*inv)[CH_NB + 1] = reinterpret_cast<T(*)[CH_NB + 1]>(ch_smem + sizeof(T) * CH_NB * (CH_NB + 1));
-  __shared__ int bad;
+  __shared__ int bad, dj;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
+  const T thr = tol * (*maxd);
   for (int e = tid; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e % b;
     a[i][j] = (j <= i) ? G[(int64_t)i * ldg + j] : (T)0;
@@ -127,21 +135,29 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
-      T d = a[j][j];
-      if (!(d > (T)0) || !isfinite((double)d)) {
+      const T d = a[j][j];
+      int f = 0;
+      if (!isfinite((double)d)) {
         bad = 1;
-        d = (T)1;
+        f = 1;
+      } else if (!(d > thr)) {
+        f = 1;
       }
-      a[j][j] = sqrt(d);
+      dj = f;
+      a[j][j] = f ? (T)1 : sqrt(d);
+      if (defl) defl[j] = f;
     }
     __syncthreads();
     const T djj = a[j][j];
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) a[i][j] /= djj;
+    const int f = dj;
+    for (int i = j + 1 + tid; i < b; i += blockDim.x) a[i][j] = f ? (T)0 : a[i][j] / djj;
     __syncthreads();
     const int rem = b - j - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k <= i) a[i][k] -= a[i][j] * a[k][j];
+    if (!f) {
+      for (int e = tid; e < rem * rem; e += blockDim.x) {
+        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+        if (k <= i) a[i][k] -= a[i][j] * a[k][j];
+      }
     }
     __syncthreads();
   }
@@ -159,7 +175,33 @@ __global__ void __launch_bounds__(256)
     G[(int64_t)i * ldg + j] = (j <= i) ? a[i][j] : (T)0;
     Li[(int64_t)i * ldi + j] = inv[i][j];
   }
-  if (tid == 0 && bad) set_status(status, DEV_BREAKDOWN);
+  if (tid == 0 && bad) set_status(status, DEV_NONFINITE);
+}
+
+template <typename T>
+__global__ void k_maxdiag(int64_t r, const T* __restrict__ G, int64_t ldg, T* __restrict__ out) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, (double)G[i * ldg + i]);
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (T)red[0];
+}
+
+// zero the columns j of P (rows x b) whose defl[j] is set
+template <typename T>
+__global__ void k_zero_defl_cols(int64_t rows, int b, T* __restrict__ P, int64_t ldp,
+                                 const int* __restrict__ defl) {
+  const int64_t total = rows * b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % b);
+    if (defl[j]) P[(e / b) * ldp + j] = (T)0;
+  }
 }
 
 template <typename T>
@@ -182,26 +224,37 @@ __global__ void k_zero2d(int64_t rows, int64_t cols, T* __restrict__ p, int64_t 
 }
 
 template <typename T>
-static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int* status,
-                          cudaStream_t st) {
+static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int* defl,
+                          int* status, cudaStream_t st) {
   const int dt = std::is_same<T, double>::value ? DT_F64 : DT_F32;
+  const T tol = std::is_same<T, double>::value ? (T)1e-12 : (T)1e-6;
   Arena ar(st);
   SPM_ALLOC(ar, T, P, r * CH_NB);
   SPM_ALLOC(ar, T, Tm, r * r);
+  SPM_ALLOC(ar, T, maxd, 1);
+  if (!defl) {
+    defl = ar.alloc<int>(r);
+    if (!defl) return SPM_ENOMEM;
+  }
   k_zero2d<T><<<grid_for(r * r), 256, 0, st>>>(r, r, Li, ldi);
+  SPM_LAUNCH_CHECK();
+  k_maxdiag<T><<<1, 256, 0, st>>>(r, G, ldg, maxd);
   SPM_LAUNCH_CHECK();
   const int smem = (int)(2 * sizeof(T) * CH_NB * (CH_NB + 1));
   SPM_CUDA_TRY(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   for (int64_t kb = 0; kb < r; kb += CH_NB) {
     const int b = (int)min64(CH_NB, r - kb);
-    k_chol_diag<T><<<1, 256, smem, st>>>(b, G + kb * ldg + kb, ldg, Li + kb * ldi + kb, ldi, status);
+    k_chol_diag<T><<<1, 256, smem, st>>>(b, G + kb * ldg + kb, ldg, Li + kb * ldi + kb, ldi, maxd,
+                                         tol, defl + kb, status);
     SPM_LAUNCH_CHECK();
     const int64_t rest = r - kb - b;
     if (rest > 0) {
-      // P = G21 * Linv_kk^T   (rest x b)
+      // P = G21 * Linv_kk^T   (rest x b), deflated columns forced to zero
       View g21 = rowmajor(G + (kb + b) * ldg + kb, dt, ldg);
       View lkT = transpose(rowmajor(Li + kb * ldi + kb, dt, ldi));
       SPM_TRY(gemm_simt(rest, b, b, 1.0, g21, lkT, 0.0, mrowmajor(P, dt, CH_NB), st));
+      k_zero_defl_cols<T><<<grid_for(rest * b), 256, 0, st>>>(rest, b, P, CH_NB, defl + kb);
+      SPM_LAUNCH_CHECK();
       // G22 -= P P^T
       SPM_TRY(gemm_simt(rest, rest, b, -1.0, rowmajor(P, dt, CH_NB),
                         transpose(rowmajor(P, dt, CH_NB)), 1.0,
@@ -223,11 +276,38 @@ static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int*
   return SPM_OK;
 }
 
-int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* status,
-                 cudaStream_t st) {
-  if (dt == DT_F64) return cholesky_inv_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, status, st);
-  if (dt == DT_F32) return cholesky_inv_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, status, st);
+int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
+                 int* status, cudaStream_t st) {
+  if (dt == DT_F64) return cholesky_inv_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, defl, status, st);
+  if (dt == DT_F32) return cholesky_inv_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, defl, status, st);
   return SPM_EINVAL;
+}
+
+// Replace the deflated columns of X (rows x c) by Gaussian columns scaled by
+// 1/sqrt(rows); Philox4x32-10 keyed by `seed`, counter (row, column, 0, 3).
+template <typename T>
+__global__ void k_fill_deflated(int64_t rows, int64_t c, T* __restrict__ X, int64_t ldx,
+                                const int* __restrict__ defl, uint32_t seed) {
+  const int64_t total = rows * c;
+  const double sc = 1.0 / sqrt((double)rows);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / c, j = e % c;
+    if (!defl[j]) continue;
+    const u32x4 w = philox4x32_10((uint32_t)i, (uint32_t)j, 0u, 3u, seed, 0x2545F491u);
+    const double u1 = ((double)w.x + 1.0) * 0x1.0p-32;
+    const double u2 = (double)w.y * 0x1.0p-32;
+    X[i * ldx + j] = (T)(sc * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+  }
+}
+
+int fill_deflated(int64_t rows, int64_t c, void* X, int64_t ldx, int dt, const int* defl,
+                  uint32_t seed, cudaStream_t st) {
+  if (dt == DT_F64) k_fill_deflated<double><<<grid_for(rows * c), 256, 0, st>>>(rows, c, (double*)X, ldx, defl, seed);
+  else if (dt == DT_F32) k_fill_deflated<float><<<grid_for(rows * c), 256, 0, st>>>(rows, c, (float*)X, ldx, defl, seed);
+  else return SPM_EINVAL;
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
 }
 
 template <typename T>
@@ -526,6 +606,7 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
                   (void*)&ldw, (void*)&mx, (void*)&tl, (void*)&gb, (void*)&offacc,
                   (void*)&status, (void*)&which};
   SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(512), args, 0, st));
+  count_launch();
   k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, a0, a1, ldw, which, Vw, ldw, V, ldv, lam);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
@@ -689,6 +770,7 @@ int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st
   } else {
     return SPM_EINVAL;
   }
+  count_launch(2);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }

@@ -29,8 +29,10 @@ inline View cview(MView v) { return View{v.p, v.dt, v.rs, v.cs}; }
 // ---------------------------------------------------------------- sketch.cu
 // out (m x r1) = A (m x n) S ; out_dt in {F32, F64, BF16}; accumulates |A|_F^2
 // into *fro2 (device double) when fro2 != nullptr.
+// out_lo (BF16 outputs only): second half of a hi/lo split, out_lo = bf16(v - hi).
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
-                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st);
+                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
+                     void* out_lo = nullptr);
 // out (r1 x p) = S^T X, X (n x p, row stride ldx)
 int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
                        void* out, int out_dt, int64_t ldo, cudaStream_t st);
@@ -67,8 +69,13 @@ int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st);
 int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStream_t st);
 // Cholesky G = L L^T of an r x r SPD matrix (row-major, ld), lower L in place,
 // and Linv = L^{-1} (row-major, ldi).  dt: F32 or F64.  Breakdown -> status.
-int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* status,
-                 cudaStream_t st);
+// Deflated columns (pivot <= tol * max diag) are flagged in defl[r] (may be
+// nullptr) and get a unit L column; see fill_deflated.
+int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
+                 int* status, cudaStream_t st);
+// Replace flagged columns of X (rows x c) by random Gaussian columns.
+int fill_deflated(int64_t rows, int64_t c, void* X, int64_t ldx, int dt, const int* defl,
+                  uint32_t seed, cudaStream_t st);
 // Add shift * I to the diagonal, where shift = coef * (sum of diag) (device-computed).
 int add_trace_shift(int64_t r, void* G, int64_t ldg, int dt, double coef, cudaStream_t st);
 // Symmetric eigendecomposition by parallel cyclic Jacobi: A (r x r, row-major,

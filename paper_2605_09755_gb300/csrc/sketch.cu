@@ -221,6 +221,10 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+__device__ __forceinline__ double as_double(float x) { return (double)x; }
+__device__ __forceinline__ double as_double(double x) { return x; }
+__device__ __forceinline__ double as_double(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 template <typename TO>
 __device__ __forceinline__ TO to_out(double v);
 template <>
@@ -243,7 +247,8 @@ __global__ void __launch_bounds__(APPLY_THREADS)
     k_sketch_apply(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, int r1,
                    int nchunks, const int64_t* __restrict__ cptr,
                    const uint32_t* __restrict__ ent, TO* __restrict__ out, int64_t ldo,
-                   int col_groups, double scale, double* __restrict__ fro2) {
+                   int col_groups, double scale, double* __restrict__ fro2,
+                   TO* __restrict__ out_lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TA* tile = reinterpret_cast<TA*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -329,7 +334,13 @@ __global__ void __launch_bounds__(APPLY_THREADS)
   for (int r = 0; r < nrows; ++r) {
     for (int i = lane; i < CPW; i += 32) {
       const int c = cbeg + i;
-      if (c < r1) out[(row0 + r) * ldo + c] = to_out<TO>((double)st[r * (CPW + 1) + i] * scale);
+      if (c < r1) {
+        const double v = (double)st[r * (CPW + 1) + i] * scale;
+        const TO h = to_out<TO>(v);
+        out[(row0 + r) * ldo + c] = h;
+        // split-precision copy: lo = v - hi, rounded (only for BF16 outputs)
+        if (out_lo) out_lo[(row0 + r) * ldo + c] = to_out<TO>(v - as_double(h));
+      }
     }
   }
   if (do_fro) {
@@ -395,7 +406,7 @@ int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint
 
 template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
 static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda, TO* out,
-                        int64_t ldo, double* fro2, cudaStream_t st) {
+                        int64_t ldo, double* fro2, cudaStream_t st, TO* out_lo = nullptr) {
   const int64_t nch = nchunks_of(S->n);
   const int cgsz = APPLY_WARPS * CPW;
   const int col_groups = (int)cdiv(S->r1, cgsz);
@@ -410,26 +421,29 @@ static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda
   const double scale = (S->kind == SPM_SKETCH_IDENTITY) ? 1.0 : 1.0 / sqrt((double)S->s);
   kern<<<(unsigned)grid, APPLY_THREADS, smem, st>>>(A, m, S->n, lda, (int)S->r1, (int)nch,
                                                    S->bucket_ptr, S->bucket_ent, out, ldo,
-                                                   col_groups, scale, fro2);
+                                                   col_groups, scale, fro2, out_lo);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }
 
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
-                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st) {
+                     void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
+                     void* out_lo) {
   if (m <= 0) return SPM_OK;
   if (a_dt == DT_F32) {
     const float* a = (const float*)A;
     if (out_dt == DT_F32) return launch_apply<float, float, float, 32, 2>(S, a, m, lda, (float*)out, ldo, fro2, st);
     if (out_dt == DT_BF16)
-      return launch_apply<float, float, __nv_bfloat16, 32, 2>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st);
+      return launch_apply<float, float, __nv_bfloat16, 32, 2>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st,
+                                                              (__nv_bfloat16*)out_lo);
     if (out_dt == DT_F64) return launch_apply<float, double, double, 16, 2>(S, a, m, lda, (double*)out, ldo, fro2, st);
   } else if (a_dt == DT_F64) {
     const double* a = (const double*)A;
     if (out_dt == DT_F64) return launch_apply<double, double, double, 16, 1>(S, a, m, lda, (double*)out, ldo, fro2, st);
     if (out_dt == DT_F32) return launch_apply<double, double, float, 16, 1>(S, a, m, lda, (float*)out, ldo, fro2, st);
     if (out_dt == DT_BF16)
-      return launch_apply<double, double, __nv_bfloat16, 16, 1>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st);
+      return launch_apply<double, double, __nv_bfloat16, 16, 1>(S, a, m, lda, (__nv_bfloat16*)out, ldo, fro2, st,
+                                                                (__nv_bfloat16*)out_lo);
   }
   return SPM_EINVAL;
 }

@@ -31,6 +31,7 @@ class SpmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reorth", ctypes.c_int32),
                 ("final_passes", ctypes.c_int32), ("small_fp64", ctypes.c_int32),
+                ("power_passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("omega", ctypes.c_void_p)]
 
 
@@ -53,6 +54,7 @@ _SIGS = {
     "spm_version": ([], I32),
     "spm_status_string": ([I32], ctypes.c_char_p),
     "spm_device_ok": ([], I32),
+    "spm_launch_count": ([], U64),
     "spm_sketch_create": ([ctypes.POINTER(VP), I64, I64, I32, U64, I32, VP], I32),
     "spm_sketch_destroy": ([VP], I32),
     "spm_sketch_shape": ([VP, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
@@ -181,8 +183,10 @@ def sketch_apply_t(S, X):
     return out
 
 
-def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False, omega=None):
-    o = Opts(int(precision), int(bool(reorth)), int(final_passes), int(bool(small_fp64)), None)
+def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False, omega=None,
+              power_passes=3):
+    o = Opts(int(precision), int(bool(reorth)), int(final_passes), int(bool(small_fp64)),
+             int(power_passes), 0, None)
     if omega is not None:
         o.omega = omega.data_ptr()
     return o

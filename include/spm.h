@@ -205,6 +205,31 @@ int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* co
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream);
 
+/* ---- no-allocation variant of spm_gemm_bf16 ------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory at all -- a plug-in running inside an engine that owns
+ * the whole device pool, or a serving process that reserves its memory once at
+ * start-up.  It computes exactly what spm_gemm_bf16 computes (same kernels, same
+ * fixed split-K reduction order) but keeps the split-K partial sums in a fixed
+ * file-scope device array of SPM_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every
+ * GPU which loads the library holds until the process exits; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - splitk > 1 needs splitk_effective * M * N <= SPM_NOALLOC_SCRATCH_FLOATS, where
+ *     splitk_effective = ceil(ceil(K/64) / ceil(ceil(K/64)/splitk)); larger
+ *     requests return SPM_EINVAL before anything is launched.  splitk = 1 uses no
+ *     scratch.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture on that device.
+ *   - All calls share the one array per device and it keeps the last call's
+ *     contents (every partial sum is written before it is read, so nothing needs
+ *     clearing).  Calls that overlap on the GPU (different streams, or concurrent
+ *     threads) race on it; serialise them. */
+#define SPM_NOALLOC_SCRATCH_FLOATS (2 * 1024 * 1024)
+int spm_gemm_bf16_noalloc(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
+                          int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb,
+                          int32_t b_mn, float* D, int64_t ldd, int32_t splitk, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

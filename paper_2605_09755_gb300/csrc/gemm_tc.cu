@@ -16,6 +16,7 @@
 // SPM_ETIMEOUT in the status word, drains its own copies and returns.
 #include <cuda.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -450,4 +451,114 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   return SPM_OK;
 }
 
+
+// ------------------------------------------------------------------ no-allocation variant
+// Some callers may not allocate device memory at all: a plug-in that runs
+// inside an inference engine which owns the whole device pool, or a serving
+// process that reserves its memory once at start-up and must not grow it.
+// For them spm_gemm_bf16_noalloc keeps its split-K partial sums in this
+// file-scope device array instead of stream-ordered workspace.  The array lives
+// on every GPU that loads the library until the process exits.  In host code
+// its name is only a host-side stand-in, never a device address: the device
+// address is looked up with cudaGetSymbolAddress, once per device.
+static constexpr int64_t kNoAllocScratchFloats = (int64_t)SPM_NOALLOC_SCRATCH_FLOATS;
+static __device__ __align__(256) float g_noalloc_scratch[SPM_NOALLOC_SCRATCH_FLOATS];
+
+namespace {
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[128] = {};
+}  // namespace
+
+// Device address of the scratch array on the current device (set-up on first use).
+static int noalloc_scratch(float** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return SPM_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPM_ECUDA;
+    g_noalloc_ptr[dev] = reinterpret_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SPM_OK;
+}
+
+int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B,
+                    float* D, int64_t ldd, int splitk, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || npass < 1 || npass > 3) return SPM_EINVAL;
+  if (M > 0x7FFFFFFF || N > 0x7FFFFFFF || K > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  for (int q = 0; q < npass; ++q)
+    if (A[q].mn_major != A[0].mn_major || B[q].mn_major != B[0].mn_major) return SPM_EINVAL;
+  const int BN = (N >= 192) ? 256 : 128;
+  const int k_tiles = (int)cdiv(K, TC_BK);
+  if (splitk < 1) splitk = 1;
+  if (splitk > k_tiles) splitk = k_tiles;
+  const int kt_per = (int)cdiv(k_tiles, splitk);
+  splitk = (int)cdiv(k_tiles, kt_per);
+  // the partial sums must fit the fixed scratch array
+  if (splitk > 1 && (int64_t)splitk * M * N > kNoAllocScratchFloats) return SPM_EINVAL;
+  const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
+  if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
+  float* scratch = nullptr;
+  SPM_TRY(noalloc_scratch(&scratch));
+  CUtensorMap ta[3], tb[3];
+  for (int q = 0; q < 3; ++q) {
+    const int qq = q < npass ? q : 0;
+    SPM_TRY(make_map(&ta[q], A[qq], M, K, TC_BM));
+    SPM_TRY(make_map(&tb[q], B[qq], N, K, BN));
+  }
+  TcParams p{};
+  p.M = (int)M;
+  p.N = (int)N;
+  p.K = (int)K;
+  p.k_tiles = k_tiles;
+  p.kt_per_split = kt_per;
+  p.npass = npass;
+  p.alpha = 1.0f;
+  p.status = nullptr;
+  if (splitk == 1) {
+    p.D = D;
+    p.d_rs = ldd;
+    p.d_cs = 1;
+    p.split_stride = 0;
+  } else {
+    // every partial the reduction reads is written first by the GEMM, so the
+    // scratch needs no clearing between calls
+    p.D = scratch;
+    p.d_rs = N;
+    p.d_cs = 1;
+    p.split_stride = M * N;
+  }
+  dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
+  if (BN == 256)
+    SPM_TRY(launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+  else
+    SPM_TRY(launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+  if (splitk > 1) {
+    const int64_t total = M * N;
+    const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
+    k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, splitk, scratch, D, ldd, 1);
+    SPM_LAUNCH_CHECK();
+  }
+  return SPM_OK;
+}
+
 }  // namespace spm
+
+extern "C" int spm_gemm_bf16_noalloc(int64_t M, int64_t N, int64_t K, int32_t npass,
+                                     const void* const* A, int64_t lda, int32_t a_mn,
+                                     const void* const* B, int64_t ldb, int32_t b_mn, float* D,
+                                     int64_t ldd, int32_t splitk, void* stream) {
+  using namespace spm;
+  if (M < 1 || N < 1 || K < 1 || npass < 1 || npass > 3 || !A || !B || !D || ldd < N || splitk < 1)
+    return SPM_EINVAL;
+  if (lda < (a_mn ? M : K) || ldb < (b_mn ? N : K)) return SPM_EINVAL;
+  if (!tc_available()) return SPM_ECUDA;
+  TcOp a[3], b[3];
+  for (int q = 0; q < npass; ++q) {
+    if (!A[q] || !B[q]) return SPM_EINVAL;
+    a[q] = TcOp{(const __nv_bfloat16*)A[q], lda, a_mn != 0};
+    b[q] = TcOp{(const __nv_bfloat16*)B[q], ldb, b_mn != 0};
+  }
+  return gemm_tc_noalloc(M, N, K, npass, a, b, D, ldd, splitk, as_stream(stream));
+}

@@ -265,3 +265,22 @@ def gemm_bf16(A_list, B_list, M, N, K, a_mn=False, b_mn=False, splitk=1):
                                B_list[0].stride(0), int(b_mn), _ptr(D), D.stride(0), int(splitk),
                                _stream()), "spm_gemm_bf16")
     return D
+
+
+def gemm_bf16_noalloc(A_list, B_list, M, N, K, D, a_mn=False, b_mn=False, splitk=1):
+    """Same product as gemm_bf16 into a caller-provided fp32 D, with no device allocation.
+
+    For callers that may not allocate device memory (see spm_gemm_bf16_noalloc in spm.h):
+    split-K partial sums use a fixed library-owned device array instead of workspace.
+    """
+    L = lib()
+    fn = L.spm_gemm_bf16_noalloc
+    fn.argtypes = [I64, I64, I64, I32, ctypes.POINTER(VP), I64, I32, ctypes.POINTER(VP), I64, I32,
+                   VP, I64, I32, VP]
+    fn.restype = I32
+    npass = len(A_list)
+    Ap = (VP * npass)(*[a.data_ptr() for a in A_list])
+    Bp = (VP * npass)(*[b.data_ptr() for b in B_list])
+    _check(fn(M, N, K, npass, Ap, A_list[0].stride(0), int(a_mn), Bp, B_list[0].stride(0),
+              int(b_mn), _ptr(D), D.stride(0), int(splitk), _stream()), "spm_gemm_bf16_noalloc")
+    return D

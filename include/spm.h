@@ -93,7 +93,7 @@ typedef struct spm_opts {
 typedef struct spm_info {
   /* inputs */
   int32_t want_timing;  /* 1: record CUDA events around stages (forces a final sync)       */
-  int32_t reserved0;
+  int32_t eig_sweeps;   /* output: Jacobi sweeps used by the core eigensolver (rsvd)       */
   /* outputs (written when info != NULL; the call synchronises its stream) */
   int32_t device_status;    /* SPM_OK or the first device-side error code                */
   int32_t cholqr_passes;    /* CholeskyQR passes executed on the final basis              */
@@ -204,6 +204,45 @@ int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, in
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream);
+
+/* ---- learned (q, sketch size) selector -------------------------------------------
+ * A multilayer perceptron (8 -> 64 -> 64 -> 64 -> 15, ReLU) that reads features
+ * of the q = 0 sketch and predicts log10(residual / optimal - 1) of the range
+ * finder for 15 candidates: q in 0..4 times sketch size r1 in {2, 4, 8} x r2
+ * (output index 3 * q + c).  The paper has no such component: it picks q and
+ * the sketch size from the bounds of Theorems 2.1-2.3, which hold up to
+ * unspecified constants.  Parameters: one packed FP32 vector of
+ * SPM_MLP_PARAMS floats, layer by layer, W (out x in, row-major) then b.
+ * All pointers are device pointers. */
+#define SPM_MLP_IN 8
+#define SPM_MLP_OUT 15
+#define SPM_MLP_PARAMS 9871
+/* Y (batch x 15) = network(X (batch x 8)). */
+int spm_mlp_forward(const float* params, const float* X, int64_t batch, float* Y, void* stream);
+/* Masked mean squared error L = sum M (Y - T)^2 / max(sum M, 1) over a batch and its
+ * gradient: grad (SPM_MLP_PARAMS floats) and loss (1 float) are overwritten. */
+int spm_mlp_loss_grad(const float* params, const float* X, const float* T, const float* M,
+                      int64_t batch, float* grad, float* loss, void* stream);
+/* One Adam step (step >= 1) on params with moments m, v. */
+int spm_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t step, float lr,
+                 float b1, float b2, float eps, void* stream);
+/* The 8 selector features of the q = 0 sketch Y0 = (A S) Omega (Algorithm 1 with
+ * q = 0; Omega r1 x r2 Gaussian from omega_seed) written to feat (device, 8 floats):
+ * log10(s_{r2/4}/s_1), log10(s_{r2/2}/s_1), log10(s_{r2}/s_1), log10(r2 s_{r2}^2 /
+ * sum s_i^2), log10(m)/4, log10(n)/4, log10(r2)/3, log2(r1/r2)/3, where s_i are the
+ * singular values of Y0. */
+int spm_selector_features(const spm_sketch* S, const void* A, int32_t dtype, int64_t m,
+                          int64_t lda, int64_t r2, uint64_t omega_seed, float* feat, void* stream);
+/* Randomized SVD of rank k with q and r1 chosen by the selector network (params,
+ * device) for a requested residual ratio target_ratio = |A - U S V^T|_F / optimal
+ * (> 1): features from a probe sketch of size min(4k, n); the cheapest candidate
+ * ((2q + 1) r1) predicted to meet the target is run; if none is, the candidate with
+ * the smallest predicted ratio.  choice (host, may be NULL) receives {q, r1 / k}.
+ * Synchronises the stream once to read the prediction. */
+int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                  double target_ratio, const float* params, uint64_t seed, const spm_opts* opts,
+                  void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, int32_t* choice,
+                  spm_info* info, void* stream);
 
 /* ---- no-allocation variant of spm_gemm_bf16 ------------------------------------
  * The paper has no counterpart: this entry point exists for callers that may not

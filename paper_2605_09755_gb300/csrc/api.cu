@@ -79,7 +79,7 @@ static int orth_f64(Call& C, double* X, int64_t rows, int64_t c, int64_t ldx, in
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F64, ldx)),
                       rowmajor(X, DT_F64, ldx), 0.0, mrowmajor(G, DT_F64, c), C.st));
-    if (ps == 0 && passes > 2)
+    if (ps == 0)
       SPM_TRY(add_trace_shift(c, G, c, DT_F64, shift_coef(true, rows, c), C.st));
     SPM_TRY(cholesky_inv(c, G, c, Li, c, DT_F64, defl, C.status, C.st));
     SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F64, ldx), transpose(rowmajor(Li, DT_F64, c)),
@@ -104,7 +104,7 @@ static int orth_small_f32(Call& C, float* X, int64_t rows, int64_t c, int64_t ld
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(gemm_simt(c, c, rows, 1.0, transpose(rowmajor(X, DT_F32, ldx)),
                       rowmajor(X, DT_F32, ldx), 0.0, mrowmajor(G, sdt, c), C.st));
-    if (ps == 0 && passes > 2) SPM_TRY(add_trace_shift(c, G, c, sdt, shift_coef(false, rows, c), C.st));
+    if (ps == 0) SPM_TRY(add_trace_shift(c, G, c, sdt, shift_coef(false, rows, c), C.st));
     SPM_TRY(cholesky_inv(c, G, c, Li, c, sdt, defl, C.status, C.st));
     SPM_TRY(gemm_simt(rows, c, c, 1.0, rowmajor(X, DT_F32, ldx), transpose(rowmajor(Li, sdt, c)), 0.0,
                       mrowmajor(Xn, DT_F32, c), C.st));
@@ -198,7 +198,7 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
       }
       if (C.reorth) {
         StageScope sc(C.timer, SPM_STAGE_ORTH);
-        SPM_TRY(orth_f64(C, Z, r1, r2, r2, 3));
+        SPM_TRY(orth_f64(C, Z, r1, r2, r2, 2));  // shifted pass + one plain pass
       }
       {
         StageScope sc(C.timer, SPM_STAGE_POWER);
@@ -259,7 +259,7 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
     }
     if (C.reorth) {
       StageScope sc(C.timer, SPM_STAGE_ORTH);
-      SPM_TRY(orth_small_f32(C, Z, r1, r2, r2, 3));
+      SPM_TRY(orth_small_f32(C, Z, r1, r2, r2, 2));  // shifted pass + one plain pass
     }
     {
       StageScope sc(C.timer, SPM_STAGE_POWER);
@@ -306,10 +306,10 @@ static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info
 }
 
 static int prepare(Call& C) {
-  C.status = C.ar.alloc<int>(1);
+  C.status = C.ar.alloc<int>(4);  // [0] device status, [1] eigensolver sweeps
   C.acc = C.ar.alloc<double>(2);
   if (!C.status || !C.acc) return SPM_ENOMEM;
-  SPM_CUDA_TRY(cudaMemsetAsync(C.status, 0, sizeof(int), C.st));
+  SPM_CUDA_TRY(cudaMemsetAsync(C.status, 0, 4 * sizeof(int), C.st));
   SPM_CUDA_TRY(cudaMemsetAsync(C.acc, 0, 2 * sizeof(double), C.st));
   if (C.prec == SPM_PREC_MIXED && !tc_available()) return SPM_ECUDA;
   return SPM_OK;
@@ -318,14 +318,16 @@ static int prepare(Call& C) {
 static int finish(Call& C, spm_info* info, int rc, bool has_b) {
   if (rc != SPM_OK) return rc;
   if (!info) return SPM_OK;
-  int dst = 0;
+  int stw[4] = {0, 0, 0, 0};
   double acc[2] = {0.0, 0.0};
-  SPM_CUDA_TRY(cudaMemcpyAsync(&dst, C.status, sizeof(int), cudaMemcpyDeviceToHost, C.st));
+  SPM_CUDA_TRY(cudaMemcpyAsync(stw, C.status, 4 * sizeof(int), cudaMemcpyDeviceToHost, C.st));
   SPM_CUDA_TRY(cudaMemcpyAsync(acc, C.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, C.st));
   SPM_CUDA_TRY(cudaStreamSynchronize(C.st));
   for (int i = 0; i < SPM_NSTAGES; ++i) info->stage_ms[i] = 0.f;
   C.timer.collect(info->stage_ms);
+  const int dst = stw[0];
   info->device_status = dst;
+  info->eig_sweeps = stw[1];
   info->cholqr_passes = C.cholqr_passes;
   info->fro_a = sqrt(acc[0]);
   info->resid_est = has_b ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
@@ -362,7 +364,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
       SPM_TRY(gemm_simt(r2, r2, n, 1.0, rowmajor(B, DT_F64, n), transpose(rowmajor(B, DT_F64, n)),
                         0.0, mrowmajor(G, DT_F64, r2), C.st));
       SPM_TRY(symmetrize(r2, G, r2, DT_F64, C.st));
-      SPM_TRY(sym_eig(r2, G, r2, Ut, r2, lam, DT_F64, C.status, C.st));
+      SPM_TRY(sym_eig(r2, G, r2, Ut, r2, lam, DT_F64, C.status, C.st, C.status + 1));
     }
     {
       StageScope sc(C.timer, SPM_STAGE_FINISH);
@@ -415,7 +417,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st));
     SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Gs, sdt, r2), C.st));
     SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
-    SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st));
+    SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st, C.status + 1));
     SPM_TRY(split_bf16(r2, r2, rowmajor(Ut, sdt, r2), mrowmajor(Uhi, DT_BF16, r2p),
                        mrowmajor(Ulo, DT_BF16, r2p), C.st));
   }

@@ -153,4 +153,8 @@ struct spm_sketch {
   int8_t* signs;          // n*s
   int64_t* bucket_ptr;    // r1+1
   uint32_t* bucket_ent;   // n*s: row index j in bits 0..30, sign (1 = minus) in bit 31
+  int2* seg;              // chunks x r1: [start, end) of each (chunk, column) segment,
+                          // relative to the chunk's first entry
+  uint32_t* entoff;       // n*s: (j mod 512) * 33 | sign bit -- shared-memory offset of the
+                          // entry's column in the transposed A tile
 };

@@ -26,6 +26,21 @@ __device__ __forceinline__ void std_<__nv_bfloat16>(__nv_bfloat16* p, double v) 
   *p = __float2bfloat16_rn((float)v);
 }
 
+// Direct element conversions; FP32 paths avoid FP64 intermediates (the FP64
+// pipe, conversions included, is far slower than FP32 on this part).
+template <typename TY, typename TX>
+__device__ __forceinline__ TY cvt(TX x) { return (TY)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double x) {
+  return __float2bfloat16_rn((float)x);
+}
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 x) { return x; }
+
 template <typename TX, typename TY>
 __global__ void k_convert(int64_t rows, int64_t cols, const TX* __restrict__ x, int64_t xrs,
                           int64_t xcs, TY* __restrict__ y, int64_t yrs, int64_t ycs) {
@@ -41,7 +56,7 @@ __global__ void k_convert(int64_t rows, int64_t cols, const TX* __restrict__ x, 
       j = e / rows;
       i = e % rows;
     }
-    std_<TY>(y + i * yrs + j * ycs, ldd<TX>(x + i * xrs + j * xcs));
+    y[i * yrs + j * ycs] = cvt<TY, TX>(x[i * xrs + j * xcs]);
   }
 }
 
@@ -60,7 +75,7 @@ __global__ void k_split(int64_t rows, int64_t cols, const TX* __restrict__ x, in
       j = e / rows;
       i = e % rows;
     }
-    const float v = (float)ldd<TX>(x + i * xrs + j * xcs);
+    const float v = (float)x[i * xrs + j * xcs];
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const float r = v - __bfloat162float(h);
     hi[i * hrs + j * hcs] = h;
@@ -107,7 +122,12 @@ int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStrea
 }
 
 // ------------------------------------------------------------------ Cholesky
-static constexpr int CH_NB = 64;
+// Leaf size of the blocked Cholesky: 128 in FP32, 64 in FP64 (shared memory).
+template <typename T>
+struct ChNB {
+  static constexpr int v = 64;
+};
+static constexpr int CH_THREADS = 512;
 
 // Factor one diagonal block G_kk = L L^T in shared memory (right-looking), write
 // L (lower, zeros above) back in place and L^{-1} into Linv.
@@ -117,62 +137,96 @@ static constexpr int CH_NB = 64;
 // caller replaces that column of the orthonormalised basis by a fresh random
 // direction which the next CholeskyQR pass orthonormalises.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(CH_THREADS)
     k_chol_diag(int b, T* __restrict__ G, int64_t ldg, T* __restrict__ Li, int64_t ldi,
                 const T* __restrict__ maxd, T tol, int* __restrict__ defl,
                 int* __restrict__ status) {
+  constexpr int NB = ChNB<T>::v;
   extern __shared__ __align__(16) unsigned char ch_smem[];
-  T(*a)[CH_NB + 1] = reinterpret_cast<T(*)[CH_NB + 1]>(ch_smem);
-  T(*inv)[CH_NB + 1] = reinterpret_cast<T(*)[CH_NB + 1]>(ch_smem + sizeof(T) * CH_NB * (CH_NB + 1));
-  __shared__ int bad, dj;
+  T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(ch_smem);
+  T(*inv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(ch_smem + sizeof(T) * NB * (NB + 1));
+  __shared__ T rdiag[NB];  // 1/sqrt(pivot), 0 for a deflated column
+  __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   const T thr = tol * (*maxd);
-  for (int e = tid; e < b * b; e += blockDim.x) {
+  for (int e = tid; e < b * b; e += CH_THREADS) {
     const int i = e / b, j = e % b;
     a[i][j] = (j <= i) ? G[(int64_t)i * ldg + j] : (T)0;
   }
   __syncthreads();
+  // Right-looking elimination with one barrier per pivot: column j is final
+  // (unscaled) when step j starts, so every thread reads the pivot itself and
+  // applies a[i][k] -= a[i][j] a[k][j] / a[j][j] to its own 2 x 4 elements of
+  // the trailing square (rows ty + 32 v, columns tx + 16 u; entries above the
+  // diagonal are skipped).  All loads of a step are issued before any store.
+  const int ty = tid / 16, tx = tid % 16;
+  static_assert(NB == 64 && CH_THREADS == 512, "2 x 4 elements per thread");
   for (int j = 0; j < b; ++j) {
+    const T d = a[j][j];
+    const bool fin = isfinite((double)d);
+    const bool piv = fin && (d > thr);
+    const T invd = piv ? (T)1 / d : (T)0;
     if (tid == 0) {
-      const T d = a[j][j];
-      int f = 0;
-      if (!isfinite((double)d)) {
-        bad = 1;
-        f = 1;
-      } else if (!(d > thr)) {
-        f = 1;
-      }
-      dj = f;
-      a[j][j] = f ? (T)1 : sqrt(d);
-      if (defl) defl[j] = f;
+      rdiag[j] = piv ? (T)1 / sqrt(d) : (T)0;
+      if (defl) defl[j] = piv ? 0 : 1;
+      if (!fin) bad = 1;
     }
-    __syncthreads();
-    const T djj = a[j][j];
-    const int f = dj;
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) a[i][j] = f ? (T)0 : a[i][j] / djj;
-    __syncthreads();
-    const int rem = b - j - 1;
-    if (!f) {
-      for (int e = tid; e < rem * rem; e += blockDim.x) {
-        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-        if (k <= i) a[i][k] -= a[i][j] * a[k][j];
+    if (piv) {
+      T ci[2], ck[4], val[2][4];
+      int ii[2], kk[4];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        ii[v] = j + 1 + ty + 32 * v;
+        ci[v] = (ii[v] < b) ? a[ii[v]][j] * invd : (T)0;
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kk[u] = j + 1 + tx + 16 * u;
+        ck[u] = (kk[u] < b) ? a[kk[u]][j] : (T)0;
+      }
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          val[v][u] = (ii[v] < b && kk[u] <= ii[v]) ? a[ii[v]][kk[u]] : (T)0;
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (ii[v] < b && kk[u] <= ii[v]) a[ii[v]][kk[u]] = val[v][u] - ci[v] * ck[u];
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular block, one column per thread
-  for (int c = tid; c < b; c += blockDim.x) {
+  // scale columns: L[i][j] = a[i][j] / sqrt(pivot j); deflated columns become e_j
+  for (int e = tid; e < b * b; e += CH_THREADS) {
+    const int i = e / b, j = e % b;
+    const T r = rdiag[j];
+    T v;
+    if (j > i) v = (T)0;
+    else if (r == (T)0) v = (i == j) ? (T)1 : (T)0;
+    else v = (i == j) ? (T)1 / r : a[i][j] * r;
+    a[i][j] = v;
+  }
+  __syncthreads();
+  // inverse of the lower-triangular block: column c by 4 threads, each summing
+  // every fourth term of the substitution, combined with warp shuffles
+  for (int c0 = 0; c0 < NB; c0 += CH_THREADS / 4) {
+    const int c = c0 + (tid >> 2), part = tid & 3;
     for (int i = 0; i < b; ++i) {
-      T sacc = (i == c) ? (T)1 : (T)0;
-      for (int k = c; k < i; ++k) sacc -= a[i][k] * inv[k][c];
-      inv[i][c] = (i < c) ? (T)0 : sacc / a[i][i];
+      T sacc = (T)0;
+      if (c < b && i > c)
+        for (int k = c + part; k < i; k += 4) sacc += a[i][k] * inv[k][c];
+      sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, 1);
+      sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, 2);
+      if (part == 0 && c < b) inv[i][c] = (i < c) ? (T)0 : (((i == c) ? (T)1 : (T)0) - sacc) / a[i][i];
+      __syncwarp();
     }
   }
   __syncthreads();
-  for (int e = tid; e < b * b; e += blockDim.x) {
+  for (int e = tid; e < b * b; e += CH_THREADS) {
     const int i = e / b, j = e % b;
-    G[(int64_t)i * ldg + j] = (j <= i) ? a[i][j] : (T)0;
+    G[(int64_t)i * ldg + j] = a[i][j];
     Li[(int64_t)i * ldi + j] = inv[i][j];
   }
   if (tid == 0 && bad) set_status(status, DEV_NONFINITE);
@@ -226,10 +280,11 @@ __global__ void k_zero2d(int64_t rows, int64_t cols, T* __restrict__ p, int64_t 
 template <typename T>
 static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int* defl,
                           int* status, cudaStream_t st) {
+  constexpr int NB = ChNB<T>::v;
   const int dt = std::is_same<T, double>::value ? DT_F64 : DT_F32;
   const T tol = std::is_same<T, double>::value ? (T)1e-12 : (T)1e-6;
   Arena ar(st);
-  SPM_ALLOC(ar, T, P, r * CH_NB);
+  SPM_ALLOC(ar, T, P, r * NB);
   SPM_ALLOC(ar, T, Tm, r * r);
   SPM_ALLOC(ar, T, maxd, 1);
   if (!defl) {
@@ -240,38 +295,54 @@ static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int*
   SPM_LAUNCH_CHECK();
   k_maxdiag<T><<<1, 256, 0, st>>>(r, G, ldg, maxd);
   SPM_LAUNCH_CHECK();
-  const int smem = (int)(2 * sizeof(T) * CH_NB * (CH_NB + 1));
+  const int smem = (int)(2 * sizeof(T) * NB * (NB + 1));
   SPM_CUDA_TRY(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  for (int64_t kb = 0; kb < r; kb += CH_NB) {
-    const int b = (int)min64(CH_NB, r - kb);
-    k_chol_diag<T><<<1, 256, smem, st>>>(b, G + kb * ldg + kb, ldg, Li + kb * ldi + kb, ldi, maxd,
-                                         tol, defl + kb, status);
+  for (int64_t kb = 0; kb < r; kb += NB) {
+    const int b = (int)min64(NB, r - kb);
+    k_chol_diag<T><<<1, CH_THREADS, smem, st>>>(b, G + kb * ldg + kb, ldg, Li + kb * ldi + kb, ldi,
+                                                 maxd, tol, defl + kb, status);
     SPM_LAUNCH_CHECK();
     const int64_t rest = r - kb - b;
     if (rest > 0) {
-      // P = G21 * Linv_kk^T   (rest x b), deflated columns forced to zero
-      View g21 = rowmajor(G + (kb + b) * ldg + kb, dt, ldg);
+      // P = G21 * Linv_kk^T (rest x b), deflated columns forced to zero
+      T* g21 = G + (kb + b) * ldg + kb;
       View lkT = transpose(rowmajor(Li + kb * ldi + kb, dt, ldi));
-      SPM_TRY(gemm_simt(rest, b, b, 1.0, g21, lkT, 0.0, mrowmajor(P, dt, CH_NB), st));
-      k_zero_defl_cols<T><<<grid_for(rest * b), 256, 0, st>>>(rest, b, P, CH_NB, defl + kb);
+      SPM_TRY(gemm_simt(rest, b, b, 1.0, rowmajor(g21, dt, ldg), lkT, 0.0, mrowmajor(P, dt, NB), st));
+      k_zero_defl_cols<T><<<grid_for(rest * b), 256, 0, st>>>(rest, b, P, NB, defl + kb);
       SPM_LAUNCH_CHECK();
       // G22 -= P P^T
-      SPM_TRY(gemm_simt(rest, rest, b, -1.0, rowmajor(P, dt, CH_NB),
-                        transpose(rowmajor(P, dt, CH_NB)), 1.0,
+      SPM_TRY(gemm_simt(rest, rest, b, -1.0, rowmajor(P, dt, NB), transpose(rowmajor(P, dt, NB)), 1.0,
                         mrowmajor(G + (kb + b) * ldg + (kb + b), dt, ldg), st));
       // L21 = P
-      k_copy_block<T><<<grid_for(rest * b), 256, 0, st>>>((int)rest, b, P, CH_NB,
-                                                           G + (kb + b) * ldg + kb, ldg);
+      k_copy_block<T><<<grid_for(rest * b), 256, 0, st>>>((int)rest, b, P, NB, g21, ldg);
       SPM_LAUNCH_CHECK();
     }
   }
-  // off-diagonal blocks of L^{-1}: Linv[i, 0:ib] = -Linv_ii * (L[i, 0:ib] * Linv[0:ib, 0:ib])
-  for (int64_t ib = CH_NB; ib < r; ib += CH_NB) {
-    const int b = (int)min64(CH_NB, r - ib);
-    SPM_TRY(gemm_simt(b, ib, ib, 1.0, rowmajor(G + ib * ldg, dt, ldg), rowmajor(Li, dt, ldi), 0.0,
-                      mrowmajor(Tm, dt, ib), st));
-    SPM_TRY(gemm_simt(b, ib, b, -1.0, rowmajor(Li + ib * ldi + ib, dt, ldi), rowmajor(Tm, dt, ib),
-                      0.0, mrowmajor(Li + ib * ldi, dt, ldi), st));
+  // Off-diagonal blocks of L^{-1} by recursive doubling: with the inverses of
+  // the two diagonal halves of a 2s x 2s diagonal block known,
+  //   Linv[o+s:o+2s, o:o+s] = -Linv[o+s:o+2s, o+s:o+2s] * L[o+s:o+2s, o:o+s] * Linv[o:o+s, o:o+s].
+  // All such blocks of one level are independent: two batched products per level.
+  for (int64_t sz = NB; sz < r; sz *= 2) {
+    const int64_t full = r / (2 * sz);            // complete 2s blocks
+    const int64_t o_tail = full * 2 * sz;
+    const int64_t tail2 = r - o_tail - sz;        // size of a ragged lower half, if any
+    const int64_t bstride_g = 2 * sz * (ldg + 1), bstride_i = 2 * sz * (ldi + 1);
+    if (full > 0) {
+      // Tm[t] = L21 * Linv11   (s x s each)
+      SPM_TRY(gemm_simt(sz, sz, sz, 1.0, rowmajor(G + sz * ldg, dt, ldg), rowmajor(Li, dt, ldi), 0.0,
+                        mrowmajor(Tm, dt, sz), st, (int)full, bstride_g, bstride_i, sz * sz));
+      // Linv21 = -Linv22 * Tm
+      SPM_TRY(gemm_simt(sz, sz, sz, -1.0, rowmajor(Li + sz * ldi + sz, dt, ldi), rowmajor(Tm, dt, sz),
+                        0.0, mrowmajor(Li + sz * ldi, dt, ldi), st, (int)full, bstride_i, sz * sz,
+                        bstride_i));
+    }
+    if (tail2 > 0) {
+      const int64_t o = o_tail;
+      SPM_TRY(gemm_simt(tail2, sz, sz, 1.0, rowmajor(G + (o + sz) * ldg + o, dt, ldg),
+                        rowmajor(Li + o * ldi + o, dt, ldi), 0.0, mrowmajor(Tm, dt, sz), st));
+      SPM_TRY(gemm_simt(tail2, sz, tail2, -1.0, rowmajor(Li + (o + sz) * ldi + (o + sz), dt, ldi),
+                        rowmajor(Tm, dt, sz), 0.0, mrowmajor(Li + (o + sz) * ldi + o, dt, ldi), st));
+    }
   }
   return SPM_OK;
 }
@@ -356,12 +427,22 @@ int symmetrize(int64_t r, void* A, int64_t lda, int dt, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ Jacobi eig
-// Parallel cyclic Jacobi (round-robin ordering): every round rotates n/2
-// disjoint index pairs at once.  The new matrix is J^T A J with J a direct sum
-// of 2 x 2 rotations, so each 2 x 2 block of the new matrix depends only on
-// one 2 x 2 block of the old one; the kernel double-buffers A and needs one
-// grid-wide barrier per round.  Launched cooperatively (all CTAs resident);
-// the barrier spin is bounded and reports SPM_ETIMEOUT on expiry.
+// Block cyclic Jacobi for the symmetric eigenproblem G = V diag(lam) V^T.
+//
+// G is padded to NB blocks of JB = 32 (NB even) with zero rows/columns, which
+// never couple to the real ones.  A sweep runs NB - 1 rounds of the
+// round-robin ("chess tournament") pairing of the blocks.  In a round:
+//   phase 1: CTA c < NB/2 takes block pair c, loads the 64 x 64 subproblem
+//            [G_PP G_PQ; G_QP G_QQ] into shared memory and diagonalises it by
+//            cyclic 2 x 2 Jacobi (a few inner sweeps), accumulating the 64 x 64
+//            rotation J_c;
+//   phase 2: every CTA applies the rotations as small dense products:
+//            G[i, j] <- J_i^T G[i, j] J_j for every pair of block pairs (each
+//            64 x 64 tile is read and written by one CTA only, so in place), and
+//            V[:, j] <- V[:, j] J_j.
+// One bounded grid barrier separates the phases; the kernel is launched
+// cooperatively so that all CTAs are resident.  A sweep starts with the
+// off-diagonal mass test.
 struct GridBar {
   unsigned* count;
   unsigned* gen;
@@ -399,159 +480,332 @@ __device__ __forceinline__ bool grid_sync(GridBar gb, unsigned nblocks, int* sta
 __device__ __forceinline__ int rr_player(int pos, int r, int np) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (np - 1));
 }
-
-template <typename T>
-__device__ __forceinline__ void rr_pair(int i, int r, int np, int n, int& p, int& q, bool& active) {
+// pair i of round r among np (even) players
+__device__ __forceinline__ void rr_pair(int i, int r, int np, int& p, int& q) {
   const int a = rr_player(i, r, np), b = rr_player(np - 1 - i, r, np);
   p = min(a, b);
   q = max(a, b);
-  active = q < n;
 }
 
+static constexpr int JB = 16;          // block size
+static constexpr int JS = 2 * JB;      // subproblem size
+static constexpr int JLD = JS + 1;     // padded shared-memory row
+static constexpr int JTHREADS = 256;
+
 template <typename T>
-__device__ __forceinline__ void rot_params(const T* A, int64_t lda, int p, int q, bool active, T& c,
-                                           T& s) {
+__device__ __forceinline__ void rot_params(T app, T aqq, T apq, T& c, T& s) {
   c = (T)1;
   s = (T)0;
-  if (!active) return;
-  const T apq = A[(int64_t)p * lda + q];
-  const T app = A[(int64_t)p * lda + p];
-  const T aqq = A[(int64_t)q * lda + q];
-  const T eps = std::is_same<T, double>::value ? (T)1e-300 : (T)1e-37;
-  if (fabs((double)apq) <= (double)eps) return;
+  if (fabs(apq) <= (T)1e-300) return;
   const T tau = (aqq - app) / ((T)2 * apq);
   const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
   c = (T)1 / sqrt((T)1 + t * t);
   s = t * c;
 }
+// FP32: approximate reciprocal / square-root intrinsics keep the rotation on the
+// critical path short; c = rsqrt(1 + t^2), s = t c stay orthogonal to rounding.
+template <>
+__device__ __forceinline__ void rot_params<float>(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.f;
+  s = 0.f;
+  if (fabsf(apq) <= 1e-37f) return;
+  const float tau = (aqq - app) * __frcp_rn(2.f * apq);
+  const float t = copysignf(1.f, tau) * __frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
+  c = rsqrtf(fmaf(t, t, 1.f));
+  s = t * c;
+}
+
+// global index of local row a (0..63) of block pair (P, Q)
+__device__ __forceinline__ int pair_index(int P, int Q, int a) {
+  return a < JB ? P * JB + a : Q * JB + (a - JB);
+}
+
+// Phase 1: eigendecomposition of a JS x JS symmetric tile in shared memory by
+// cyclic 2 x 2 Jacobi.  Each inner round first tabulates its JB index pairs and
+// rotations (one thread per pair), then every thread updates whole 2 x 2
+// blocks of M and row pairs of J from the tables.
+template <typename T>
+__device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inner, double tol2) {
+  const int tid = threadIdx.x;
+  __shared__ double red[2];
+  __shared__ unsigned char pp[JB], qq[JB];
+  for (int e = tid; e < JS * JS; e += JTHREADS) J[e / JS][e % JS] = (e / JS == e % JS) ? (T)1 : (T)0;
+  __syncthreads();
+  for (int sw = 0; sw < max_inner; ++sw) {
+    if (max_inner > 1) {
+      if (tid < 2) red[tid] = 0.0;
+      __syncthreads();
+      double off = 0.0, tot = 0.0;
+      for (int e = tid; e < JS * JS; e += JTHREADS) {
+        const double v = (double)M[e / JS][e % JS];
+        tot += v * v;
+        if (e / JS != e % JS) off += v * v;
+      }
+      atomicAdd(&red[0], off);
+      atomicAdd(&red[1], tot);
+      __syncthreads();
+      const bool done = red[0] <= tol2 * red[1];
+      __syncthreads();
+      if (done) break;
+    }
+    for (int r = 0; r < JS - 1; ++r) {
+      if (tid < JB) {
+        int p, q;
+        rr_pair(tid, r, JS, p, q);
+        T c, s;
+        rot_params<T>(M[p][p], M[q][q], M[p][q], c, s);
+        pp[tid] = (unsigned char)p;
+        qq[tid] = (unsigned char)q;
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      for (int w = tid; w < JB * JB; w += JTHREADS) {
+        const int bi = w / JB, bj = w % JB;
+        const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
+        const T ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
+        const T m00 = M[pi][pj], m01 = M[pi][qj], m10 = M[qi][pj], m11 = M[qi][qj];
+        const T t00 = ci * m00 - si * m10, t01 = ci * m01 - si * m11;
+        const T t10 = si * m00 + ci * m10, t11 = si * m01 + ci * m11;
+        T n00 = cj * t00 - sj * t01, n01 = sj * t00 + cj * t01;
+        T n10 = cj * t10 - sj * t11, n11 = sj * t10 + cj * t11;
+        if (bi == bj) {
+          n01 = (T)0;
+          n10 = (T)0;
+        }
+        M[pi][pj] = n00;
+        M[pi][qj] = n01;
+        M[qi][pj] = n10;
+        M[qi][qj] = n11;
+      }
+      for (int w = tid; w < JS * JB; w += JTHREADS) {
+        const int row = w / JB, bj = w % JB;
+        const int pj = pp[bj], qj = qq[bj];
+        const T cj = cs[bj], sj = sn[bj];
+        const T vp = J[row][pj], vq = J[row][qj];
+        J[row][pj] = cj * vp - sj * vq;
+        J[row][qj] = sj * vp + cj * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// C (JS x JS, smem) = op(X) * Y with op = transpose when tx; 256 threads on a
+// 16 x 16 grid, each (JS/16)^2 outputs.
+template <typename T>
+__device__ __forceinline__ void tile_mm(const T (*X)[JLD], const T (*Y)[JLD], T (*C)[JLD], bool tx) {
+  constexpr int R = JS / 16;
+  const int tid = threadIdx.x, ty = tid / 16, tx4 = tid % 16;
+  T acc[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) acc[a][b] = (T)0;
+#pragma unroll 4
+  for (int l = 0; l < JS; ++l) {
+    T xa[R], yb[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) xa[a] = tx ? X[l][ty + 16 * a] : X[ty + 16 * a][l];
+#pragma unroll
+    for (int b = 0; b < R; ++b) yb[b] = Y[l][tx4 + 16 * b];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) C[ty + 16 * a][tx4 + 16 * b] = acc[a][b];
+  __syncthreads();
+}
 
 template <typename T>
-__global__ void __launch_bounds__(512)
-    k_jacobi(int n, int np, T* __restrict__ A0, T* __restrict__ A1, int64_t lda, T* __restrict__ V,
-             int64_t ldv, int max_sweeps, double tol2, GridBar gb, double* __restrict__ offacc,
-             int* __restrict__ status, int* __restrict__ which) {
+__global__ void __launch_bounds__(JTHREADS)
+    k_block_jacobi(int n, int NB, T* __restrict__ G, T* __restrict__ V, T* __restrict__ Jbuf,
+                   int max_sweeps, double tol2, int max_inner, double tol2_inner, GridBar gb,
+                   double* __restrict__ offacc, int* __restrict__ status, int* __restrict__ sweeps_out) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  T(*S0)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm);
+  T(*S1)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + sizeof(T) * JS * JLD);
+  T(*S2)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + 2 * sizeof(T) * JS * JLD);
+  T(*S3)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + 3 * sizeof(T) * JS * JLD);
+  __shared__ T cs[JB], sn[JB];
+  __shared__ double red2[2];
   const unsigned nb = gridDim.x;
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-  const int hp = np / 2;
-  T* Acur = A0;
-  T* Anew = A1;
+  const int tid = threadIdx.x;
+  const int npad = NB * JB;
+  const int hp = NB / 2;
+  const int64_t ld = npad;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    // convergence test on the current matrix
-    double off = 0.0, dia = 0.0;
-    for (int64_t e = gtid; e < (int64_t)n * n; e += gsz) {
-      const int64_t i = e / n, j = e % n;
-      const double v = (double)Acur[i * lda + j];
-      if (i == j) dia += v * v;
-      else off += v * v;
+    // off-diagonal mass
+    double off = 0.0, tot = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)JTHREADS + tid; e < (int64_t)npad * npad;
+         e += (int64_t)nb * JTHREADS) {
+      const double v = (double)G[e];
+      tot += v * v;
+      if (e / npad != e % npad) off += v * v;
     }
-    if (gtid == 0) {
+    if (tid < 2) red2[tid] = 0.0;
+    if (blockIdx.x == 0 && tid == 0) {
       offacc[2 * (sweep & 1)] = 0.0;
       offacc[2 * (sweep & 1) + 1] = 0.0;
     }
     if (!grid_sync(gb, nb, status)) return;
-    {
-      __shared__ double red_off[32], red_dia[32];
-      for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
-        dia += __shfl_xor_sync(0xFFFFFFFFu, dia, o);
-      }
-      if ((threadIdx.x & 31) == 0) {
-        red_off[threadIdx.x >> 5] = off;
-        red_dia[threadIdx.x >> 5] = dia;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double so = 0.0, sd = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-          so += red_off[w];
-          sd += red_dia[w];
-        }
-        atomicAdd(&offacc[2 * (sweep & 1)], so);
-        atomicAdd(&offacc[2 * (sweep & 1) + 1], sd);
-      }
+    atomicAdd(&red2[0], off);
+    atomicAdd(&red2[1], tot);
+    __syncthreads();
+    if (tid == 0) {
+      atomicAdd(&offacc[2 * (sweep & 1)], red2[0]);
+      atomicAdd(&offacc[2 * (sweep & 1) + 1], red2[1]);
     }
     if (!grid_sync(gb, nb, status)) return;
     const double offv = *((volatile double*)&offacc[2 * (sweep & 1)]);
-    const double diav = *((volatile double*)&offacc[2 * (sweep & 1) + 1]);
-    if (offv <= tol2 * (offv + diav)) break;
-    for (int r = 0; r < np - 1; ++r) {
-      // 2x2 blocks of the new matrix
-      for (int64_t w = gtid; w < (int64_t)hp * hp; w += gsz) {
-        const int bi = (int)(w / hp), bj = (int)(w % hp);
-        int pi, qi, pj, qj;
-        bool ai, aj;
-        rr_pair<T>(bi, r, np, n, pi, qi, ai);
-        rr_pair<T>(bj, r, np, n, pj, qj, aj);
-        T ci, si, cj, sj;
-        rot_params<T>(Acur, lda, pi, qi, ai, ci, si);
-        rot_params<T>(Acur, lda, pj, qj, aj, cj, sj);
-        // rows present: pi always (< n unless pi itself is the dummy, impossible: p < q)
-        const bool rq = qi < n, cq = qj < n;
-        const T m00 = Acur[(int64_t)pi * lda + pj];
-        const T m01 = cq ? Acur[(int64_t)pi * lda + qj] : (T)0;
-        const T m10 = rq ? Acur[(int64_t)qi * lda + pj] : (T)0;
-        const T m11 = (rq && cq) ? Acur[(int64_t)qi * lda + qj] : (T)0;
-        // J_i^T M
-        const T t00 = ci * m00 - si * m10, t01 = ci * m01 - si * m11;
-        const T t10 = si * m00 + ci * m10, t11 = si * m01 + ci * m11;
-        // (J_i^T M) J_j
-        T n00 = cj * t00 - sj * t01, n01 = sj * t00 + cj * t01;
-        T n10 = cj * t10 - sj * t11, n11 = sj * t10 + cj * t11;
-        if (bi == bj && ai) {
-          n01 = (T)0;
-          n10 = (T)0;
+    const double totv = *((volatile double*)&offacc[2 * (sweep & 1) + 1]);
+    if (offv <= tol2 * totv) break;
+    for (int r = 0; r < NB - 1; ++r) {
+      // ---------------- phase 1: subproblems
+      for (int c = blockIdx.x; c < hp; c += nb) {
+        int P, Q;
+        rr_pair(c, r, NB, P, Q);
+        for (int e = tid; e < JS * JS; e += JTHREADS) {
+          const int a = e / JS, b = e % JS;
+          S0[a][b] = G[(int64_t)pair_index(P, Q, a) * ld + pair_index(P, Q, b)];
         }
-        Anew[(int64_t)pi * lda + pj] = n00;
-        if (cq) Anew[(int64_t)pi * lda + qj] = n01;
-        if (rq) Anew[(int64_t)qi * lda + pj] = n10;
-        if (rq && cq) Anew[(int64_t)qi * lda + qj] = n11;
-      }
-      // V <- V J (column pairs)
-      for (int64_t w = gtid; w < (int64_t)n * hp; w += gsz) {
-        const int row = (int)(w / hp), bj = (int)(w % hp);
-        int pj, qj;
-        bool aj;
-        rr_pair<T>(bj, r, np, n, pj, qj, aj);
-        if (!aj) continue;
-        T cj, sj;
-        rot_params<T>(Acur, lda, pj, qj, aj, cj, sj);
-        const T vp = V[(int64_t)row * ldv + pj], vq = V[(int64_t)row * ldv + qj];
-        V[(int64_t)row * ldv + pj] = cj * vp - sj * vq;
-        V[(int64_t)row * ldv + qj] = sj * vp + cj * vq;
+        __syncthreads();
+        inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
+        T* Jc = Jbuf + (size_t)c * JS * JS;
+        for (int e = tid; e < JS * JS; e += JTHREADS) Jc[e] = S1[e / JS][e % JS];
+        __syncthreads();
       }
       if (!grid_sync(gb, nb, status)) return;
-      T* tmp = Acur;
-      Acur = Anew;
-      Anew = tmp;
+      // ---------------- phase 2: G <- J^T G J (tile pairs), V <- V J
+      // One warp per item; lane = column of the 32 x 32 tile.
+      {
+        const int lane = tid & 31, warp = tid >> 5;
+        T(*X)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + (size_t)warp * 3 * sizeof(T) * JS * JLD);
+        T(*Jt)[JLD] = X + JS;
+        T(*Tt)[JLD] = X + 2 * JS;
+        const int gitems = hp * (hp + 1) / 2;  // tile pairs i <= j; G_ji is the transpose
+        const int vitems = (npad / JS) * hp;
+        const int nwarps = (int)nb * (JTHREADS / 32);
+        for (int w = (int)blockIdx.x * (JTHREADS / 32) + warp; w < gitems + vitems; w += nwarps) {
+          if (w < gitems) {
+            // w -> (i, j), i <= j, row-wise over the upper triangle of pair indices
+            int i = (int)(((2.0f * hp + 1.0f) - sqrtf((2.0f * hp + 1.0f) * (2.0f * hp + 1.0f) - 8.0f * w)) * 0.5f);
+            if (i < 0) i = 0;
+            while (i > 0 && i * hp - i * (i - 1) / 2 > w) --i;
+            while ((i + 1) * hp - (i + 1) * i / 2 <= w) ++i;
+            const int j = i + (w - (i * hp - i * (i - 1) / 2));
+            int Pi, Qi, Pj, Qj;
+            rr_pair(i, r, NB, Pi, Qi);
+            rr_pair(j, r, NB, Pj, Qj);
+            const T* Ji = Jbuf + (size_t)i * JS * JS;
+            const T* Jj = Jbuf + (size_t)j * JS * JS;
+            const int64_t colj = pair_index(Pj, Qj, lane), coli = pair_index(Pi, Qi, lane);
+            for (int a = 0; a < JS; ++a) {
+              X[a][lane] = G[(int64_t)pair_index(Pi, Qi, a) * ld + colj];
+              Jt[a][lane] = Ji[a * JS + lane];
+            }
+            __syncwarp();
+            // Tt = Ji^T X
+            for (int a0 = 0; a0 < JS; a0 += 8) {
+              T acc[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
+              for (int l = 0; l < JS; ++l) {
+                const T xv = X[l][lane];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = fma(Jt[l][a0 + u], xv, acc[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) Tt[a0 + u][lane] = acc[u];
+            }
+            __syncwarp();
+            for (int a = 0; a < JS; ++a) Jt[a][lane] = Jj[a * JS + lane];
+            __syncwarp();
+            // X = Tt Jj
+            for (int a0 = 0; a0 < JS; a0 += 8) {
+              T acc[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
+              for (int l = 0; l < JS; ++l) {
+                const T jv = Jt[l][lane];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = fma(Tt[a0 + u][l], jv, acc[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) X[a0 + u][lane] = acc[u];
+            }
+            __syncwarp();
+            for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = X[a][lane];
+            if (i != j)
+              for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pj, Qj, a) * ld + coli] = X[lane][a];
+            __syncwarp();
+          } else {
+            const int v = w - gitems;
+            const int rb = v / hp, j = v % hp;
+            int Pj, Qj;
+            rr_pair(j, r, NB, Pj, Qj);
+            const T* Jj = Jbuf + (size_t)j * JS * JS;
+            const int64_t colj = pair_index(Pj, Qj, lane);
+            for (int a = 0; a < JS; ++a) {
+              X[a][lane] = V[(int64_t)(rb * JS + a) * ld + colj];
+              Jt[a][lane] = Jj[a * JS + lane];
+            }
+            __syncwarp();
+            for (int a0 = 0; a0 < JS; a0 += 8) {
+              T acc[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
+              for (int l = 0; l < JS; ++l) {
+                const T jv = Jt[l][lane];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = fma(X[a0 + u][l], jv, acc[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) Tt[a0 + u][lane] = acc[u];
+            }
+            __syncwarp();
+            for (int a = 0; a < JS; ++a) V[(int64_t)(rb * JS + a) * ld + colj] = Tt[a][lane];
+            __syncwarp();
+          }
+        }
+      }
+      if (!grid_sync(gb, nb, status)) return;
     }
   }
-  if (gtid == 0) *which = (Acur == A0) ? 0 : 1;
+  if (blockIdx.x == 0 && tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
 }
 
 template <typename T>
-__global__ void k_eye(int64_t n, T* V, int64_t ldv) {
-  const int64_t total = n * n;
+__global__ void k_eye_pad(int n, int npad, const T* __restrict__ A, int64_t lda, T* __restrict__ G,
+                          T* __restrict__ V) {
+  const int64_t total = (int64_t)npad * npad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x)
-    V[(e / n) * ldv + (e % n)] = (e / n == e % n) ? (T)1 : (T)0;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / npad, j = e % npad;
+    G[e] = (i < n && j < n) ? A[i * lda + j] : (T)0;
+    V[e] = (i == j) ? (T)1 : (T)0;
+  }
 }
 
-// Sort eigenvalues descending and permute eigenvector columns accordingly.
+// Sort the first n eigenvalues (diagonal of G) descending and gather eigenvector
+// columns; padded positions (>= n) hold the decoupled zero rows and are skipped.
 template <typename T>
-__global__ void k_eig_sort(int n, const T* __restrict__ A0, const T* __restrict__ A1, int64_t lda,
-                           const int* __restrict__ which, const T* __restrict__ Vin, int64_t ldvi,
+__global__ void k_eig_sort(int n, int64_t ldg, const T* __restrict__ G, const T* __restrict__ Vin,
                            T* __restrict__ Vout, int64_t ldvo, T* __restrict__ lam) {
-  const T* A = (*which == 0) ? A0 : A1;
+  __shared__ int rk;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const T li = A[(int64_t)i * lda + i];
-    __shared__ int rk;
+    const T li = G[(int64_t)i * ldg + i];
     if (threadIdx.x == 0) rk = 0;
     __syncthreads();
     int cnt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const T lj = A[(int64_t)j * lda + j];
+      const T lj = G[(int64_t)j * ldg + j];
       if (lj > li || (lj == li && j < i)) ++cnt;
     }
     atomicAdd(&rk, cnt);
@@ -559,65 +813,66 @@ __global__ void k_eig_sort(int n, const T* __restrict__ A0, const T* __restrict_
     const int pos = rk;
     if (threadIdx.x == 0) lam[pos] = li;
     for (int row = threadIdx.x; row < n; row += blockDim.x)
-      Vout[(int64_t)row * ldvo + pos] = Vin[(int64_t)row * ldvi + i];
+      Vout[(int64_t)row * ldvo + pos] = Vin[(int64_t)row * ldg + i];
     __syncthreads();
   }
 }
 
 template <typename T>
 static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, int* status,
-                     cudaStream_t st) {
+                     cudaStream_t st, int* sweeps) {
   const int n = (int)r;
-  const int np = n + (n & 1);
+  int NB = (int)cdiv(n, JB);
+  if (NB < 2) NB = 2;
+  if (NB & 1) ++NB;
+  const int npad = NB * JB;
   Arena ar(st);
-  SPM_ALLOC(ar, T, A1, r * r);
-  SPM_ALLOC(ar, T, Vw, r * r);
+  SPM_ALLOC(ar, T, G, (int64_t)npad * npad);
+  SPM_ALLOC(ar, T, Vw, (int64_t)npad * npad);
+  SPM_ALLOC(ar, T, Jbuf, (int64_t)(NB / 2) * JS * JS);
   SPM_ALLOC(ar, unsigned, bar, 2);
   SPM_ALLOC(ar, double, offacc, 4);
-  SPM_ALLOC(ar, int, which, 1);
   SPM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  k_eye<T><<<grid_for(r * r), 256, 0, st>>>(r, Vw, r);
+  k_eye_pad<T><<<grid_for((int64_t)npad * npad), 256, 0, st>>>(n, npad, A, lda, G, Vw);
   SPM_LAUNCH_CHECK();
-  k_copy_block<T><<<grid_for(r * r), 256, 0, st>>>(n, n, A, lda, A1, r);
-  SPM_LAUNCH_CHECK();
-  SPM_CUDA_TRY(cudaMemsetAsync(which, 0, sizeof(int), st));
   int dev = 0, sms = 0, per_sm = 0;
   SPM_CUDA_TRY(cudaGetDevice(&dev));
   SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  auto kern = k_jacobi<T>;
-  SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0));
+  const int smem = (int)((JTHREADS / 32) * 3 * sizeof(T) * JS * JLD);
+  auto kern = k_block_jacobi<T>;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JTHREADS, smem));
   if (per_sm < 1) return SPM_ECUDA;
-  const int64_t work = (int64_t)(np / 2) * (np / 2) + (int64_t)n * (np / 2);
-  int blocks = (int)min64(cdiv(work, 512 * 4), (int64_t)sms);
-  if (blocks < 1) blocks = 1;
+  const int hp = NB / 2;
+  const int items = hp * (hp + 1) / 2 + (npad / JS) * hp;
+  // one CTA per SM: the grid barrier's arrival count stays small
+  int blocks = min(items, sms);
+  blocks = max(blocks, hp);
+  if (blocks > sms * per_sm) return SPM_EUNSUPPORTED;  // too large for one resident grid
   const bool is64 = std::is_same<T, double>::value;
-  const int max_sweeps = is64 ? 30 : 20;
-  // stop when the off-diagonal mass reaches the rounding floor: (10 n eps)^2 relative
   const double eps = is64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
-  const double tol = (10.0 * n * eps) * (10.0 * n * eps);
+  double tol2 = (4.0 * npad * eps) * (4.0 * npad * eps);
+  double tol2i = (4.0 * JS * eps) * (4.0 * JS * eps);
+  int max_sweeps = is64 ? 25 : 20;
+  int max_inner = 1;  // one inner sweep per round: the outer sweeps converge the rest
   GridBar gb{bar, bar + 1};
-  SPM_ALLOC(ar, T, A2, r * r);
-  T* a0 = A1;  // the kernel works on two private copies (ld r)
-  T* a1 = A2;
-  int64_t ldw = r;
-  int mx = max_sweeps;
-  double tl = tol;
-  void* args[] = {(void*)&n, (void*)&np, (void*)&a0, (void*)&a1, (void*)&ldw, (void*)&Vw,
-                  (void*)&ldw, (void*)&mx, (void*)&tl, (void*)&gb, (void*)&offacc,
-                  (void*)&status, (void*)&which};
-  SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(512), args, 0, st));
+  int NBv = NB;
+  void* args[] = {(void*)&n, (void*)&NBv, (void*)&G, (void*)&Vw, (void*)&Jbuf,
+                  (void*)&max_sweeps, (void*)&tol2, (void*)&max_inner, (void*)&tol2i,
+                  (void*)&gb, (void*)&offacc, (void*)&status, (void*)&sweeps};
+  SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(JTHREADS), args, smem, st));
   count_launch();
-  k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, a0, a1, ldw, which, Vw, ldw, V, ldv, lam);
+  k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, npad, G, Vw, V, ldv, lam);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }
 
 int sym_eig(int64_t r, void* A, int64_t lda, void* V, int64_t ldv, void* lam, int dt, int* status,
-            cudaStream_t st) {
+            cudaStream_t st, int* sweeps) {
   if (r <= 0) return SPM_OK;
-  if (r > 0x3FFFFFFF) return SPM_EUNSUPPORTED;
-  if (dt == DT_F64) return sym_eig_t<double>(r, (double*)A, lda, (double*)V, ldv, (double*)lam, status, st);
-  if (dt == DT_F32) return sym_eig_t<float>(r, (float*)A, lda, (float*)V, ldv, (float*)lam, status, st);
+  if (r > 16384) return SPM_EUNSUPPORTED;
+  if (dt == DT_F64) return sym_eig_t<double>(r, (double*)A, lda, (double*)V, ldv, (double*)lam, status, st, sweeps);
+  if (dt == DT_F32) return sym_eig_t<float>(r, (float*)A, lda, (float*)V, ldv, (float*)lam, status, st, sweeps);
   return SPM_EINVAL;
 }
 

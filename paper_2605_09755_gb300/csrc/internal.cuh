@@ -81,8 +81,9 @@ int add_trace_shift(int64_t r, void* G, int64_t ldg, int dt, double coef, cudaSt
 // Symmetric eigendecomposition by parallel cyclic Jacobi: A (r x r, row-major,
 // overwritten), V (r x r row-major eigenvectors in columns), lam (r) sorted
 // descending, V columns permuted accordingly.  dt F32 or F64.
+// sweeps (device int, may be nullptr): atomic max of the Jacobi sweeps executed.
 int sym_eig(int64_t r, void* A, int64_t lda, void* V, int64_t ldv, void* lam, int dt, int* status,
-            cudaStream_t st);
+            cudaStream_t st, int* sweeps = nullptr);
 // out[j] = sqrt(sum_i X[i,j]^2) for columns (col = true) or rows (col = false), in FP64.
 int norms(int64_t rows, int64_t cols, View X, bool by_col, double* out, cudaStream_t st);
 // Scale rows (or columns) of X by s[i] (or 1/s[i] when inv).

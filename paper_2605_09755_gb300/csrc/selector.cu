@@ -1,0 +1,162 @@
+// Learned choice of the power count q and the sketch size r1.
+//
+// Theorems 2.1-2.3 size q and r1 only up to unspecified constants, so in
+// practice they are tuned.  This file computes cheap features of the q = 0
+// sketch (Algorithm 1 with q = 0: Y0 = A S Omega), feeds them to the selector
+// network (mlp.cu) and runs the Randomized SVD with the cheapest candidate the
+// network predicts to meet a requested residual ratio.
+//
+// Features (one FP32 vector of 8, see spm.h), from the singular values
+// s_1 >= ... >= s_r2 of Y0 (square roots of the eigenvalues of Y0^T Y0):
+//   log10(s_{r2/4}/s_1), log10(s_{r2/2}/s_1), log10(s_{r2}/s_1),
+//   log10(r2 s_{r2}^2 / sum s_i^2), log10(m)/4, log10(n)/4, log10(r2)/3,
+//   log2(r1/r2)/3.
+#include <math.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace spm {
+
+int mlp_forward_dev(const float* params, const float* X, int64_t batch, float* Y, cudaStream_t st);
+
+__global__ void k_selector_features(const float* __restrict__ lam, int r2, double m, double n,
+                                    double r1, float* __restrict__ feat) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s0 = sqrt(fmax((double)lam[0], 0.0));
+  if (!(s0 > 0.0)) s0 = 1e-300;
+  double tot = 0.0;
+  for (int i = 0; i < r2; ++i) {
+    const double si = fmax(sqrt(fmax((double)lam[i], 0.0)), 1e-30 * s0);
+    tot += si * si;
+  }
+  auto sv = [&](int i) { return fmax(sqrt(fmax((double)lam[i], 0.0)), 1e-30 * s0); };
+  const int i4 = max(1, r2 / 4), i2 = max(1, r2 / 2);
+  const double sl = sv(r2 - 1);
+  feat[0] = (float)log10(sv(i4 - 1) / s0);
+  feat[1] = (float)log10(sv(i2 - 1) / s0);
+  feat[2] = (float)log10(sl / s0);
+  feat[3] = (float)log10(r2 * sl * sl / tot);
+  feat[4] = (float)(log10(m) / 4.0);
+  feat[5] = (float)(log10(n) / 4.0);
+  feat[6] = (float)(log10((double)r2) / 3.0);
+  feat[7] = (float)(log2(r1 / r2) / 3.0);
+}
+
+static int64_t pad8s(int64_t x) { return round_up(x, 8); }
+
+int selector_features_dev(const spm_sketch* S, const void* A, int adt, int64_t m, int64_t lda,
+                          int64_t r2, uint64_t seed, float* feat, cudaStream_t st) {
+  const int64_t r1 = S->r1, r1p = pad8s(r1), r2p = pad8s(r2);
+  Arena ar(st);
+  SPM_ALLOC(ar, __nv_bfloat16, Ahi, m * r1p);
+  SPM_ALLOC(ar, __nv_bfloat16, Alo, m * r1p);
+  SPM_ALLOC(ar, float, Om, r1 * r2);
+  SPM_ALLOC(ar, __nv_bfloat16, Ohi, r1 * r2p);
+  SPM_ALLOC(ar, __nv_bfloat16, Olo, r1 * r2p);
+  SPM_ALLOC(ar, float, Y, m * r2);
+  SPM_ALLOC(ar, float, G, r2 * r2);
+  SPM_ALLOC(ar, float, V, r2 * r2);
+  SPM_ALLOC(ar, float, lam, r2);
+  SPM_ALLOC(ar, int, status, 1);
+  SPM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  SPM_TRY(gaussian_dev(Om, DT_F32, r1, r2, r2, seed, st));
+  SPM_TRY(split_bf16(r1, r2, rowmajor(Om, DT_F32, r2), mrowmajor(Ohi, DT_BF16, r2p),
+                     mrowmajor(Olo, DT_BF16, r2p), st));
+  SPM_TRY(sketch_apply_dev(S, A, adt, m, lda, Ahi, DT_BF16, r1p, nullptr, st, Alo));
+  // Y0 = A~ Omega as a split-precision product (A~ K-major, Omega MN-major)
+  TcOp a[3] = {{Ahi, r1p, false}, {Ahi, r1p, false}, {Alo, r1p, false}};
+  TcOp b[3] = {{Ohi, r2p, true}, {Olo, r2p, true}, {Ohi, r2p, true}};
+  SPM_TRY(gemm_tc(m, r2, r1, 3, a, b, 1.0f, Y, r2, 1, 1, st));
+  SPM_TRY(gemm_simt(r2, r2, m, 1.0, transpose(rowmajor(Y, DT_F32, r2)), rowmajor(Y, DT_F32, r2), 0.0,
+                    mrowmajor(G, DT_F32, r2), st));
+  SPM_TRY(symmetrize(r2, G, r2, DT_F32, st));
+  SPM_TRY(sym_eig(r2, G, r2, V, r2, lam, DT_F32, status, st));
+  k_selector_features<<<1, 32, 0, st>>>(lam, (int)r2, (double)m, (double)S->n, (double)r1, feat);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+int spm_selector_features(const spm_sketch* S, const void* A, int32_t dtype, int64_t m,
+                          int64_t lda, int64_t r2, uint64_t omega_seed, float* feat, void* stream) {
+  if (!S || !A || !feat || m < 1 || lda < S->n || r2 < 1 || r2 > S->r1 || r2 > m) return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  if (!tc_available()) return SPM_ECUDA;
+  return selector_features_dev(S, A, dtype == SPM_F64 ? DT_F64 : DT_F32, m, lda, r2, omega_seed, feat,
+                               as_stream(stream));
+}
+
+int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
+                  double target_ratio, const float* params, uint64_t seed, const spm_opts* opts,
+                  void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, int32_t* choice,
+                  spm_info* info, void* stream) {
+  if (!A || !params || !U || !sigma || !Vt || m < 1 || n < 1 || lda < n || k < 1 || k > m ||
+      k > n || ldu < k || ldvt < n || !(target_ratio > 1.0))
+    return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const int s = 8;
+  const int64_t r1p = (4 * k < n) ? 4 * k : n;
+  spm_sketch* P = nullptr;
+  SPM_TRY(spm_sketch_create(&P, n, r1p, (int32_t)(s < r1p ? s : r1p), seed, SPM_SKETCH_SPARSE_SIGN, st));
+  int rc = SPM_OK;
+  float pred[SPM_MLP_OUT];
+  {
+    Arena ar(st);
+    float* feat = ar.alloc<float>(SPM_MLP_IN);
+    float* out = ar.alloc<float>(SPM_MLP_OUT);
+    if (!feat || !out) rc = SPM_ENOMEM;
+    if (rc == SPM_OK) rc = spm_selector_features(P, A, dtype, m, lda, k, seed + 1, feat, stream);
+    if (rc == SPM_OK) rc = mlp_forward_dev(params, feat, 1, out, st);
+    if (rc == SPM_OK && cudaMemcpyAsync(pred, out, sizeof(pred), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = SPM_ECUDA;
+    if (rc == SPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPM_ECUDA;
+  }
+  if (rc != SPM_OK) {
+    spm_sketch_destroy(P);
+    return rc;
+  }
+  // cheapest candidate predicted to reach the target; cost ~ (2q + 1) r1 for
+  // the power products, ties broken towards smaller q; if no candidate is
+  // predicted to reach it, the one with the smallest predicted error
+  const double thr = log10(target_ratio - 1.0);
+  const int cs[3] = {2, 4, 8};
+  int best = -1, best_any = 0;
+  double best_cost = 1e300;
+  for (int q = 0; q <= 4; ++q)
+    for (int c = 0; c < 3; ++c) {
+      const int idx = 3 * q + c;
+      if (pred[idx] < pred[best_any]) best_any = idx;
+      const double cost = (2.0 * q + 1.0) * cs[c];
+      if (pred[idx] <= thr && cost < best_cost) {
+        best_cost = cost;
+        best = idx;
+      }
+    }
+  if (best < 0) best = best_any;
+  const int q = best / 3, c = cs[best % 3];
+  int64_t r1 = c * k;
+  if (r1 > n) r1 = n;
+  if (choice) {
+    choice[0] = q;
+    choice[1] = c;
+  }
+  spm_sketch* S = P;
+  if (r1 != r1p) {
+    spm_sketch_destroy(P);
+    P = nullptr;
+    SPM_TRY(spm_sketch_create(&S, n, r1, (int32_t)(s < r1 ? s : r1), seed, SPM_SKETCH_SPARSE_SIGN, st));
+  }
+  rc = spm_rsvd(S, A, dtype, m, lda, k, q, seed + 1, k, opts, U, ldu, sigma, Vt, ldvt, info, stream);
+  spm_sketch_destroy(S);
+  return rc;
+}
+
+}  // extern "C"

@@ -19,7 +19,7 @@ namespace spm {
 
 static constexpr int CHUNK = 512;          // rows of S (columns of A) per tile
 static constexpr int APPLY_ROWS = 32;      // rows of A per CTA (one per lane)
-static constexpr int APPLY_WARPS = 16;
+static constexpr int APPLY_WARPS = 32;
 static constexpr int APPLY_THREADS = APPLY_WARPS * 32;
 static constexpr int APPLY_TILE_LD = APPLY_ROWS + 1;   // padded: conflict-free
 static constexpr uint32_t SIGN_BIT = 0x80000000u;
@@ -142,6 +142,23 @@ __global__ void k_chunk_sort(int64_t n, int r1, int s, const int32_t* __restrict
 
 __global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
 
+// Segment bounds relative to each chunk's first entry, and per-entry tile offsets.
+__global__ void k_apply_tables(int64_t nnz, int r1, int nchunks, const int64_t* __restrict__ cptr,
+                               const uint32_t* __restrict__ ent, int2* __restrict__ seg,
+                               uint32_t* __restrict__ entoff) {
+  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t q = g0; q < (int64_t)nchunks * r1; q += gsz) {
+    const int64_t base = cptr[(q / r1) * r1];
+    seg[q] = make_int2((int)(cptr[q] - base), (int)(cptr[q + 1] - base));
+  }
+  for (int64_t e = g0; e < nnz; e += gsz) {
+    const uint32_t v = ent[e];
+    const uint32_t jj = (v & ~SIGN_BIT) % (uint32_t)CHUNK;
+    entoff[e] = (jj * (uint32_t)APPLY_TILE_LD) | (v & SIGN_BIT);
+  }
+}
+
 // Plain CSC view for spm_sketch_tables: count per column over all chunks.
 __global__ void k_bucket_counts(int r1, int nchunks, const int64_t* __restrict__ cptr,
                                 int64_t* __restrict__ cnt) {
@@ -216,6 +233,10 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_elem8(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
@@ -224,6 +245,17 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ double as_double(float x) { return (double)x; }
 __device__ __forceinline__ double as_double(double x) { return x; }
 __device__ __forceinline__ double as_double(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+template <typename TO, typename TV>
+__device__ __forceinline__ TO cvt_out(TV v) { return (TO)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16, double>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
 
 template <typename TO>
 __device__ __forceinline__ TO to_out(double v);
@@ -237,33 +269,79 @@ __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(double v) {
 }
 
 // One CTA: 32 rows of A (lane = row) x a group of CG = 16 warps * CPW output
-// columns.  The A tile (32 rows x CHUNK columns) is staged transposed in shared
-// memory ([jj][row], row stride 33) so that one warp-wide read of a column jj
-// hits 32 distinct banks; every bucket entry then costs one conflict-free
-// shared load and one FMA per lane.  Accumulators stay in registers across
-// all chunks.  NBUF = 2 double-buffers the tile with 4/8-byte cp.async.
-template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
-__global__ void __launch_bounds__(APPLY_THREADS)
+// columns.  Per chunk of CHUNK = 512 columns of A (rows of S):
+//   * the A tile (32 x 512) is staged transposed in shared memory ([jj][row],
+//     row stride 33), so one warp-wide read of column jj hits 32 distinct banks;
+//   * the CTA's segment bounds and bucket entries for this chunk (one
+//     contiguous range) are staged next to it; each entry already holds the
+//     tile offset of its column and its sign bit;
+//   all with cp.async into a double buffer, so chunk k+1 streams in while
+//   chunk k is reduced.  Each warp owns CPW output columns with one accumulator
+//   per lane and column in registers across all chunks; an entry costs one
+//   broadcast shared load, one conflict-free shared load of A, a sign flip and
+//   an add per lane.
+template <typename TA, typename TACC>
+__device__ __forceinline__ TACC signed_val(TA a, uint32_t e) {
+  return (e & SIGN_BIT) ? -(TACC)a : (TACC)a;
+}
+template <>
+__device__ __forceinline__ float signed_val<float, float>(float a, uint32_t e) {
+  return __int_as_float(__float_as_int(a) ^ (int)(e & SIGN_BIT));
+}
+
+// Sum of the signed tile values of one (chunk, column) segment [p, pe) of the
+// staged entries; entries past the staged capacity are read from global memory.
+template <typename TA, typename TACC>
+__device__ __noinline__ TACC segment_sum(const uint32_t* es, const TA* t, const uint32_t* eg, int p,
+                                         int pe, int ent_cap) {
+  TACC a0 = (TACC)0, a1 = (TACC)0;
+  if (pe <= ent_cap) {
+    for (; p + 1 < pe; p += 2) {
+      const uint32_t e0 = es[p], e1 = es[p + 1];
+      a0 += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
+      a1 += signed_val<TA, TACC>(t[e1 & ~SIGN_BIT], e1);
+    }
+    if (p < pe) {
+      const uint32_t e0 = es[p];
+      a0 += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
+    }
+  } else {
+    for (; p < pe; ++p) {
+      const uint32_t e0 = (p < ent_cap) ? es[p] : __ldg(eg + p);
+      a0 += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
+    }
+  }
+  return a0 + a1;
+}
+
+template <typename TA, typename TACC, typename TO, int CPW, int NBUF, bool GENT>
+__global__ void __launch_bounds__(APPLY_THREADS, 1)
     k_sketch_apply(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda, int r1,
-                   int nchunks, const int64_t* __restrict__ cptr,
-                   const uint32_t* __restrict__ ent, TO* __restrict__ out, int64_t ldo,
+                   int nchunks, const int64_t* __restrict__ cptr, const int2* __restrict__ seg,
+                   const uint32_t* __restrict__ entoff, TO* __restrict__ out, int64_t ldo,
                    int col_groups, double scale, double* __restrict__ fro2,
-                   TO* __restrict__ out_lo) {
+                   TO* __restrict__ out_lo, int ent_cap) {
+  constexpr int CG = APPLY_WARPS * CPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TA* tile = reinterpret_cast<TA*>(smem_raw);
+  int2* seg_s = reinterpret_cast<int2*>(smem_raw + (size_t)NBUF * CHUNK * APPLY_TILE_LD * sizeof(TA));
+  uint32_t* ent_s = reinterpret_cast<uint32_t*>(seg_s + (size_t)NBUF * CG);  // NBUF x ent_cap
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t rb = blockIdx.x / col_groups;
   const int cg = blockIdx.x % col_groups;
   const int64_t row0 = rb * APPLY_ROWS;
   const int nrows = (int)min64(APPLY_ROWS, m - row0);
-  const int cbeg = cg * (APPLY_WARPS * CPW) + warp * CPW;
+  const int c0 = cg * CG;
+  const int c1 = (int)min64(c0 + CG, r1);
+  const int ncols = c1 - c0;
+  const int wc0 = warp * CPW;  // first column of this warp, relative to c0
   const bool do_fro = (fro2 != nullptr) && (cg == 0);
   TACC acc[CPW];
 #pragma unroll
   for (int i = 0; i < CPW; ++i) acc[i] = (TACC)0;
   double fro_local = 0.0;
 
-  // stage chunk k into buffer b: thread tid owns column jj = tid (+512 ...)
+  // stage chunk k into buffer b (A tile, segment bounds, entries)
   auto stage = [&](int k, int b) {
     TA* t = tile + (size_t)b * CHUNK * APPLY_TILE_LD;
     const int64_t j0 = (int64_t)k * CHUNK;
@@ -278,6 +356,15 @@ __global__ void __launch_bounds__(APPLY_THREADS)
           *dst = (TA)0;
       }
     }
+    const int2* sg = seg + (int64_t)k * r1 + c0;
+    int2* ss = seg_s + (size_t)b * CG;
+    for (int i = tid; i < ncols; i += APPLY_THREADS) cp_async_elem8(ss + i, sg + i);
+    const int e_beg = __ldg(&sg[0].x), e_end = __ldg(&sg[ncols - 1].y);
+    const int cnt = min(e_end - e_beg, ent_cap);
+    const uint32_t* src = entoff + __ldg(cptr + (int64_t)k * r1) + e_beg;
+    uint32_t* es = ent_s + (size_t)b * ent_cap;
+    if (!GENT)
+      for (int i = tid; i < cnt; i += APPLY_THREADS) cp_async_elem(es + i, src + i);
     cp_async_commit();
   };
 
@@ -296,31 +383,39 @@ __global__ void __launch_bounds__(APPLY_THREADS)
       cp_async_wait<0>();
     }
     __syncthreads();
-    const TA* t = tile + (size_t)b * CHUNK * APPLY_TILE_LD;
+    const TA* t = tile + (size_t)b * CHUNK * APPLY_TILE_LD + lane;
+    const int2* ss = seg_s + (size_t)b * CG;
+    const uint32_t* es = ent_s + (size_t)b * ent_cap;
     if (do_fro) {
+      // |A|_F^2: per-chunk partial in the tile's type, one FP64 add per chunk
+      const TA* tt = tile + (size_t)b * CHUNK * APPLY_TILE_LD;
+      TA part = (TA)0;
       for (int jj = tid; jj < CHUNK; jj += APPLY_THREADS) {
 #pragma unroll 8
         for (int r = 0; r < APPLY_ROWS; ++r) {
-          const double v = (double)t[jj * APPLY_TILE_LD + r];
-          fro_local += v * v;
+          const TA v = tt[jj * APPLY_TILE_LD + r];
+          part += v * v;
         }
       }
+      fro_local += (double)part;
     }
-    const uint32_t j0 = (uint32_t)k * CHUNK;
-    const int64_t* cp = cptr + (int64_t)k * r1;
+    const int base = ss[0].x;
+    const uint32_t* eglob = entoff + __ldg(cptr + (int64_t)k * r1);  // for entries beyond ent_cap
+    // The accumulators need static register indices, so the column loop is
+    // unrolled; each copy is a minimal loop (a few instructions per entry) so
+    // that the unrolled code stays within the instruction cache.
+    if (GENT) es = eglob + base;  // very dense sketches: entries straight from global
 #pragma unroll
     for (int i = 0; i < CPW; ++i) {
-      const int c = cbeg + i;
-      if (c < r1) {
-        int64_t p = __ldg(cp + c);
-        const int64_t pe = __ldg(cp + c + 1);
-        for (; p < pe; ++p) {
-          const uint32_t e = __ldg(ent + p);
-          const uint32_t jj = (e & ~SIGN_BIT) - j0;
-          if (jj >= (uint32_t)CHUNK) continue;  // cannot happen with consistent tables
-          const TACC v = (TACC)t[jj * APPLY_TILE_LD + lane];
-          acc[i] += (e & SIGN_BIT) ? -v : v;
+      const int cl = wc0 + i;
+      if (cl < ncols) {
+        const int2 se = ss[cl];
+        TACC a = (TACC)0;
+        for (int p = se.x - base; p < se.y - base; ++p) {
+          const uint32_t e0 = es[p];
+          a += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
         }
+        acc[i] += a;
       }
     }
     __syncthreads();
@@ -333,27 +428,27 @@ __global__ void __launch_bounds__(APPLY_THREADS)
   __syncwarp();
   for (int r = 0; r < nrows; ++r) {
     for (int i = lane; i < CPW; i += 32) {
-      const int c = cbeg + i;
-      if (c < r1) {
-        const double v = (double)st[r * (CPW + 1) + i] * scale;
-        const TO h = to_out<TO>(v);
+      const int c = c0 + wc0 + i;
+      if (wc0 + i < ncols) {
+        // epilogue arithmetic stays in the accumulator type (FP64 is slow on this part)
+        const TACC v = st[r * (CPW + 1) + i] * (TACC)scale;
+        const TO h = cvt_out<TO>(v);
         out[(row0 + r) * ldo + c] = h;
         // split-precision copy: lo = v - hi, rounded (only for BF16 outputs)
-        if (out_lo) out_lo[(row0 + r) * ldo + c] = to_out<TO>(v - as_double(h));
+        if (out_lo) out_lo[(row0 + r) * ldo + c] = cvt_out<TO>(v - (TACC)as_double(h));
       }
     }
   }
   if (do_fro) {
-    // block reduction of fro_local
     for (int o = 16; o > 0; o >>= 1) fro_local += __shfl_xor_sync(0xFFFFFFFFu, fro_local, o);
     __syncthreads();
     double* red = reinterpret_cast<double*>(smem_raw);
     if (lane == 0) red[warp] = fro_local;
     __syncthreads();
     if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < APPLY_WARPS; ++w) s += red[w];
-      atomicAdd(fro2, s);
+      double sum = 0.0;
+      for (int w = 0; w < APPLY_WARPS; ++w) sum += red[w];
+      atomicAdd(fro2, sum);
     }
   }
 }
@@ -408,22 +503,33 @@ template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
 static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda, TO* out,
                         int64_t ldo, double* fro2, cudaStream_t st, TO* out_lo = nullptr) {
   const int64_t nch = nchunks_of(S->n);
-  const int cgsz = APPLY_WARPS * CPW;
-  const int col_groups = (int)cdiv(S->r1, cgsz);
+  constexpr int CG = APPLY_WARPS * CPW;
+  const int col_groups = (int)cdiv(S->r1, CG);
   const int64_t row_blocks = cdiv(m, APPLY_ROWS);
   const int64_t grid = row_blocks * col_groups;
   if (grid > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
-  size_t tile_bytes = (size_t)NBUF * CHUNK * APPLY_TILE_LD * sizeof(TA);
-  size_t epi_bytes = (size_t)APPLY_WARPS * APPLY_ROWS * (CPW + 1) * sizeof(TACC);
-  size_t smem = tile_bytes > epi_bytes ? tile_bytes : epi_bytes;
-  auto kern = k_sketch_apply<TA, TACC, TO, CPW, NBUF>;
-  SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t tile_bytes = (size_t)NBUF * CHUNK * APPLY_TILE_LD * sizeof(TA);
+  const size_t seg_bytes = (size_t)NBUF * CG * sizeof(int2);
+  const size_t epi_bytes = (size_t)APPLY_WARPS * APPLY_ROWS * (CPW + 1) * sizeof(TACC);
+  // all entries of one chunk (at most CHUNK * s) are staged when they fit;
+  // otherwise the kernel reads them from global memory
+  const size_t budget = 225 * 1024;
+  int ent_cap = CHUNK * (S->kind == SPM_SKETCH_IDENTITY ? 1 : S->s);
+  const bool gent = tile_bytes + seg_bytes + (size_t)NBUF * ent_cap * 4 > budget;
+  if (gent) ent_cap = 0;
+  size_t smem = tile_bytes + seg_bytes + (size_t)NBUF * ent_cap * 4;
+  if (epi_bytes > smem) smem = epi_bytes;
   const double scale = (S->kind == SPM_SKETCH_IDENTITY) ? 1.0 : 1.0 / sqrt((double)S->s);
-  kern<<<(unsigned)grid, APPLY_THREADS, smem, st>>>(A, m, S->n, lda, (int)S->r1, (int)nch,
-                                                   S->bucket_ptr, S->bucket_ent, out, ldo,
-                                                   col_groups, scale, fro2, out_lo);
-  SPM_LAUNCH_CHECK();
-  return SPM_OK;
+  auto go = [&](auto kern) -> int {
+    SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, APPLY_THREADS, smem, st>>>(A, m, S->n, lda, (int)S->r1, (int)nch,
+                                                     S->bucket_ptr, S->seg, S->entoff, out, ldo,
+                                                     col_groups, scale, fro2, out_lo, ent_cap);
+    SPM_LAUNCH_CHECK();
+    return SPM_OK;
+  };
+  if (gent) return go(k_sketch_apply<TA, TACC, TO, CPW, NBUF, true>);
+  return go(k_sketch_apply<TA, TACC, TO, CPW, NBUF, false>);
 }
 
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
@@ -512,6 +618,8 @@ int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64
   if (cudaMallocAsync((void**)&S->bucket_ent, nnz * sizeof(uint32_t), st) != cudaSuccess) return fail(SPM_ENOMEM);
   if (cudaMallocAsync((void**)&S->bucket_ptr, (nch * r1 + 1) * sizeof(int64_t), st) != cudaSuccess)
     return fail(SPM_ENOMEM);
+  if (cudaMallocAsync((void**)&S->seg, nch * r1 * sizeof(int2), st) != cudaSuccess) return fail(SPM_ENOMEM);
+  if (cudaMallocAsync((void**)&S->entoff, nnz * sizeof(uint32_t), st) != cudaSuccess) return fail(SPM_ENOMEM);
   if (kind == SPM_SKETCH_IDENTITY) {
     const int64_t blocks = cdiv(max64(n, 1), 256);
     k_sketch_identity<<<(unsigned)min64(blocks, 65535 * 16), 256, 0, st>>>(
@@ -532,6 +640,12 @@ int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64
     k_set_i64<<<1, 1, 0, st>>>(S->bucket_ptr + nch * r1, nnz);
     if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
   }
+  {
+    const int64_t work = max64(nnz, nch * r1);
+    k_apply_tables<<<(unsigned)min64(cdiv(work, 256), 152 * 16), 256, 0, st>>>(
+        nnz, (int)r1, (int)nch, S->bucket_ptr, S->bucket_ent, S->seg, S->entoff);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+  }
   *out = S;
   return SPM_OK;
 }
@@ -542,6 +656,8 @@ int spm_sketch_destroy(spm_sketch* S) {
   if (S->signs) cudaFreeAsync(S->signs, S->stream);
   if (S->bucket_ent) cudaFreeAsync(S->bucket_ent, S->stream);
   if (S->bucket_ptr) cudaFreeAsync(S->bucket_ptr, S->stream);
+  if (S->seg) cudaFreeAsync(S->seg, S->stream);
+  if (S->entoff) cudaFreeAsync(S->entoff, S->stream);
   delete S;
   return SPM_OK;
 }

@@ -36,13 +36,14 @@ class Opts(ctypes.Structure):
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("want_timing", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    _fields_ = [("want_timing", ctypes.c_int32), ("eig_sweeps", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("cholqr_passes", ctypes.c_int32),
                 ("resid_est", ctypes.c_double), ("fro_a", ctypes.c_double),
                 ("stage_ms", ctypes.c_float * 8)]
 
     def as_dict(self):
         return {"device_status": self.device_status, "cholqr_passes": self.cholqr_passes,
+                "eig_sweeps": self.eig_sweeps,
                 "resid_est": self.resid_est, "fro_a": self.fro_a,
                 "stage_ms": {k: float(v) for k, v in zip(STAGES, self.stage_ms)}}
 
@@ -284,3 +285,66 @@ def gemm_bf16_noalloc(A_list, B_list, M, N, K, D, a_mn=False, b_mn=False, splitk
     _check(fn(M, N, K, npass, Ap, A_list[0].stride(0), int(a_mn), Bp, B_list[0].stride(0),
               int(b_mn), _ptr(D), D.stride(0), int(splitk), _stream()), "spm_gemm_bf16_noalloc")
     return D
+
+
+# ---------------------------------------------------------------- learned selector
+MLP_IN, MLP_OUT, MLP_PARAMS = 8, 15, 9871
+CANDIDATES = [(q, c) for q in range(5) for c in (2, 4, 8)]   # output index 3 q + c_idx
+
+
+def _fn(name, args, res=I32):
+    f = getattr(lib(), name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+def mlp_forward(params, X):
+    Y = torch.empty(X.shape[0], MLP_OUT, device="cuda", dtype=torch.float32)
+    f = _fn("spm_mlp_forward", [VP, VP, I64, VP, VP])
+    _check(f(_ptr(params), _ptr(X), X.shape[0], _ptr(Y), _stream()), "spm_mlp_forward")
+    return Y
+
+
+def mlp_loss_grad(params, X, T, M):
+    grad = torch.empty(MLP_PARAMS, device="cuda", dtype=torch.float32)
+    loss = torch.empty(1, device="cuda", dtype=torch.float32)
+    f = _fn("spm_mlp_loss_grad", [VP, VP, VP, VP, I64, VP, VP, VP])
+    _check(f(_ptr(params), _ptr(X), _ptr(T), _ptr(M), X.shape[0], _ptr(grad), _ptr(loss), _stream()),
+           "spm_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam(params, m, v, grad, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    f = _fn("spm_mlp_adam", [VP, VP, VP, VP, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, VP])
+    _check(f(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), lr, b1, b2, eps, _stream()),
+           "spm_mlp_adam")
+
+
+def selector_features(S, A, r2, omega_seed=43):
+    _require_cuda(A)
+    feat = torch.empty(MLP_IN, device="cuda", dtype=torch.float32)
+    f = _fn("spm_selector_features", [VP, VP, I32, I64, I64, I64, U64, VP, VP])
+    _check(f(S.handle, _ptr(A), _dt(A), A.shape[0], A.stride(0), r2, int(omega_seed), _ptr(feat),
+             _stream()), "spm_selector_features")
+    return feat
+
+
+def rsvd_auto(A, k, target_ratio, params, seed=42, precision=PREC_MIXED, **kw):
+    """RandSVD with (q, r1) picked by the selector network; returns U, sigma, Vt, (q, c), info."""
+    _require_cuda(A)
+    m, n = A.shape
+    o = make_opts(precision, **kw)
+    U = torch.empty(m, k, dtype=A.dtype, device=A.device)
+    sg = torch.empty(k, dtype=A.dtype, device=A.device)
+    Vt = torch.empty(k, n, dtype=A.dtype, device=A.device)
+    choice = (ctypes.c_int32 * 2)()
+    inf = _info(False)
+    f = _fn("spm_rsvd_auto", [VP, I32, I64, I64, I64, I64, ctypes.c_double, VP, U64,
+                              ctypes.POINTER(Opts), VP, I64, VP, VP, I64, ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(Info), VP])
+    _check(f(_ptr(A), _dt(A), m, n, A.stride(0), k, float(target_ratio), _ptr(params), int(seed),
+             ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sg), _ptr(Vt), Vt.stride(0), choice,
+             ctypes.byref(inf), _stream()), "spm_rsvd_auto")
+    return U, sg, Vt, (int(choice[0]), int(choice[1])), inf.as_dict()

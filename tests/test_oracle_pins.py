@@ -287,3 +287,65 @@ def test_gmm_kernel_is_psd_with_unit_diagonal():
     assert np.allclose(np.diag(K), 1.0)
     assert np.linalg.eigvalsh(K).min() > -1e-10
     assert h > 0
+
+
+# ---------------------------------------------------------------- selector network (oracle)
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    p = mlp.init_params(3) * 0.5
+    X = rng.standard_normal((5, mlp.D_IN))
+    T = rng.standard_normal((5, mlp.D_OUT))
+    M = (rng.uniform(size=(5, mlp.D_OUT)) > 0.3).astype(float)
+    loss, g = mlp.loss_grad(p, X, T, M)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (mlp.loss_grad(p + e, X, T, M)[0] - mlp.loss_grad(p - e, X, T, M)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_forward_small_case_by_hand():
+    """Identity-like weights: check the forward pass against a hand evaluation."""
+    from oracle import mlp
+    p = np.zeros(mlp.N_PARAMS)
+    layers = mlp.unpack(p)  # views into p
+    layers[0][0][0, 0] = 2.0      # h1_0 = relu(2 x0 - 1)
+    layers[0][1][0] = -1.0
+    layers[1][0][0, 0] = 1.0      # h2_0 = h1_0
+    layers[2][0][0, 0] = -3.0     # h3_0 = relu(-3 h2_0 + 10)
+    layers[2][1][0] = 10.0
+    layers[3][0][4, 0] = 0.5      # y_4 = 0.5 h3_0 + 7
+    layers[3][1][4] = 7.0
+    x = np.zeros((1, mlp.D_IN))
+    x[0, 0] = 2.0
+    y, _ = mlp.forward(p, x)
+    h1 = max(2 * 2.0 - 1, 0)
+    h3 = max(-3 * h1 + 10, 0)
+    assert y[0, 4] == 0.5 * h3 + 7 and np.count_nonzero(y) == 1
+
+
+def test_adam_first_step_is_sign_times_lr():
+    """With bias correction the first Adam step moves each parameter by lr * g / (|g| + eps)."""
+    from oracle import mlp
+    p = np.arange(6.0)
+    g = np.array([1.0, -2.0, 3.0, -4.0, 0.5, -0.25])
+    p1, m1, v1 = mlp.adam(p, np.zeros(6), np.zeros(6), g, step=1, lr=0.01)
+    assert np.allclose(p1, p - 0.01 * np.sign(g), atol=1e-9)
+
+
+def test_selector_features_closed_form():
+    """Features of a sketch with known singular values s_i = 2^-i."""
+    from oracle import mlp
+    r2 = 8
+    s = 2.0 ** -np.arange(r2)
+    U, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((50, r2)))
+    V, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((r2, r2)))
+    Y0 = (U * s) @ V.T
+    f = mlp.features_from_sketch(Y0, m=50, n=30, r1=32)
+    assert np.isclose(f[0], np.log10(s[1]))
+    assert np.isclose(f[1], np.log10(s[3]))
+    assert np.isclose(f[2], np.log10(s[7]))
+    assert np.isclose(f[3], np.log10(r2 * s[7] ** 2 / np.sum(s ** 2)))
+    assert np.isclose(f[7], 2.0 / 3)

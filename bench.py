@@ -47,6 +47,12 @@ def parse():
     p.add_argument("--final-passes", type=int, default=3)
     p.add_argument("--power-passes", type=int, default=3)
     p.add_argument("--cpu-rows", type=int, default=2048)
+    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched"],
+                   help="rsvd: the 65536 x 16384 RandSVD (default); batched: 512 uneven "
+                        "problems in one graph-captured spm_rsvd_batched call")
+    p.add_argument("--batch", type=int, default=512)
+    p.add_argument("--nstreams", type=int, default=16)
+    p.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"])
     return p.parse_args()
 
 
@@ -163,10 +169,136 @@ def residual(A, U, sg, Vt, chunk=4096):
     return tot ** 0.5
 
 
+def batched_main(a):
+    """512 uneven dense problems (m in [512, 8192], n in [256, 4096] log-uniform,
+    k in [16, 256], sigma ~ i^-alpha or exp(-i/tau)); r1 = 2k, s = 8, q = 2.
+    One step = one replay of the CUDA graph captured around one
+    spm_rsvd_batched call over all problems."""
+    import numpy as np
+    import torch
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import selector as sel
+    from paper_2605_09755_gb300 import workloads as wl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    lib = spm.lib()
+    specs = wl.batch_specs(a.batch)
+    probs, sigmas = [], []
+    for sp in specs:
+        A, sig = sel.make_matrix(sp)
+        r1 = min(2 * sp["k"], sp["n"])
+        probs.append(dict(A=A, k=sp["k"], r1=r1, q=a.q, s=min(a.s, r1), seed=42))
+        sigmas.append(sig)
+    torch.cuda.synchronize()
+    prec = {"mixed": spm.PREC_MIXED, "fp32": spm.PREC_FP32}[a.batch_precision]
+    batch = spm.Batch(probs, precision=prec, nstreams=a.nstreams)
+    for _ in range(a.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    batch.check_status()
+    c0 = lib.spm_launch_count()
+    batch.run()
+    torch.cuda.synchronize()
+    launches = int(lib.spm_launch_count() - c0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.run()
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    batch.check_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    # accuracy: residual / Eckart-Young optimum per problem
+    ratios = []
+    for p, sig, (U, sg, Vt) in zip(probs, sigmas, batch.outputs):
+        opt = float(np.sqrt(np.sum(np.sort(sig)[::-1][p["k"]:] ** 2)))
+        R = p["A"] - (U * sg) @ Vt
+        ratios.append(float(torch.linalg.norm(R.double())) / opt if opt > 0 else 1.0)
+    a_bytes = sum(p["A"].numel() * 4 for p in probs)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach = 2.0 * a_bytes / (ms * 1e-3) / 1e9
+    roof = {"kernel": "whole batch (two passes over every A: A S and Q^T A)", "bound": "hbm",
+            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    # end to end: host copies of every A in, every U, sigma, V^T out, eager call
+    hostA = [p["A"].cpu().pin_memory() for p in probs]
+    hostO = [tuple(t.cpu().pin_memory() for t in o) for o in batch.outputs]
+    e0.record()
+    for hA, p in zip(hostA, probs):
+        p["A"].copy_(hA, non_blocking=True)
+    batch.run()
+    for ho, o in zip(hostO, batch.outputs):
+        for h, d in zip(ho, o):
+            h.copy_(d, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e = {"value": e0.elapsed_time(e1), "unit": "ms", "h2d_bytes_per_step": int(a_bytes),
+           "d2h_bytes_per_step": int(sum(sum(t.numel() * 4 for t in o) for o in batch.outputs))}
+    cpu = None
+    if not a.no_cpu:
+        from oracle import algorithms as alg
+        from oracle import sketch as osk
+        rng = np.random.default_rng(3)
+        sample = sorted(rng.choice(len(probs), size=min(12, len(probs)), replace=False).tolist())
+        work = [float(p["A"].shape[0]) * p["A"].shape[1] * p["k"] for p in probs]
+        t0 = time.perf_counter()
+        for i in sample:
+            p = probs[i]
+            A = p["A"].double().cpu().numpy()
+            n = A.shape[1]
+            alg.rsvd(A, osk.Sketch(n, p["r1"], p["s"], 42), osk.gaussian(p["r1"], p["k"], 43), p["q"],
+                     p["k"])
+        t = (time.perf_counter() - t0) * 1e3
+        scale = sum(work) / sum(work[i] for i in sample)
+        cpu = {"value": t * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle RandSVD of {len(sample)} of the {len(probs)} problems, time "
+                         f"scaled by total m n k ({scale:.1f}x)"}
+    line = {
+        "metric": "time to rank-k approx of a batch of 512 uneven dense matrices", "value": ms,
+        "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32" if prec == spm.PREC_MIXED else "f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"batched RandSVD: {len(probs)} matrices m in [512, 8192], n in "
+                               f"[256, 4096] log-uniform, k in [16, 256], r1 = 2k, s = {a.s}, "
+                               f"q = {a.q}, one CUDA graph replay per step",
+                   "precision": a.batch_precision, "nstreams": a.nstreams,
+                   "l2": f"inputs ({a_bytes / 1e9:.1f} GB) larger than L2; no flush"},
+        "matrices_per_s": len(probs) / (ms * 1e-3), "eager_ms": eager_ms,
+        "accuracy": {"median_ratio_vs_optimal": float(np.median(ratios)),
+                     "max_ratio_vs_optimal": float(np.max(ratios))},
+        "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches * a.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_main(a)
+        return
+    if a.workload == "batched":
+        batched_main(a)
         return
     import numpy as np
     import torch

@@ -62,6 +62,10 @@ extern "C" {
 #define SPM_PREC_MIXED 1  /* BF16 tensor-core products (FP32 accumulate), split-precision
                              (hi+lo BF16) products where accuracy is needed, FP32/FP64
                              small factorisations; A may be SPM_F32 or SPM_F64            */
+#define SPM_PREC_FP32 2   /* every product and factorisation in FP32 on CUDA cores: the
+                             FP64 schedule at single precision (no BF16 rounding; for
+                             small problems whose optimal residual is far below the
+                             BF16 split-product error)                                     */
 
 #define SPM_NSTAGES 8     /* stage timers reported through spm_info                       */
 /* stage indices of spm_info.stage_ms */
@@ -77,8 +81,11 @@ extern "C" {
 typedef struct spm_sketch spm_sketch; /* opaque: device tables of one sketch S */
 
 typedef struct spm_opts {
-  int32_t precision;    /* SPM_PREC_FP64 (default when opts == NULL) or SPM_PREC_MIXED      */
-  int32_t reorth;       /* 1 (default): re-orthonormalise after each A~^T product; 0: none  */
+  int32_t precision;    /* SPM_PREC_FP64 (default when opts == NULL), _MIXED or _FP32       */
+  int32_t reorth;       /* 1 (default): re-orthonormalise Z after each A~^T product; 0: none;
+                           2: also re-orthonormalise Y before each A~^T product, so that no
+                           iterate is worse conditioned than A~ (for steep spectra in FP32 or
+                           mixed precision, where the Gram of A~^T Y would lose the tail)   */
   int32_t final_passes; /* MIXED only: BF16 passes for the final projection Q^T A: 1 or 3
                            (hi*hi + hi*lo + lo*hi); 0 selects the default 3                 */
   int32_t small_fp64;   /* MIXED only: 1 = FP64 Cholesky / eigensolver, 0 (default) = FP32   */
@@ -205,6 +212,33 @@ int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* co
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream);
 
+/* ---- batched Randomized SVD (many uneven problems, one capturable call) ------
+ * One problem: A (m x n, row-major, ld lda, device, dtype of the call), rank k
+ * (the range-finder width r2 = k), sparse sign sketch of size r1 (k <= r1 <= n)
+ * with s non-zeros per row drawn from seed `seed` (Omega from seed + 1), q power
+ * steps (Algorithm 1, then the SVD of B = Q^T A).  Outputs (device, caller-owned):
+ * U (m x k, ld ldu), sigma (k), Vt (k x n, ld ldvt). */
+typedef struct spm_batch_item {
+  const void* A;
+  int64_t m, n, lda, k, r1;
+  int32_t s, q;
+  uint64_t seed;
+  void* U;
+  int64_t ldu;
+  void* sigma;
+  void* Vt;
+  int64_t ldvt;
+} spm_batch_item;
+/* Runs every item of the host array `items` (count >= 0) on `nstreams` side
+ * streams (0 = 16, at most 32) forked from and joined back into `stream`, with
+ * no host synchronisation: the whole call may be captured into one CUDA graph.
+ * Results equal those of separate spm_rsvd calls with the same arguments.
+ * dev_status (device, count int32, may be NULL) receives each problem's device
+ * status (0 or an SPM_E* code); the return value covers host-side checks and
+ * launch errors only.  SPM_EINVAL on any invalid item (nothing is launched). */
+int spm_rsvd_batched(int32_t count, const spm_batch_item* items, int32_t dtype,
+                     const spm_opts* opts, int32_t nstreams, int32_t* dev_status, void* stream);
+
 /* ---- learned (q, sketch size) selector -------------------------------------------
  * A multilayer perceptron (8 -> 64 -> 64 -> 64 -> 15, ReLU) that reads features
  * of the q = 0 sketch and predicts log10(residual / optimal - 1) of the range
@@ -243,6 +277,17 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
                   double target_ratio, const float* params, uint64_t seed, const spm_opts* opts,
                   void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, int32_t* choice,
                   spm_info* info, void* stream);
+
+/* Batched form of spm_rsvd_auto: the q = 0 features of every item (probe sketch
+ * r1 = min(4k, n), s = min(8, r1), seed item.seed, Omega seed item.seed + 1) on side
+ * streams, one network evaluation over the batch, one host read of the predictions
+ * (the only synchronisation), then spm_rsvd_batched with each item's chosen (q, r1):
+ * item.q, item.r1 and item.s are overwritten with the choice.  choices (host, 2 count
+ * int32, may be NULL) receives (q, c) with r1 = c k.  dev_status as in
+ * spm_rsvd_batched.  Needs the tensor-core path (sm_103). */
+int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, double target_ratio,
+                          const float* params, const spm_opts* opts, int32_t nstreams,
+                          int32_t* dev_status, int32_t* choices, void* stream);
 
 /* ---- no-allocation variant of spm_gemm_bf16 ------------------------------------
  * The paper has no counterpart: this entry point exists for callers that may not

@@ -2,8 +2,9 @@
 // Randomized SVD finish, Algorithm 2 (Sketch-Powered Low-Rank Factorization)
 // and Algorithm 3 (Sketch-Powered Nystrom Approximation).
 //
-// Two precision modes share one schedule:
+// Three precision modes share one schedule:
 //   SPM_PREC_FP64  -- every product on CUDA cores in FP64 (the plain form);
+//   SPM_PREC_FP32  -- the same on CUDA cores in FP32;
 //   SPM_PREC_MIXED -- A~ in BF16, power products on tcgen05 tensor cores with
 //                     FP32 accumulation; the products whose accuracy reaches the
 //                     output (CholeskyQR Gram and triangular products, Q^T A,
@@ -28,7 +29,8 @@ struct Call {
   bool small64 = false;
   int final_passes = 3;
   int power_passes = 3;
-  bool reorth = true;
+  bool reorth = true;     // orthonormalise Z = A~^T Y after every A~^T product
+  bool reorth_y = false;  // also orthonormalise Y before every A~^T product
   const void* omega = nullptr;
   int* status = nullptr;
   double* acc = nullptr;  // [0] = |A|_F^2, [1] = |B|_F^2
@@ -114,11 +116,11 @@ static int orth_small_f32(Call& C, float* X, int64_t rows, int64_t c, int64_t ld
   return SPM_OK;
 }
 
-// Shifted CholeskyQR3 of the tall m x c FP32 basis Y on tensor cores: Gram and
-// Y R^{-1} as split-precision (3-pass) BF16 products.  On return Y holds Q and
+// Shifted CholeskyQR (3 passes by default) of the tall m x c FP32 basis Y on
+// tensor cores: Gram and Y R^{-1} as split-precision (3-pass) BF16 products.  On return Y holds Q and
 // (Qhi, Qlo) its BF16 split (row-major, ld pad8(c)).
 static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
-                          __nv_bfloat16* Qhi, __nv_bfloat16* Qlo) {
+                          __nv_bfloat16* Qhi, __nv_bfloat16* Qlo, int passes = 3) {
   const int sdt = C.small64 ? DT_F64 : DT_F32;
   const size_t es = dt_size(sdt);
   const int64_t cp = pad8(c);
@@ -129,7 +131,6 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
   SPM_ALLOC(C.ar, __nv_bfloat16, Lhi, c * cp);
   SPM_ALLOC(C.ar, __nv_bfloat16, Llo, c * cp);
   SPM_ALLOC(C.ar, int, defl, c);
-  const int passes = 3;
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
                        mrowmajor(Qlo, DT_BF16, cp), C.st));
@@ -159,61 +160,85 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
 struct RF {
   int64_t m = 0, r2 = 0;
   double* Q64 = nullptr;       // FP64 mode: m x r2 (ld r2)
-  float* Q32 = nullptr;        // MIXED: m x r2 (ld r2)
+  float* Q32 = nullptr;        // MIXED and FP32: m x r2 (ld r2)
   __nv_bfloat16* Qhi = nullptr;  // MIXED: BF16 split of Q (ld pad8(r2))
   __nv_bfloat16* Qlo = nullptr;
 };
+
+static void store_q(RF& out, double* Y) { out.Q64 = Y; }
+static void store_q(RF& out, float* Y) { out.Q32 = Y; }
+static const double* rf_q(const RF& rf, double*) { return rf.Q64; }
+static const float* rf_q(const RF& rf, float*) { return rf.Q32; }
+static int orth_simt(Call& C, double* X, int64_t rows, int64_t c, int64_t ldx, int passes) {
+  return orth_f64(C, X, rows, c, ldx, passes);
+}
+static int orth_simt(Call& C, float* X, int64_t rows, int64_t c, int64_t ldx, int passes) {
+  return orth_small_f32(C, X, rows, c, ldx, passes);
+}
+
+// Algorithm 1 on CUDA cores in one precision T (FP64: the plain form; FP32:
+// every product and factorisation in FP32).
+template <typename T>
+static int range_finder_simt(Call& C, const spm_sketch* S, const void* A, int64_t m, int64_t lda,
+                             int64_t r2, int q, uint64_t seed, RF& out) {
+  const int64_t r1 = S->r1;
+  const int dt = std::is_same<T, double>::value ? DT_F64 : DT_F32;
+  SPM_ALLOC(C.ar, T, At, m * r1);
+  SPM_ALLOC(C.ar, T, Om, r1 * r2);
+  SPM_ALLOC(C.ar, T, Y, m * r2);
+  SPM_ALLOC(C.ar, T, Z, r1 * r2);
+  {
+    StageScope sc(C.timer, SPM_STAGE_SKETCH);
+    if (C.omega)
+      SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Om, dt, r2), C.st));
+    else
+      SPM_TRY(gaussian_dev(Om, dt, r1, r2, r2, seed, C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_APPLY);
+    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, dt, r1, C.acc, C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_POWER);
+    SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, dt, r1), rowmajor(Om, dt, r2), 0.0,
+                      mrowmajor(Y, dt, r2), C.st));
+  }
+  for (int t = 0; t < q; ++t) {
+    if (C.reorth_y) {
+      StageScope sc(C.timer, SPM_STAGE_ORTH);
+      SPM_TRY(orth_simt(C, Y, m, r2, r2, 2));
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      SPM_TRY(gemm_simt(r1, r2, m, 1.0, transpose(rowmajor(At, dt, r1)),
+                        rowmajor(Y, dt, r2), 0.0, mrowmajor(Z, dt, r2), C.st));
+    }
+    if (C.reorth) {
+      StageScope sc(C.timer, SPM_STAGE_ORTH);
+      SPM_TRY(orth_simt(C, Z, r1, r2, r2, 2));  // shifted pass + one plain pass
+    }
+    {
+      StageScope sc(C.timer, SPM_STAGE_POWER);
+      SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, dt, r1), rowmajor(Z, dt, r2), 0.0,
+                        mrowmajor(Y, dt, r2), C.st));
+    }
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_ORTH);
+    SPM_TRY(orth_simt(C, Y, m, r2, r2, 3));
+    C.cholqr_passes = 3;
+  }
+  store_q(out, Y);
+  return SPM_OK;
+}
 
 static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_t m, int64_t lda,
                              int64_t r2, int q, uint64_t seed, RF& out) {
   const int64_t n = S->n, r1 = S->r1;
   out.m = m;
   out.r2 = r2;
-  if (C.prec == SPM_PREC_FP64) {
-    SPM_ALLOC(C.ar, double, At, m * r1);
-    SPM_ALLOC(C.ar, double, Om, r1 * r2);
-    SPM_ALLOC(C.ar, double, Y, m * r2);
-    SPM_ALLOC(C.ar, double, Z, r1 * r2);
-    {
-      StageScope sc(C.timer, SPM_STAGE_SKETCH);
-      if (C.omega)
-        SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Om, DT_F64, r2), C.st));
-      else
-        SPM_TRY(gaussian_dev(Om, DT_F64, r1, r2, r2, seed, C.st));
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_APPLY);
-      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_F64, r1, C.acc, C.st));
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_POWER);
-      SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, DT_F64, r1), rowmajor(Om, DT_F64, r2), 0.0,
-                        mrowmajor(Y, DT_F64, r2), C.st));
-    }
-    for (int t = 0; t < q; ++t) {
-      {
-        StageScope sc(C.timer, SPM_STAGE_POWER);
-        SPM_TRY(gemm_simt(r1, r2, m, 1.0, transpose(rowmajor(At, DT_F64, r1)),
-                          rowmajor(Y, DT_F64, r2), 0.0, mrowmajor(Z, DT_F64, r2), C.st));
-      }
-      if (C.reorth) {
-        StageScope sc(C.timer, SPM_STAGE_ORTH);
-        SPM_TRY(orth_f64(C, Z, r1, r2, r2, 2));  // shifted pass + one plain pass
-      }
-      {
-        StageScope sc(C.timer, SPM_STAGE_POWER);
-        SPM_TRY(gemm_simt(m, r2, r1, 1.0, rowmajor(At, DT_F64, r1), rowmajor(Z, DT_F64, r2), 0.0,
-                          mrowmajor(Y, DT_F64, r2), C.st));
-      }
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_ORTH);
-      SPM_TRY(orth_f64(C, Y, m, r2, r2, 3));
-      C.cholqr_passes = 3;
-    }
-    out.Q64 = Y;
-    return SPM_OK;
-  }
+  if (C.prec == SPM_PREC_FP64) return range_finder_simt<double>(C, S, A, m, lda, r2, q, seed, out);
+  if (C.prec == SPM_PREC_FP32) return range_finder_simt<float>(C, S, A, m, lda, r2, q, seed, out);
   // ---------------- mixed precision
   const int64_t r1p = pad8(r1), r2p = pad8(r2);
   const int pp = C.power_passes;
@@ -250,11 +275,19 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
     SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
   }
   for (int t = 0; t < q; ++t) {
+    if (C.reorth_y) {
+      // Y <- orth(Y); (Qhi, Qlo) is then its split
+      StageScope sc(C.timer, SPM_STAGE_ORTH);
+      const int keep = C.cholqr_passes;
+      SPM_TRY(orth_big_mixed(C, Y, m, r2, r2, Qhi, Qlo, 2));
+      C.cholqr_passes = keep;
+    }
     {
       // Z = A~^T Y: A-op A~^T (M = r1, K = m) MN-major; B-op Y (N = r2, K = m) MN-major
       StageScope sc(C.timer, SPM_STAGE_POWER);
-      SPM_TRY(split_bf16(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Qhi, DT_BF16, r2p),
-                         mrowmajor(Qlo, DT_BF16, r2p), C.st));
+      if (!C.reorth_y)
+        SPM_TRY(split_bf16(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Qhi, DT_BF16, r2p),
+                           mrowmajor(Qlo, DT_BF16, r2p), C.st));
       SPM_TRY(tc_split(r1, r2, m, At, Alo, r1p, true, Qhi, Qlo, r2p, true, pp, Z, r2, 1, C.st));
     }
     if (C.reorth) {
@@ -285,8 +318,11 @@ static int check_common(const spm_sketch* S, const void* A, int32_t dtype, int64
   if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
   if (m < 1 || lda < S->n || r2 < 1 || r2 > S->r1 || r2 > m || q < 0) return SPM_EINVAL;
   if (o) {
-    if (o->precision != SPM_PREC_FP64 && o->precision != SPM_PREC_MIXED) return SPM_EINVAL;
+    if (o->precision != SPM_PREC_FP64 && o->precision != SPM_PREC_MIXED &&
+        o->precision != SPM_PREC_FP32)
+      return SPM_EINVAL;
     if (o->final_passes != 0 && o->final_passes != 1 && o->final_passes != 3) return SPM_EINVAL;
+    if (o->reorth < 0 || o->reorth > 2) return SPM_EINVAL;
     if (o->power_passes != 0 && o->power_passes != 1 && o->power_passes != 3) return SPM_EINVAL;
   }
   return SPM_OK;
@@ -297,6 +333,7 @@ static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info
   if (o) {
     C.prec = o->precision;
     C.reorth = o->reorth != 0;
+    C.reorth_y = o->reorth == 2;
     C.final_passes = o->final_passes == 0 ? 3 : o->final_passes;
     C.power_passes = o->power_passes == 0 ? 3 : o->power_passes;
     C.small64 = o->small_fp64 != 0;
@@ -341,46 +378,58 @@ static int store_out(int64_t rows, int64_t cols, View src, void* dst, int adt, i
 }
 
 // ------------------------------------------------------------------ RandSVD finish
+// SVD of B = Q^T A on CUDA cores in one precision T.
+template <typename T>
+static int rsvd_finish_simt(Call& C, const void* A, int64_t m, int64_t n, int64_t lda, const RF& rf,
+                            int64_t k, void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt) {
+  const int64_t r2 = rf.r2;
+  const int edt = C.adt;
+  const int dt = std::is_same<T, double>::value ? DT_F64 : DT_F32;
+  const T* Q = rf_q(rf, (T*)nullptr);
+  SPM_ALLOC(C.ar, T, B, r2 * n);
+  SPM_ALLOC(C.ar, T, G, r2 * r2);
+  SPM_ALLOC(C.ar, T, Ut, r2 * r2);
+  SPM_ALLOC(C.ar, T, lam, r2);
+  SPM_ALLOC(C.ar, T, W, r2 * n);
+  SPM_ALLOC(C.ar, double, sig, r2);
+  SPM_ALLOC(C.ar, T, Uo, m * k);
+  {
+    StageScope sc(C.timer, SPM_STAGE_PROJECT);
+    SPM_TRY(gemm_simt(r2, n, m, 1.0, transpose(rowmajor(Q, dt, r2)),
+                      rowmajor(A, edt, lda), 0.0, mrowmajor(B, dt, n), C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_SMALL);
+    SPM_TRY(sumsq(r2, n, rowmajor(B, dt, n), C.acc + 1, C.st));
+    SPM_TRY(gemm_simt(r2, r2, n, 1.0, rowmajor(B, dt, n), transpose(rowmajor(B, dt, n)),
+                      0.0, mrowmajor(G, dt, r2), C.st));
+    SPM_TRY(symmetrize(r2, G, r2, dt, C.st));
+    SPM_TRY(sym_eig(r2, G, r2, Ut, r2, lam, dt, C.status, C.st, C.status + 1));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_FINISH);
+    SPM_TRY(gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(Ut, dt, r2)),
+                      rowmajor(B, dt, n), 0.0, mrowmajor(W, dt, n), C.st));
+    SPM_TRY(norms(r2, n, rowmajor(W, dt, n), false, sig, C.st));
+    SPM_TRY(scale_lines(k, n, mrowmajor(W, dt, n), true, sig, true, C.st));
+    SPM_TRY(gemm_simt(m, k, r2, 1.0, rowmajor(Q, dt, r2), rowmajor(Ut, dt, r2), 0.0,
+                      mrowmajor(Uo, dt, k), C.st));
+    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, dt, k), mrowmajor(W, dt, n), C.st));
+    SPM_TRY(store_out(m, k, rowmajor(Uo, dt, k), U, edt, ldu, C.st));
+    SPM_TRY(store_out(k, n, rowmajor(W, dt, n), Vt, edt, ldvt, C.st));
+    SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
+  }
+  return SPM_OK;
+}
+
 static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda, const RF& rf,
                        int64_t k, void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt) {
   const int64_t r2 = rf.r2;
   const int edt = C.adt;
-  if (C.prec == SPM_PREC_FP64) {
-    SPM_ALLOC(C.ar, double, B, r2 * n);
-    SPM_ALLOC(C.ar, double, G, r2 * r2);
-    SPM_ALLOC(C.ar, double, Ut, r2 * r2);
-    SPM_ALLOC(C.ar, double, lam, r2);
-    SPM_ALLOC(C.ar, double, W, r2 * n);
-    SPM_ALLOC(C.ar, double, sig, r2);
-    SPM_ALLOC(C.ar, double, Uo, m * k);
-    {
-      StageScope sc(C.timer, SPM_STAGE_PROJECT);
-      SPM_TRY(gemm_simt(r2, n, m, 1.0, transpose(rowmajor(rf.Q64, DT_F64, r2)),
-                        rowmajor(A, edt, lda), 0.0, mrowmajor(B, DT_F64, n), C.st));
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_SMALL);
-      SPM_TRY(sumsq(r2, n, rowmajor(B, DT_F64, n), C.acc + 1, C.st));
-      SPM_TRY(gemm_simt(r2, r2, n, 1.0, rowmajor(B, DT_F64, n), transpose(rowmajor(B, DT_F64, n)),
-                        0.0, mrowmajor(G, DT_F64, r2), C.st));
-      SPM_TRY(symmetrize(r2, G, r2, DT_F64, C.st));
-      SPM_TRY(sym_eig(r2, G, r2, Ut, r2, lam, DT_F64, C.status, C.st, C.status + 1));
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_FINISH);
-      SPM_TRY(gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(Ut, DT_F64, r2)),
-                        rowmajor(B, DT_F64, n), 0.0, mrowmajor(W, DT_F64, n), C.st));
-      SPM_TRY(norms(r2, n, rowmajor(W, DT_F64, n), false, sig, C.st));
-      SPM_TRY(scale_lines(k, n, mrowmajor(W, DT_F64, n), true, sig, true, C.st));
-      SPM_TRY(gemm_simt(m, k, r2, 1.0, rowmajor(rf.Q64, DT_F64, r2), rowmajor(Ut, DT_F64, r2), 0.0,
-                        mrowmajor(Uo, DT_F64, k), C.st));
-      SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F64, k), mrowmajor(W, DT_F64, n), C.st));
-      SPM_TRY(store_out(m, k, rowmajor(Uo, DT_F64, k), U, edt, ldu, C.st));
-      SPM_TRY(store_out(k, n, rowmajor(W, DT_F64, n), Vt, edt, ldvt, C.st));
-      SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
-    }
-    return SPM_OK;
-  }
+  if (C.prec == SPM_PREC_FP64)
+    return rsvd_finish_simt<double>(C, A, m, n, lda, rf, k, U, ldu, sigma, Vt, ldvt);
+  if (C.prec == SPM_PREC_FP32)
+    return rsvd_finish_simt<float>(C, A, m, n, lda, rf, k, U, ldu, sigma, Vt, ldvt);
   // ---------------- mixed precision
   const int64_t np_ = pad8(n), r2p = pad8(r2);
   const int sdt = C.small64 ? DT_F64 : DT_F32;
@@ -434,6 +483,25 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     SPM_TRY(store_out(k, n, rowmajor(W, DT_F32, n), Vt, edt, ldvt, C.st));
     SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
   }
+  return SPM_OK;
+}
+
+// spm_rsvd without any host synchronisation: the device status word of the
+// call (0 or an SPM_E* code set by a kernel) is copied to dev_status (device,
+// may be null) instead of being read back, so the call can be captured.
+int rsvd_async(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda, int64_t r2,
+               int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts, void* U, int64_t ldu,
+               void* sigma, void* Vt, int64_t ldvt, int32_t* dev_status, cudaStream_t st) {
+  SPM_TRY(check_common(S, A, dtype, m, lda, r2, q, opts));
+  if (!U || !sigma || !Vt || k < 1 || k > r2 || ldu < k || ldvt < S->n) return SPM_EINVAL;
+  Call C(st);
+  setup_call(C, dtype, opts, nullptr);
+  SPM_TRY(prepare(C));
+  RF rf;
+  SPM_TRY(range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf));
+  SPM_TRY(rsvd_finish(C, A, m, S->n, lda, rf, k, U, ldu, sigma, Vt, ldvt));
+  if (dev_status)
+    SPM_CUDA_TRY(cudaMemcpyAsync(dev_status, C.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return SPM_OK;
 }
 

@@ -1,0 +1,408 @@
+// Cholesky factorisation G = L L^T of a small Gram matrix and the inverse
+// L^{-1}, in one cooperative kernel (the small factorisation of CholeskyQR).
+//
+// The matrix is cut into 64 x 64 tiles; nt = ceil(r / 64).  Per panel p:
+//   * CTA 0 factors the diagonal tile (blocked by 16 inside the tile: a warp
+//     factors each 16 x 16 block in registers, then a panel solve and a
+//     trailing update in shared memory) and inverts it;
+//   * all CTAs form the panel L[ib][p] = G[ib][p] L_pp^{-T} (ib > p);
+//   * all CTAs apply the trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T;
+//     the tile (p + 1, p + 1) goes to CTA 0, which factors it right away.
+// Two bounded grid barriers per panel.  The off-diagonal tiles of L^{-1} then
+// follow by recursive doubling: for a lower-triangular [L11 0; L21 L22],
+//   inv(L)_21 = -inv(L22) (L21 inv(L11)),
+// applied level by level over groups of 1, 2, 4, ... tiles, two products and
+// two barriers per level.
+//
+// Deflation follows the unblocked rule: a pivot (Schur complement diagonal)
+// at or below tol * max(diag G) marks its column deflated; that column of L
+// becomes e_j, the elimination step is skipped and the column of every panel
+// below is zeroed.
+#include <algorithm>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace spm {
+
+static constexpr int CT = 64;
+static constexpr int CLD = CT + 1;
+static constexpr int CTHREADS = 512;
+
+// s = tile (r0.., c0..) of a row-major matrix, zero outside [0, R) x [0, Cc);
+// trans: s[j][i] = M[r0 + i][c0 + j].  Loads bypass L1 (the data may have been
+// written by another CTA since this SM last read it).
+template <typename T>
+__device__ __forceinline__ void ld_tile(T (*s)[CLD], const T* M, int64_t ld, int r0, int c0, int R,
+                                        int Cc, bool trans) {
+  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
+    const int i = e >> 6, j = e & 63;
+    const int gi = r0 + i, gj = c0 + j;
+    const T v = (gi < R && gj < Cc) ? __ldcg(M + (int64_t)gi * ld + gj) : (T)0;
+    if (trans)
+      s[j][i] = v;
+    else
+      s[i][j] = v;
+  }
+}
+
+// acc[v][u] += sum_k Xt[k][row_v] Y[k][col_u]; rows ty, ty + 32; columns tx + 16 u
+template <typename T>
+__device__ __forceinline__ void tile_mma(T acc[2][4], const T (*Xt)[CLD], const T (*Y)[CLD]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll 8
+  for (int k = 0; k < CT; ++k) {
+    const T x0 = Xt[k][ty], x1 = Xt[k][ty + 32];
+    T y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[u] = Y[k][tx + 16 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[0][u] = fma(x0, y[u], acc[0][u]);
+      acc[1][u] = fma(x1, y[u], acc[1][u]);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_zero(T acc[2][4]) {
+#pragma unroll
+  for (int v = 0; v < 2; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[v][u] = (T)0;
+}
+
+// Factor the 64 x 64 tile in a (lower part valid, padded with the identity
+// beyond b) in place into L, and write L^{-1} into inv.  Deflated columns get
+// flag 1 in defl[0..b) (global) and are e_j in L.
+template <typename T>
+__device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl, int* bad) {
+  __shared__ unsigned dfl16;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int o = 0; o < CT; o += 16) {
+    // (1) one warp factors the 16 x 16 diagonal block in registers (lane = row)
+    if (warp == 0) {
+      T row[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) row[c] = (lane < 16 && c <= lane) ? a[o + lane][o + c] : (T)0;
+      unsigned df = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const T d = __shfl_sync(0xFFFFFFFFu, row[c], c);
+        const bool fin = isfinite((double)d);
+        const bool piv = fin && (d > thr);
+        if (!fin && lane == 0) *bad = 1;
+        if (piv) {
+          const T sd = sqrt(d);
+          const T lc = (lane == c) ? sd : ((lane > c) ? row[c] / sd : (T)0);
+          row[c] = lc;
+#pragma unroll
+          for (int k = c + 1; k < 16; ++k) {
+            const T lkc = __shfl_sync(0xFFFFFFFFu, lc, k);
+            if (lane >= k) row[k] -= lc * lkc;
+          }
+        } else {
+          row[c] = (lane == c) ? (T)1 : (T)0;
+          df |= 1u << c;
+        }
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) a[o + lane][o + c] = (c <= lane) ? row[c] : (T)0;
+        if (defl && o + lane < b) defl[o + lane] = (df >> lane) & 1u;
+      }
+      if (lane == 0) dfl16 = df;
+    }
+    __syncthreads();
+    const int nbelow = CT - o - 16;
+    if (nbelow <= 0) break;
+    // (2) panel: rows below solve x L_oo^T = a (forward substitution per row)
+    if (tid < nbelow) {
+      const int i = o + 16 + tid;
+      const unsigned df = dfl16;
+      T x[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) x[c] = a[i][o + c];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        T s = x[c];
+#pragma unroll
+        for (int j = 0; j < c; ++j) s -= x[j] * a[o + c][o + j];
+        x[c] = ((df >> c) & 1u) ? (T)0 : s / a[o + c][o + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a[i][o + c] = x[c];
+    }
+    __syncthreads();
+    // (3) trailing update of the lower part below the block
+    for (int e = tid; e < nbelow * nbelow; e += CTHREADS) {
+      const int ii = e / nbelow, kk = e - ii * nbelow;
+      if (kk > ii) continue;
+      const int i = o + 16 + ii, k = o + 16 + kk;
+      T s = a[i][k];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) s -= a[i][o + c] * a[k][o + c];
+      a[i][k] = s;
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular tile: thread c owns column c and runs the
+  // forward substitution x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii down it
+  // with the column in registers (x_k = 0 above the diagonal comes out of the
+  // same formula); four partial sums shorten the dependent chain.
+  if (tid < CT) {
+    const int c = tid;
+    T x[CT];
+#pragma unroll
+    for (int i = 0; i < CT; ++i) {
+      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+#pragma unroll
+      for (int k = 0; k + 3 < i; k += 4) {
+        s0 = fma(a[i][k], x[k], s0);
+        s1 = fma(a[i][k + 1], x[k + 1], s1);
+        s2 = fma(a[i][k + 2], x[k + 2], s2);
+        s3 = fma(a[i][k + 3], x[k + 3], s3);
+      }
+#pragma unroll
+      for (int k = i & ~3; k < i; ++k) s0 = fma(a[i][k], x[k], s0);
+      const T rhs = ((i == c) ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
+      x[i] = rhs / a[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < CT; ++i) inv[i][c] = x[i];
+  }
+  __syncthreads();
+}
+
+// CTA-wide: factor diagonal tile p of G into G (L) and Li (L^{-1}).
+template <typename T>
+__device__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi, T thr, int* defl,
+                            T (*s0)[CLD], T (*s1)[CLD], int* bad) {
+  const int o = p * CT, b = min(CT, r - o);
+  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
+    const int i = e >> 6, j = e & 63;
+    T v;
+    if (i < b && j < b)
+      v = (j <= i) ? __ldcg(G + (int64_t)(o + i) * ldg + o + j) : (T)0;
+    else
+      v = (i == j) ? (T)1 : (T)0;
+    s0[i][j] = v;
+  }
+  __syncthreads();
+  diag_factor<T>(s0, s1, b, thr, defl ? defl + o : nullptr, bad);
+  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
+    const int i = e >> 6, j = e & 63;
+    if (i < b && j < b) {
+      G[(int64_t)(o + i) * ldg + o + j] = s0[i][j];
+      Li[(int64_t)(o + i) * ldi + o + j] = s1[i][j];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CTHREADS, 1)
+    k_chol_coop(int r, T* __restrict__ G, int64_t ldg, T* __restrict__ Li, int64_t ldi,
+                T* __restrict__ Tm, int64_t ldt, T tol, int* __restrict__ defl,
+                int* __restrict__ status, GridBar gb) {
+  extern __shared__ __align__(16) unsigned char cc_smem[];
+  T(*s0)[CLD] = reinterpret_cast<T(*)[CLD]>(cc_smem);
+  T(*s1)[CLD] = s0 + CT;
+  __shared__ int bad;
+  __shared__ T thr_s;
+  __shared__ T red[CTHREADS / 32];
+  const unsigned nb = gridDim.x;
+  const int cta = blockIdx.x, tid = threadIdx.x;
+  const int nt = (r + CT - 1) / CT;
+  const int ty = tid >> 4, tx = tid & 15;
+  if (tid == 0) bad = 0;
+  if (cta == 0) {
+    T mx = (T)0;
+    for (int i = tid; i < r; i += CTHREADS) mx = fmax(mx, G[(int64_t)i * ldg + i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      T m2 = red[0];
+      for (int w = 1; w < CTHREADS / 32; ++w) m2 = fmax(m2, red[w]);
+      thr_s = tol * m2;
+    }
+    __syncthreads();
+    factor_tile<T>(0, r, G, ldg, Li, ldi, thr_s, defl, s0, s1, &bad);
+  }
+  // strictly upper tiles of L^{-1} are zero
+  for (int t = cta; t < nt * nt; t += nb) {
+    const int ib = t / nt, jb = t - ib * nt;
+    if (jb <= ib) continue;
+    for (int e = tid; e < CT * CT; e += CTHREADS) {
+      const int i = ib * CT + (e >> 6), j = jb * CT + (e & 63);
+      if (i < r && j < r) Li[(int64_t)i * ldi + j] = (T)0;
+    }
+  }
+  if (!grid_sync(gb, nb, status)) return;
+
+  for (int p = 0; p + 1 < nt; ++p) {
+    const int o = p * CT;
+    // panel: L[ib][p] = G[ib][p] inv(L_pp)^T, deflated columns zeroed
+    for (int ib = p + 1 + cta; ib < nt; ib += nb) {
+      ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
+      ld_tile<T>(s1, Li, ldi, o, o, r, r, true);
+      __syncthreads();
+      T acc[2][4];
+      acc_zero(acc);
+      tile_mma<T>(acc, s0, s1);
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = ib * CT + ty + 32 * v, j = o + tx + 16 * u;
+          if (i < r && j < r) G[(int64_t)i * ldg + j] = __ldcg(defl + j) ? (T)0 : acc[v][u];
+        }
+      __syncthreads();
+    }
+    if (!grid_sync(gb, nb, status)) return;
+    // trailing update; tile index t = 0 is the next diagonal tile (CTA 0)
+    const int rest = nt - p - 1;
+    const int ntr = rest * (rest + 1) / 2;
+    int t0, step;
+    if (nb == 1) {
+      t0 = 0;
+      step = 1;
+    } else if (cta == 0) {
+      t0 = 0;
+      step = ntr;  // only tile 0
+    } else {
+      t0 = cta;    // tiles 1.. over CTAs 1..nb-1
+      step = nb - 1;
+    }
+    for (int t = t0; t < ntr; t += step) {
+      // t -> (ib, jb) with p + 1 <= jb <= ib, row-major over the lower triangle
+      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      while (ii * (ii + 1) / 2 > t) --ii;
+      const int jj = t - ii * (ii + 1) / 2;
+      const int ib = p + 1 + ii, jb = p + 1 + jj;
+      ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
+      ld_tile<T>(s1, G, ldg, jb * CT, o, r, r, true);
+      __syncthreads();
+      T acc[2][4];
+      acc_zero(acc);
+      tile_mma<T>(acc, s0, s1);
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
+          if (i < r && j < r && j <= i) {
+            T* g = G + (int64_t)i * ldg + j;
+            *g = __ldcg(g) - acc[v][u];
+          }
+        }
+      __syncthreads();
+      if (nb > 1 && cta == 0) break;
+    }
+    if (cta == 0) factor_tile<T>(p + 1, r, G, ldg, Li, ldi, thr_s, defl, s0, s1, &bad);
+    if (!grid_sync(gb, nb, status)) return;
+  }
+
+  // off-diagonal tiles of L^{-1}, recursive doubling over tile groups
+  for (int h = 1; h < nt; h *= 2) {
+    const int groups = (nt + 2 * h - 1) / (2 * h);
+    const int total = groups * h * h;
+    // Tm[ib][jb] = sum_{kb = jb}^{o + h - 1} L[ib][kb] inv(L)[kb][jb]
+    for (int it = cta; it < total; it += nb) {
+      const int g = it / (h * h), rem = it - g * h * h;
+      const int og = 2 * h * g;
+      const int ib = og + h + rem / h, jb = og + rem % h;
+      if (ib >= nt) continue;
+      T acc[2][4];
+      acc_zero(acc);
+      for (int kb = jb; kb < og + h; ++kb) {
+        ld_tile<T>(s0, G, ldg, ib * CT, kb * CT, r, r, true);
+        ld_tile<T>(s1, Li, ldi, kb * CT, jb * CT, r, r, false);
+        __syncthreads();
+        tile_mma<T>(acc, s0, s1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          Tm[(int64_t)(ib * CT + ty + 32 * v) * ldt + jb * CT + tx + 16 * u] = acc[v][u];
+    }
+    if (!grid_sync(gb, nb, status)) return;
+    // inv(L)[ib][jb] = -sum_{kb = o + h}^{ib} inv(L)[ib][kb] Tm[kb][jb]
+    for (int it = cta; it < total; it += nb) {
+      const int g = it / (h * h), rem = it - g * h * h;
+      const int og = 2 * h * g;
+      const int ib = og + h + rem / h, jb = og + rem % h;
+      if (ib >= nt) continue;
+      T acc[2][4];
+      acc_zero(acc);
+      for (int kb = og + h; kb <= ib; ++kb) {
+        ld_tile<T>(s0, Li, ldi, ib * CT, kb * CT, r, r, true);
+        ld_tile<T>(s1, Tm, ldt, kb * CT, jb * CT, nt * CT, nt * CT, false);
+        __syncthreads();
+        tile_mma<T>(acc, s0, s1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
+          if (i < r && j < r) Li[(int64_t)i * ldi + j] = -acc[v][u];
+        }
+    }
+    if (!grid_sync(gb, nb, status)) return;
+  }
+  if (tid == 0 && bad) set_status(status, DEV_NONFINITE);
+}
+
+// Returns SPM_EUNSUPPORTED (nothing launched) when the cooperative grid does
+// not fit; the caller then takes the multi-launch path.
+template <typename T>
+static int cholesky_inv_coop_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int* defl,
+                               int* status, cudaStream_t st) {
+  const int nt = (int)cdiv(r, CT);
+  const T tol = std::is_same<T, double>::value ? (T)1e-12 : (T)1e-6;
+  int dev = 0, sms = 0, per_sm = 0;
+  SPM_CUDA_TRY(cudaGetDevice(&dev));
+  SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int smem = (int)(2 * CT * CLD * sizeof(T));
+  auto kern = k_chol_coop<T>;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CTHREADS, smem));
+  if (per_sm < 1) return SPM_EUNSUPPORTED;
+  const int want = std::max(1, nt * (nt - 1) / 2 + 1);
+  const int blocks = std::min(want, sms);
+  Arena ar(st);
+  SPM_ALLOC(ar, T, Tm, (int64_t)nt * CT * nt * CT);
+  SPM_ALLOC(ar, unsigned, bar, 2);
+  if (!defl) {
+    defl = ar.alloc<int>(r);
+    if (!defl) return SPM_ENOMEM;
+  }
+  SPM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  GridBar gb{bar, bar + 1};
+  int rr = (int)r;
+  int64_t ldt = (int64_t)nt * CT;
+  T tolv = tol;
+  void* args[] = {(void*)&rr, (void*)&G, (void*)&ldg, (void*)&Li, (void*)&ldi, (void*)&Tm,
+                  (void*)&ldt, (void*)&tolv, (void*)&defl, (void*)&status, (void*)&gb};
+  SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(CTHREADS), args, smem, st));
+  count_launch();
+  return SPM_OK;
+}
+
+int cholesky_inv_coop(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
+                      int* status, cudaStream_t st) {
+  if (r < 1 || r > 8192) return SPM_EUNSUPPORTED;
+  if (dt == DT_F64)
+    return cholesky_inv_coop_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, defl, status, st);
+  if (dt == DT_F32)
+    return cholesky_inv_coop_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, defl, status, st);
+  return SPM_EINVAL;
+}
+
+}  // namespace spm

@@ -139,6 +139,43 @@ struct StageScope {
   ~StageScope() { t.end(); }
 };
 
+// Bounded grid-wide barrier for cooperative kernels: thread 0 of each CTA
+// arrives on a counter and waits (at most ~2^32 clocks) for the generation to
+// change; on expiry it records DEV_TIMEOUT and the caller returns.
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar gb, unsigned nblocks, int* status) {
+  __syncthreads();
+  __shared__ int timed_out;
+  if (threadIdx.x == 0) {
+    timed_out = 0;
+    volatile unsigned* vgen = gb.gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(gb.count, 1u) + 1u;
+    if (arrived == nblocks) {
+      *gb.count = 0;
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > (1ll << 32)) {
+          set_status(status, DEV_TIMEOUT);
+          timed_out = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return timed_out == 0;
+}
+
 }  // namespace spm
 
 // The sketch handle (opaque to C callers).

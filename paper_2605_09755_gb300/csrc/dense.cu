@@ -349,6 +349,9 @@ static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int*
 
 int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
                  int* status, cudaStream_t st) {
+  // one cooperative kernel where the grid fits; the multi-launch path otherwise
+  const int rc = cholesky_inv_coop(r, G, ldg, Linv, ldi, dt, defl, status, st);
+  if (rc != SPM_EUNSUPPORTED) return rc;
   if (dt == DT_F64) return cholesky_inv_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, defl, status, st);
   if (dt == DT_F32) return cholesky_inv_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, defl, status, st);
   return SPM_EINVAL;
@@ -443,40 +446,6 @@ int symmetrize(int64_t r, void* A, int64_t lda, int dt, cudaStream_t st) {
 // One bounded grid barrier separates the phases; the kernel is launched
 // cooperatively so that all CTAs are resident.  A sweep starts with the
 // off-diagonal mass test.
-struct GridBar {
-  unsigned* count;
-  unsigned* gen;
-};
-
-__device__ __forceinline__ bool grid_sync(GridBar gb, unsigned nblocks, int* status) {
-  __syncthreads();
-  __shared__ int timed_out;
-  if (threadIdx.x == 0) {
-    timed_out = 0;
-    volatile unsigned* vgen = gb.gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(gb.count, 1u) + 1u;
-    if (arrived == nblocks) {
-      *gb.count = 0;
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (clock64() - t0 > (1ll << 32)) {
-          set_status(status, DEV_TIMEOUT);
-          timed_out = 1;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return timed_out == 0;
-}
-
 __device__ __forceinline__ int rr_player(int pos, int r, int np) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (np - 1));
 }

@@ -71,6 +71,10 @@ int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStrea
 // and Linv = L^{-1} (row-major, ldi).  dt: F32 or F64.  Breakdown -> status.
 // Deflated columns (pivot <= tol * max diag) are flagged in defl[r] (may be
 // nullptr) and get a unit L column; see fill_deflated.
+// Cholesky + inverse in one cooperative kernel (r <= 8192); SPM_EUNSUPPORTED
+// when it cannot be launched.
+int cholesky_inv_coop(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
+                      int* status, cudaStream_t st);
 int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
                  int* status, cudaStream_t st);
 // Replace flagged columns of X (rows x c) by random Gaussian columns.

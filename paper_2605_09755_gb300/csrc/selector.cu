@@ -13,6 +13,9 @@
 //   log2(r1/r2)/3.
 #include <math.h>
 
+#include <functional>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -20,6 +23,8 @@
 namespace spm {
 
 int mlp_forward_dev(const float* params, const float* X, int64_t batch, float* Y, cudaStream_t st);
+int on_side_streams(int count, const int* order, int ns, cudaStream_t st,
+                    const std::function<int(int, cudaStream_t)>& body);
 
 __global__ void k_selector_features(const float* __restrict__ lam, int r2, double m, double n,
                                     double r1, float* __restrict__ feat) {
@@ -45,6 +50,29 @@ __global__ void k_selector_features(const float* __restrict__ lam, int r2, doubl
 }
 
 static int64_t pad8s(int64_t x) { return round_up(x, 8); }
+
+// The cheapest candidate predicted to reach the target; cost ~ (2q + 1) r1 for
+// the power products, ties broken towards smaller q; if no candidate is
+// predicted to reach it, the one with the smallest predicted error.
+void choose_candidate(const float* pred, double target_ratio, int* q_out, int* c_out) {
+  const double thr = log10(target_ratio - 1.0);
+  const int cs[3] = {2, 4, 8};
+  int best = -1, best_any = 0;
+  double best_cost = 1e300;
+  for (int q = 0; q <= 4; ++q)
+    for (int c = 0; c < 3; ++c) {
+      const int idx = 3 * q + c;
+      if (pred[idx] < pred[best_any]) best_any = idx;
+      const double cost = (2.0 * q + 1.0) * cs[c];
+      if (pred[idx] <= thr && cost < best_cost) {
+        best_cost = cost;
+        best = idx;
+      }
+    }
+  if (best < 0) best = best_any;
+  *q_out = best / 3;
+  *c_out = cs[best % 3];
+}
 
 int selector_features_dev(const spm_sketch* S, const void* A, int adt, int64_t m, int64_t lda,
                           int64_t r2, uint64_t seed, float* feat, cudaStream_t st) {
@@ -123,25 +151,8 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
     spm_sketch_destroy(P);
     return rc;
   }
-  // cheapest candidate predicted to reach the target; cost ~ (2q + 1) r1 for
-  // the power products, ties broken towards smaller q; if no candidate is
-  // predicted to reach it, the one with the smallest predicted error
-  const double thr = log10(target_ratio - 1.0);
-  const int cs[3] = {2, 4, 8};
-  int best = -1, best_any = 0;
-  double best_cost = 1e300;
-  for (int q = 0; q <= 4; ++q)
-    for (int c = 0; c < 3; ++c) {
-      const int idx = 3 * q + c;
-      if (pred[idx] < pred[best_any]) best_any = idx;
-      const double cost = (2.0 * q + 1.0) * cs[c];
-      if (pred[idx] <= thr && cost < best_cost) {
-        best_cost = cost;
-        best = idx;
-      }
-    }
-  if (best < 0) best = best_any;
-  const int q = best / 3, c = cs[best % 3];
+  int q = 0, c = 2;
+  choose_candidate(pred, target_ratio, &q, &c);
   int64_t r1 = c * k;
   if (r1 > n) r1 = n;
   if (choice) {
@@ -157,6 +168,77 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
   rc = spm_rsvd(S, A, dtype, m, lda, k, q, seed + 1, k, opts, U, ldu, sigma, Vt, ldvt, info, stream);
   spm_sketch_destroy(S);
   return rc;
+}
+
+int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, double target_ratio,
+                          const float* params, const spm_opts* opts, int32_t nstreams,
+                          int32_t* dev_status, int32_t* choices, void* stream) {
+  if (count < 0 || (count > 0 && !items) || !params || !(target_ratio > 1.0) || nstreams < 0 ||
+      nstreams > 32)
+    return SPM_EINVAL;
+  if (dtype != SPM_F32 && dtype != SPM_F64) return SPM_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    const spm_batch_item& it = items[i];
+    if (!it.A || !it.U || !it.sigma || !it.Vt || it.m < 1 || it.n < 1 || it.lda < it.n ||
+        it.k < 1 || it.k > it.m || it.k > it.n || it.ldu < it.k || it.ldvt < it.n)
+      return SPM_EINVAL;
+  }
+  if (count == 0) return SPM_OK;
+  if (!tc_available()) return SPM_ECUDA;
+  cudaStream_t st = as_stream(stream);
+  const int ns = nstreams == 0 ? 16 : nstreams;
+  const int adt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  // probe sketches: r1 = 4k (at most n), s = 8 (at most r1), one per distinct shape and seed
+  std::map<std::tuple<int64_t, int64_t, uint64_t>, spm_sketch*> probes;
+  std::vector<spm_sketch*> of(count, nullptr);
+  int rc = SPM_OK;
+  for (int i = 0; i < count && rc == SPM_OK; ++i) {
+    const spm_batch_item& it = items[i];
+    const int64_t r1p = std::min<int64_t>(4 * it.k, it.n);
+    const auto key = std::make_tuple(it.n, r1p, it.seed);
+    auto f = probes.find(key);
+    if (f == probes.end()) {
+      spm_sketch* P = nullptr;
+      rc = spm_sketch_create(&P, it.n, r1p, (int32_t)std::min<int64_t>(8, r1p), it.seed,
+                             SPM_SKETCH_SPARSE_SIGN, st);
+      if (rc == SPM_OK) probes[key] = of[i] = P;
+    } else {
+      of[i] = f->second;
+    }
+  }
+  std::vector<float> pred((size_t)count * SPM_MLP_OUT);
+  {
+    Arena ar(st);
+    float* feat = ar.alloc<float>((int64_t)count * SPM_MLP_IN);
+    float* out = ar.alloc<float>((int64_t)count * SPM_MLP_OUT);
+    if (rc == SPM_OK && (!feat || !out)) rc = SPM_ENOMEM;
+    if (rc == SPM_OK)
+      rc = on_side_streams(count, nullptr, ns, st, [&](int i, cudaStream_t s) {
+        const spm_batch_item& it = items[i];
+        return selector_features_dev(of[i], it.A, adt, it.m, it.lda, it.k, it.seed + 1,
+                                     feat + (int64_t)i * SPM_MLP_IN, s);
+      });
+    if (rc == SPM_OK) rc = mlp_forward_dev(params, feat, count, out, st);
+    if (rc == SPM_OK && cudaMemcpyAsync(pred.data(), out, pred.size() * sizeof(float),
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = SPM_ECUDA;
+    if (rc == SPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPM_ECUDA;
+  }
+  for (auto& kv : probes) spm_sketch_destroy(kv.second);
+  if (rc != SPM_OK) return rc;
+  for (int i = 0; i < count; ++i) {
+    spm_batch_item& it = items[i];
+    int q = 0, c = 2;
+    choose_candidate(pred.data() + (size_t)i * SPM_MLP_OUT, target_ratio, &q, &c);
+    it.q = q;
+    it.r1 = std::min<int64_t>((int64_t)c * it.k, it.n);
+    it.s = (int32_t)std::min<int64_t>(8, it.r1);
+    if (choices) {
+      choices[2 * i] = q;
+      choices[2 * i + 1] = c;
+    }
+  }
+  return spm_rsvd_batched(count, items, dtype, opts, nstreams, dev_status, stream);
 }
 
 }  // extern "C"

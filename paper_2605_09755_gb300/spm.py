@@ -14,7 +14,7 @@ from . import _build
 
 F32, F64 = 0, 1
 SPARSE_SIGN, IDENTITY = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
 STAGES = ("sketch", "apply", "power", "orth", "project", "small", "finish", "other")
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
@@ -186,7 +186,7 @@ def sketch_apply_t(S, X):
 
 def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False, omega=None,
               power_passes=3):
-    o = Opts(int(precision), int(bool(reorth)), int(final_passes), int(bool(small_fp64)),
+    o = Opts(int(precision), int(reorth), int(final_passes), int(bool(small_fp64)),
              int(power_passes), 0, None)
     if omega is not None:
         o.omega = omega.data_ptr()
@@ -348,3 +348,86 @@ def rsvd_auto(A, k, target_ratio, params, seed=42, precision=PREC_MIXED, **kw):
              ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sg), _ptr(Vt), Vt.stride(0), choice,
              ctypes.byref(inf), _stream()), "spm_rsvd_auto")
     return U, sg, Vt, (int(choice[0]), int(choice[1])), inf.as_dict()
+
+
+# ---------------------------------------------------------------- batched RandSVD
+class BatchItem(ctypes.Structure):
+    _fields_ = [("A", VP), ("m", I64), ("n", I64), ("lda", I64), ("k", I64), ("r1", I64),
+                ("s", I32), ("q", I32), ("seed", U64), ("U", VP), ("ldu", I64), ("sigma", VP),
+                ("Vt", VP), ("ldvt", I64)]
+
+
+class Batch:
+    """A prepared batch of RandSVD problems with preallocated outputs.
+
+    problems: list of dicts {A (cuda m x n), k, r1, q, s=8, seed=42}.  run()
+    issues one spm_rsvd_batched call on the current stream; it may be captured
+    with torch.cuda.graph and replayed.  outputs[i] = (U, sigma, Vt), status =
+    device int32 per problem.
+    """
+
+    def __init__(self, problems, precision=PREC_MIXED, nstreams=0, **kw):
+        self.items = (BatchItem * len(problems))()
+        self.outputs = []
+        self.inputs = []
+        dt = None
+        dev = None
+        for i, p in enumerate(problems):
+            A = p["A"]
+            _require_cuda(A)
+            if A.stride(1) != 1:
+                raise ValueError("A must be row-major")
+            d = _dt(A)
+            if dt is not None and d != dt:
+                raise ValueError("all problems of a batch share one dtype")
+            dt, dev = d, A.device
+            m, n = A.shape
+            k = p["k"]
+            U = torch.empty(m, k, dtype=A.dtype, device=A.device)
+            sg = torch.empty(k, dtype=A.dtype, device=A.device)
+            Vt = torch.empty(k, n, dtype=A.dtype, device=A.device)
+            self.items[i] = BatchItem(A.data_ptr(), m, n, A.stride(0), k, p.get("r1", min(2 * k, n)),
+                                      p.get("s", 8), p.get("q", 2), p.get("seed", 42), U.data_ptr(), U.stride(0),
+                                      sg.data_ptr(), Vt.data_ptr(), Vt.stride(0))
+            self.inputs.append(A)
+            self.outputs.append((U, sg, Vt))
+        self.dtype = dt if dt is not None else F32
+        self.status = torch.zeros(max(len(problems), 1), dtype=torch.int32,
+                                  device=dev if dev is not None else "cuda")
+        self.opts = make_opts(precision, **kw)
+        self.nstreams = nstreams
+        self._f = _fn("spm_rsvd_batched", [I32, ctypes.POINTER(BatchItem), I32,
+                                           ctypes.POINTER(Opts), I32, VP, VP])
+
+    def run(self):
+        _check(self._f(len(self.outputs), self.items, self.dtype, ctypes.byref(self.opts),
+                       self.nstreams, self.status.data_ptr(), _stream()), "spm_rsvd_batched")
+        return self.outputs
+
+    def run_auto(self, target_ratio, params):
+        """spm_rsvd_batched_auto: pick (q, r1) per problem with the selector network and
+        run the batch; the picks stay in the items, so run() replays them.  Returns the
+        (q, c) pairs (r1 = c k)."""
+        count = len(self.outputs)
+        ch = (ctypes.c_int32 * max(2 * count, 2))()
+        f = _fn("spm_rsvd_batched_auto", [I32, ctypes.POINTER(BatchItem), I32, ctypes.c_double, VP,
+                                          ctypes.POINTER(Opts), I32, VP, ctypes.POINTER(ctypes.c_int32),
+                                          VP])
+        _check(f(count, self.items, self.dtype, float(target_ratio), _ptr(params),
+                 ctypes.byref(self.opts), self.nstreams, self.status.data_ptr(), ch, _stream()),
+               "spm_rsvd_batched_auto")
+        return [(int(ch[2 * i]), int(ch[2 * i + 1])) for i in range(count)]
+
+    def check_status(self):
+        st = self.status.cpu()
+        bad = [(i, int(v)) for i, v in enumerate(st.tolist()[:len(self.outputs)]) if v != 0]
+        if bad:
+            raise RuntimeError(f"spm_rsvd_batched: device status {bad[:5]}")
+
+
+def rsvd_batched(problems, precision=PREC_MIXED, nstreams=0, **kw):
+    """One eager batched call; returns [(U, sigma, Vt)] after checking device status."""
+    b = Batch(problems, precision, nstreams, **kw)
+    out = b.run()
+    b.check_status()
+    return out

@@ -1,0 +1,191 @@
+"""Batched Randomized SVD (spm_rsvd_batched) through the C ABI.
+
+Expected values come from the oracle (FP64 parity, the same bounds as the
+single-problem tests) and from separate single-problem calls of the library,
+which the batched call must reproduce bit for bit: both run the same kernels on
+the same inputs, only on other streams.  Graph capture is checked by replaying a
+captured batch on new matrix contents.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithms as alg
+from oracle import sketch as osk
+from paper_2605_09755_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spm():
+    from paper_2605_09755_gb300 import _build, spm as _spm
+    _build.build()
+    _spm.lib()
+    assert torch.cuda.is_available()
+    return _spm
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _small_specs(count, seed):
+    """Uneven small problems: shapes, ranks, sketch sizes and power counts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.integers(150, 1500))
+        n = int(rng.integers(80, 900))
+        k = int(rng.integers(4, min(64, m, n // 2) + 1))
+        r1 = min(int(k * rng.choice([2, 4, 8])), n)
+        out.append(dict(m=m, n=n, k=k, r1=r1, q=int(rng.integers(0, 4)), s=int(rng.choice([1, 4, 8])),
+                        seed=int(rng.integers(1, 1000)) * 2, kind="poly", par=float(rng.uniform(0.5, 2))))
+    return out
+
+
+def _matrix(spec, dtype):
+    A, sigma = wl.dense_lowrank(spec["m"], spec["n"], wl.batch_sigma(spec), seed=spec["seed"])
+    return A, sigma, torch.tensor(A, dtype=dtype, device="cuda")
+
+
+def _separate(spm, p, prec):
+    S = spm.Sketch(p["A"].shape[1], p["r1"], p.get("s", 8), p["seed"])
+    U, sg, Vt, _ = spm.rsvd(S, p["A"], p["k"], p["q"], p["k"], omega_seed=p["seed"] + 1,
+                            precision=prec)
+    S.close()
+    return U, sg, Vt
+
+
+def test_batched_fp64_matches_oracle(spm):
+    specs = _small_specs(9, seed=21)
+    probs, host_A = [], []
+    for sp in specs:
+        A, sigma, Ad = _matrix(sp, torch.float64)
+        host_A.append((A, sigma))
+        probs.append(dict(A=Ad, k=sp["k"], r1=sp["r1"], q=sp["q"], s=sp["s"], seed=sp["seed"]))
+    outs = spm.rsvd_batched(probs, precision=spm.PREC_FP64, nstreams=4)
+    for sp, (A, sigma), (U, sg, Vt) in zip(specs, host_A, outs):
+        So = osk.Sketch(sp["n"], sp["r1"], sp["s"], sp["seed"])
+        U_o, s_o, Vt_o, _ = alg.rsvd(A, So, osk.gaussian(sp["r1"], sp["k"], sp["seed"] + 1), sp["q"],
+                                     sp["k"])
+        U, sg, Vt = host(U), host(sg), host(Vt)
+        res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+        res = np.linalg.norm(A - (U * sg) @ Vt)
+        assert abs(res - res_o) <= 1e-10 * res_o, sp
+        assert np.max(np.abs(sg - s_o) / s_o) <= 1e-10, sp
+        assert np.linalg.norm(U.T @ U - np.eye(sp["k"])) <= 1e-12
+
+
+def test_batched_mixed_equals_separate_calls(spm):
+    specs = _small_specs(12, seed=22)
+    probs = []
+    for sp in specs:
+        _, _, Ad = _matrix(sp, torch.float32)
+        probs.append(dict(A=Ad, k=sp["k"], r1=sp["r1"], q=sp["q"], s=sp["s"], seed=sp["seed"]))
+    outs = spm.rsvd_batched(probs, precision=spm.PREC_MIXED)
+    for p, got in zip(probs, outs):
+        ref = _separate(spm, p, spm.PREC_MIXED)
+        for g, r in zip(got, ref):
+            assert torch.equal(g, r)
+
+
+def test_batched_graph_capture_replay(spm):
+    """A captured batch replays on new contents of the same input buffers."""
+    specs = _small_specs(6, seed=23)
+    probs = []
+    for sp in specs:
+        _, _, Ad = _matrix(sp, torch.float32)
+        probs.append(dict(A=Ad, k=sp["k"], r1=sp["r1"], q=sp["q"], s=sp["s"], seed=sp["seed"]))
+    batch = spm.Batch(probs, precision=spm.PREC_MIXED, nstreams=3)
+    batch.run()                      # eager warm-up (kernel attributes, stream pool)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    for it in range(2):
+        for j, (sp, p) in enumerate(zip(specs, probs)):
+            sp2 = dict(sp, seed=sp["seed"] + 100 * (it + 1) + j)
+            _, _, Anew = _matrix(sp2, torch.float32)
+            p["A"].copy_(Anew)
+        g.replay()
+        torch.cuda.synchronize()
+        batch.check_status()
+        for p, got in zip(probs, batch.outputs):
+            ref = _separate(spm, p, spm.PREC_MIXED)
+            for a, b in zip(got, ref):
+                assert torch.equal(a, b)
+
+
+def test_batched_full_size_sample_matches_oracle(spm):
+    """The largest, the smallest and the highest-rank problems of the 512-matrix
+    batch (m in [512, 8192], n in [256, 4096], k in [16, 256]) in one batched call
+    in FP64 against the oracle at the same seeds.  (Their spectra fall to 1e-4 and
+    far below within k: FP32 and mixed runs of these problems lose the directions
+    under the single-precision rounding of the Gram matrices, so the bound here is
+    the FP64 one.)"""
+    specs = wl.batch_specs(512)
+    by_size = sorted(range(512), key=lambda i: specs[i]["m"] * specs[i]["n"])
+    pick = [by_size[-1], by_size[0], max(range(512), key=lambda i: specs[i]["k"])]
+    probs, host_A = [], []
+    for i in pick:
+        sp = specs[i]
+        A, sigma = wl.dense_lowrank(sp["m"], sp["n"], wl.batch_sigma(sp), seed=sp["seed"])
+        host_A.append(A)
+        r1 = min(2 * sp["k"], sp["n"])
+        probs.append(dict(A=torch.tensor(A, dtype=torch.float64, device="cuda"), k=sp["k"], r1=r1,
+                          q=2, s=min(8, r1), seed=42))
+    outs = spm.rsvd_batched(probs, precision=spm.PREC_FP64)
+    for p, A, (U, sg, Vt) in zip(probs, host_A, outs):
+        n, k, r1 = A.shape[1], p["k"], p["r1"]
+        U_o, s_o, Vt_o, _ = alg.rsvd(A, osk.Sketch(n, r1, p["s"], 42), osk.gaussian(r1, k, 43), 2, k)
+        U, sg, Vt = host(U), host(sg), host(Vt)
+        res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+        res = np.linalg.norm(A - (U * sg) @ Vt)
+        assert abs(res - res_o) <= 1e-8 * res_o + 1e-13 * np.linalg.norm(A), (A.shape, k, res, res_o)
+        assert np.max(np.abs(sg - s_o)) <= 1e-10 * s_o[0]
+
+
+def test_batched_invalid_and_empty(spm):
+    A = torch.randn(100, 50, device="cuda")
+    with pytest.raises(spm.SpmError):
+        spm.rsvd_batched([dict(A=A, k=10, r1=5, q=1)])           # r1 < k
+    with pytest.raises(spm.SpmError):
+        spm.rsvd_batched([dict(A=A, k=10, r1=60, q=1)])          # r1 > n
+    assert spm.rsvd_batched([]) == []
+
+
+def test_batched_auto_matches_single_problem_selector(spm):
+    """spm_rsvd_batched_auto picks, per problem, what spm_rsvd_auto picks alone, and
+    its outputs equal separate RandSVD calls at the picked (q, r1)."""
+    from paper_2605_09755_gb300 import selector as sel
+    params = sel.load_params()
+    rng = np.random.default_rng(123)
+    probs = []
+    for _ in range(8):
+        spec = sel.random_spec(rng)
+        A, _ = sel.make_matrix(spec)
+        probs.append(dict(A=A, k=spec["k"], seed=42))
+    batch = spm.Batch(probs, precision=spm.PREC_MIXED, nstreams=4)
+    picks = batch.run_auto(1.1, params)
+    torch.cuda.synchronize()
+    batch.check_status()
+    for p, (q, c), got in zip(probs, picks, batch.outputs):
+        _, _, _, (q1, c1), _ = spm.rsvd_auto(p["A"], p["k"], 1.1, params, seed=42)
+        assert (q, c) == (q1, c1)
+        n = p["A"].shape[1]
+        r1 = min(c * p["k"], n)
+        ref = _separate(spm, dict(A=p["A"], k=p["k"], r1=r1, q=q, s=min(8, r1), seed=42),
+                        spm.PREC_MIXED)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+    # the picks stay in the batch: a captured replay reproduces the outputs
+    first = [tuple(t.clone() for t in o) for o in batch.outputs]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, f in zip(batch.outputs, first):
+        for a, b in zip(o, f):
+            assert torch.equal(a, b)

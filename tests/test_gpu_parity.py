@@ -216,6 +216,31 @@ def test_rsvd_mixed_parity(spm, m, n, r1, r2, q):
     assert info["device_status"] == 0
 
 
+@pytest.mark.parametrize("m,n,r1,r2,q", [(2000, 1000, 100, 50, 2), (1500, 1100, 1000, 700, 1)])
+def test_rsvd_fp32_parity(spm, m, n, r1, r2, q):
+    """FP32 on CUDA cores: residual within 1% of the oracle's.
+    With r2 = 700 of sigma_i = 1/i the iterates A~^T Y are conditioned like
+    kappa(A~)^2 ~ 5e5, beyond what an FP32 Gram resolves, so Y is re-orthonormalised
+    before each A~^T product too (reorth = 2)."""
+    A, sigma = wl.plain_fp64(m, n, seed=1001)
+    A = A.astype(np.float32).astype(np.float64)
+    k = r2
+    U_o, s_o, Vt_o, _ = _oracle_rsvd(A, n, r1, 8, r2, q, k)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(n, r1, 8, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A, torch.float32), r2, q, k, precision=spm.PREC_FP32,
+                               reorth=2)
+    U, sg, Vt = host(U), host(sg), host(Vt)
+    res = np.linalg.norm(A - (U * sg) @ Vt)
+    assert res <= 1.01 * res_o, (res, res_o)
+    # sigma from an FP32 Gram eigensolver: absolute error ~ sqrt(r2) u32 sigma_1 times a
+    # modest constant (observed < 15); bound 1e-6 sqrt(r2) sigma_1
+    assert np.max(np.abs(sg - s_o)) <= 1e-6 * np.sqrt(r2) * s_o[0]
+    # FP32 loss of orthogonality grows with k (a few hundred u32 per entry at k = 700)
+    assert np.linalg.norm(U.T @ U - np.eye(k)) <= 3e-5 * k
+    assert info["device_status"] == 0
+
+
 def test_rsvd_mixed_small_fp64_option(spm):
     A, sigma = wl.plain_fp64(1500, 700, seed=11)
     U_o, s_o, Vt_o, _ = _oracle_rsvd(A, 700, 120, 8, 40, 2, 40)

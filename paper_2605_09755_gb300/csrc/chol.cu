@@ -46,6 +46,34 @@ __device__ __forceinline__ void ld_tile(T (*s)[CLD], const T* M, int64_t ld, int
   }
 }
 
+// A tile in registers: thread t holds elements t + 512 u (u = 0..7), row-major.
+template <typename T>
+struct TileRegs {
+  T v[CT * CT / CTHREADS];
+};
+template <typename T>
+__device__ __forceinline__ void ld_regs(TileRegs<T>& t, const T* M, int64_t ld, int r0, int c0, int R,
+                                        int Cc) {
+#pragma unroll
+  for (int u = 0; u < CT * CT / CTHREADS; ++u) {
+    const int e = threadIdx.x + CTHREADS * u;
+    const int gi = r0 + (e >> 6), gj = c0 + (e & 63);
+    t.v[u] = (gi < R && gj < Cc) ? __ldcg(M + (int64_t)gi * ld + gj) : (T)0;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st_regs(T (*s)[CLD], const TileRegs<T>& t, bool trans) {
+#pragma unroll
+  for (int u = 0; u < CT * CT / CTHREADS; ++u) {
+    const int e = threadIdx.x + CTHREADS * u;
+    const int i = e >> 6, j = e & 63;
+    if (trans)
+      s[j][i] = t.v[u];
+    else
+      s[i][j] = t.v[u];
+  }
+}
+
 // acc[v][u] += sum_k Xt[k][row_v] Y[k][col_u]; rows ty, ty + 32; columns tx + 16 u
 template <typename T>
 __device__ __forceinline__ void tile_mma(T acc[2][4], const T (*Xt)[CLD], const T (*Y)[CLD]) {
@@ -72,12 +100,40 @@ __device__ __forceinline__ void acc_zero(T acc[2][4]) {
     for (int u = 0; u < 4; ++u) acc[v][u] = (T)0;
 }
 
+// acc += sum_{kb in [k0, k1)} X(kb) Y(kb) with X(kb) staged transposed; the
+// next pair of tiles is loaded into registers while the current product runs.
+template <typename T, typename FX, typename FY>
+__device__ __forceinline__ void tile_chain(T acc[2][4], int k0, int k1, FX fx, FY fy, T (*s0)[CLD],
+                                           T (*s1)[CLD]) {
+  if (k0 >= k1) return;
+  TileRegs<T> rx, ry;
+  fx(rx, k0);
+  fy(ry, k0);
+  for (int kb = k0; kb < k1; ++kb) {
+    st_regs(s0, rx, true);
+    st_regs(s1, ry, false);
+    __syncthreads();
+    if (kb + 1 < k1) {
+      fx(rx, kb + 1);
+      fy(ry, kb + 1);
+    }
+    tile_mma<T>(acc, s0, s1);
+    __syncthreads();
+  }
+}
+
+// 1 / sqrt(d): the fast reciprocal square root in FP32 (a few ulp; CholeskyQR
+// repeats its passes), the exact quotient in FP64.
+__device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
+__device__ __forceinline__ double rsqrt_t(double d) { return 1.0 / sqrt(d); }
+
 // Factor the 64 x 64 tile in a (lower part valid, padded with the identity
 // beyond b) in place into L, and write L^{-1} into inv.  Deflated columns get
 // flag 1 in defl[0..b) (global) and are e_j in L.
 template <typename T>
 __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl, int* bad) {
   __shared__ unsigned dfl16;
+  __shared__ T rdg[CT];  // 1 / L_ii (1 for a deflated column)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int o = 0; o < CT; o += 16) {
     // (1) one warp factors the 16 x 16 diagonal block in registers (lane = row)
@@ -89,12 +145,13 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const T d = __shfl_sync(0xFFFFFFFFu, row[c], c);
-        const bool fin = isfinite((double)d);
+        const bool fin = isfinite(d);
         const bool piv = fin && (d > thr);
         if (!fin && lane == 0) *bad = 1;
         if (piv) {
-          const T sd = sqrt(d);
-          const T lc = (lane == c) ? sd : ((lane > c) ? row[c] / sd : (T)0);
+          const T isd = rsqrt_t(d);
+          const T lc = (lane == c) ? d * isd : ((lane > c) ? row[c] * isd : (T)0);
+          if (lane == 0) rdg[o + c] = isd;
           row[c] = lc;
 #pragma unroll
           for (int k = c + 1; k < 16; ++k) {
@@ -103,6 +160,7 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
           }
         } else {
           row[c] = (lane == c) ? (T)1 : (T)0;
+          if (lane == 0) rdg[o + c] = (T)1;
           df |= 1u << c;
         }
       }
@@ -128,7 +186,7 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
         T s = x[c];
 #pragma unroll
         for (int j = 0; j < c; ++j) s -= x[j] * a[o + c][o + j];
-        x[c] = ((df >> c) & 1u) ? (T)0 : s / a[o + c][o + c];
+        x[c] = ((df >> c) & 1u) ? (T)0 : s * rdg[o + c];
       }
 #pragma unroll
       for (int c = 0; c < 16; ++c) a[i][o + c] = x[c];
@@ -148,6 +206,7 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
   }
   // inverse of the lower-triangular tile: thread c owns column c and runs the
   // forward substitution x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii down it
+  // (1 / L_ii from the table, so the dependent chain holds no division)
   // with the column in registers (x_k = 0 above the diagonal comes out of the
   // same formula); four partial sums shorten the dependent chain.
   if (tid < CT) {
@@ -166,7 +225,7 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
 #pragma unroll
       for (int k = i & ~3; k < i; ++k) s0 = fma(a[i][k], x[k], s0);
       const T rhs = ((i == c) ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
-      x[i] = rhs / a[i][i];
+      x[i] = rhs * rdg[i];
     }
 #pragma unroll
     for (int i = 0; i < CT; ++i) inv[i][c] = x[i];
@@ -317,13 +376,10 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       if (ib >= nt) continue;
       T acc[2][4];
       acc_zero(acc);
-      for (int kb = jb; kb < og + h; ++kb) {
-        ld_tile<T>(s0, G, ldg, ib * CT, kb * CT, r, r, true);
-        ld_tile<T>(s1, Li, ldi, kb * CT, jb * CT, r, r, false);
-        __syncthreads();
-        tile_mma<T>(acc, s0, s1);
-        __syncthreads();
-      }
+      tile_chain<T>(
+          acc, jb, og + h,
+          [&](TileRegs<T>& t, int kb) { ld_regs(t, (const T*)G, ldg, ib * CT, kb * CT, r, r); },
+          [&](TileRegs<T>& t, int kb) { ld_regs(t, (const T*)Li, ldi, kb * CT, jb * CT, r, r); }, s0, s1);
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll
@@ -339,13 +395,13 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       if (ib >= nt) continue;
       T acc[2][4];
       acc_zero(acc);
-      for (int kb = og + h; kb <= ib; ++kb) {
-        ld_tile<T>(s0, Li, ldi, ib * CT, kb * CT, r, r, true);
-        ld_tile<T>(s1, Tm, ldt, kb * CT, jb * CT, nt * CT, nt * CT, false);
-        __syncthreads();
-        tile_mma<T>(acc, s0, s1);
-        __syncthreads();
-      }
+      tile_chain<T>(
+          acc, og + h, ib + 1,
+          [&](TileRegs<T>& t, int kb) { ld_regs(t, (const T*)Li, ldi, ib * CT, kb * CT, r, r); },
+          [&](TileRegs<T>& t, int kb) {
+            ld_regs(t, (const T*)Tm, ldt, kb * CT, jb * CT, nt * CT, nt * CT);
+          },
+          s0, s1);
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll

@@ -85,6 +85,35 @@ __global__ void k_split(int64_t rows, int64_t cols, const TX* __restrict__ x, in
 
 static int grid_for(int64_t total) { return (int)min64(max64(cdiv(total, 256), 1), 152 * 16); }
 
+// Row-major FP32 -> (hi, lo) BF16 split, four consecutive elements per thread:
+// one 16-byte load and two 8-byte stores, rows from the grid's y dimension
+// (no 64-bit division per element).
+__global__ void k_split_rows4(int64_t rows, int64_t cols4, const float* __restrict__ x, int64_t xrs,
+                              __nv_bfloat16* __restrict__ hi, int64_t hrs, __nv_bfloat16* __restrict__ lo,
+                              int64_t lrs) {
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+    const float4* xr = reinterpret_cast<const float4*>(x + i * xrs);
+    uint2* hr = reinterpret_cast<uint2*>(hi + i * hrs);
+    uint2* lr = reinterpret_cast<uint2*>(lo + i * lrs);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols4;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const float4 v = __ldcs(xr + j);
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
+      const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+      const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+      uint2 hv, lv;
+      hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+      hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+      lv.x = *reinterpret_cast<const uint32_t*>(&l01);
+      lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+      hr[j] = hv;
+      lr[j] = lv;
+    }
+  }
+}
+
 int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return SPM_OK;
   const int g = grid_for(rows * cols);
@@ -106,6 +135,20 @@ int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st) {
 
 int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return SPM_OK;
+  const bool rows4 = x.dt == DT_F32 && x.cs == 1 && hi.cs == 1 && lo.cs == 1 && cols % 4 == 0 &&
+                     x.rs % 4 == 0 && hi.rs % 4 == 0 && lo.rs % 4 == 0 &&
+                     ((uintptr_t)x.p & 15) == 0 && ((uintptr_t)hi.p & 7) == 0 &&
+                     ((uintptr_t)lo.p & 7) == 0;
+  if (rows4) {
+    const int64_t cols4 = cols / 4;
+    const int gx = (int)min64(cdiv(cols4, 256), 64);
+    const int gy = (int)min64(rows, max64(1, (152 * 32) / gx));
+    k_split_rows4<<<dim3(gx, gy), 256, 0, st>>>(rows, cols4, (const float*)x.p, x.rs,
+                                                 (__nv_bfloat16*)hi.p, hi.rs, (__nv_bfloat16*)lo.p,
+                                                 lo.rs);
+    SPM_LAUNCH_CHECK();
+    return SPM_OK;
+  }
   const int g = grid_for(rows * cols);
   if (x.dt == DT_F32)
     k_split<float><<<g, 256, 0, st>>>(rows, cols, (const float*)x.p, x.rs, x.cs,
@@ -362,6 +405,10 @@ int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int d
 template <typename T>
 __global__ void k_fill_deflated(int64_t rows, int64_t c, T* __restrict__ X, int64_t ldx,
                                 const int* __restrict__ defl, uint32_t seed) {
+  // nothing to do unless some column was deflated (the common case)
+  int any = 0;
+  for (int64_t j = threadIdx.x; j < c; j += blockDim.x) any |= defl[j];
+  if (!__syncthreads_or(any)) return;
   const int64_t total = rows * c;
   const double sc = 1.0 / sqrt((double)rows);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -460,6 +507,30 @@ static constexpr int JB = 16;          // block size
 static constexpr int JS = 2 * JB;      // subproblem size
 static constexpr int JLD = JS + 1;     // padded shared-memory row
 static constexpr int JTHREADS = 256;
+static constexpr int JL4 = JS + 4;     // 16-byte aligned rows for vector shared loads
+
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = t0.x;
+  v[1] = t0.y;
+  v[2] = t1.x;
+  v[3] = t1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
 
 template <typename T>
 __device__ __forceinline__ void rot_params(T app, T aqq, T apq, T& c, T& s) {
@@ -471,15 +542,17 @@ __device__ __forceinline__ void rot_params(T app, T aqq, T apq, T& c, T& s) {
   c = (T)1 / sqrt((T)1 + t * t);
   s = t * c;
 }
-// FP32: approximate reciprocal / square-root intrinsics keep the rotation on the
-// critical path short; c = rsqrt(1 + t^2), s = t c stay orthogonal to rounding.
+// FP32: approximate reciprocal intrinsics keep the rotation on the critical
+// path short.  Only the angle depends on them; c = rsqrt(1 + t^2), s = t c
+// keep the rotation orthogonal to rounding.
 template <>
 __device__ __forceinline__ void rot_params<float>(float app, float aqq, float apq, float& c, float& s) {
   c = 1.f;
   s = 0.f;
   if (fabsf(apq) <= 1e-37f) return;
-  const float tau = (aqq - app) * __frcp_rn(2.f * apq);
-  const float t = copysignf(1.f, tau) * __frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
+  const float tau = (aqq - app) * __fdividef(0.5f, apq);
+  const float at = fabsf(tau);
+  const float t = copysignf(at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + sqrtf(fmaf(at, at, 1.f))), tau);
   c = rsqrtf(fmaf(t, t, 1.f));
   s = t * c;
 }
@@ -519,8 +592,10 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
     }
     for (int r = 0; r < JS - 1; ++r) {
       if (tid < JB) {
-        int p, q;
-        rr_pair(tid, r, JS, p, q);
+        // XOR ordering: round x = r + 1 pairs i with i ^ x (all pairs once per
+        // sweep); the low member has a 0 at the top set bit of x
+        const int x = r + 1, hb = 31 - __clz(x);
+        const int p = ((tid >> hb) << (hb + 1)) | (tid & ((1 << hb) - 1)), q = p ^ x;
         T c, s;
         rot_params<T>(M[p][p], M[q][q], M[p][q], c, s);
         pp[tid] = (unsigned char)p;
@@ -652,16 +727,18 @@ __global__ void __launch_bounds__(JTHREADS)
       }
       if (!grid_sync(gb, nb, status)) return;
       // ---------------- phase 2: G <- J^T G J (tile pairs), V <- V J
-      // One warp per item; lane = column of the 32 x 32 tile.
+      // One warp per item; lane c keeps column c of the tile (and of J_j) in
+      // registers, and each product reads its other operand row by row as
+      // broadcast 16-byte shared loads: four multiply-adds per load.
       {
         const int lane = tid & 31, warp = tid >> 5;
-        T(*X)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + (size_t)warp * 3 * sizeof(T) * JS * JLD);
-        T(*Jt)[JLD] = X + JS;
-        T(*Tt)[JLD] = X + 2 * JS;
+        T(*Ja)[JL4] = reinterpret_cast<T(*)[JL4]>(jsm + (size_t)warp * 2 * sizeof(T) * JS * JL4);
+        T(*Tt)[JL4] = Ja + JS;
         const int gitems = hp * (hp + 1) / 2;  // tile pairs i <= j; G_ji is the transpose
         const int vitems = (npad / JS) * hp;
         const int nwarps = (int)nb * (JTHREADS / 32);
         for (int w = (int)blockIdx.x * (JTHREADS / 32) + warp; w < gitems + vitems; w += nwarps) {
+          T x[JS], acc[JS];
           if (w < gitems) {
             // w -> (i, j), i <= j, row-wise over the upper triangle of pair indices
             int i = (int)(((2.0f * hp + 1.0f) - sqrtf((2.0f * hp + 1.0f) * (2.0f * hp + 1.0f) - 8.0f * w)) * 0.5f);
@@ -674,45 +751,49 @@ __global__ void __launch_bounds__(JTHREADS)
             rr_pair(j, r, NB, Pj, Qj);
             const T* Ji = Jbuf + (size_t)i * JS * JS;
             const T* Jj = Jbuf + (size_t)j * JS * JS;
-            const int64_t colj = pair_index(Pj, Qj, lane), coli = pair_index(Pi, Qi, lane);
+            const int64_t colj = pair_index(Pj, Qj, lane);
+#pragma unroll
             for (int a = 0; a < JS; ++a) {
-              X[a][lane] = G[(int64_t)pair_index(Pi, Qi, a) * ld + colj];
-              Jt[a][lane] = Ji[a * JS + lane];
+              x[a] = G[(int64_t)pair_index(Pi, Qi, a) * ld + colj];  // X[a][c]
+              Ja[a][lane] = Ji[a * JS + lane];
             }
             __syncwarp();
-            // Tt = Ji^T X
-            for (int a0 = 0; a0 < JS; a0 += 8) {
-              T acc[8];
+            // T = Ji^T X:  T[a][c] = sum_l Ji[l][a] X[l][c]
 #pragma unroll
-              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
-              for (int l = 0; l < JS; ++l) {
-                const T xv = X[l][lane];
+            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u] = fma(Jt[l][a0 + u], xv, acc[u]);
+            for (int l = 0; l < JS; ++l)
+#pragma unroll
+              for (int a = 0; a < JS; a += 4) {
+                T v[4];
+                ld4(&Ja[l][a], v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[a + u] = fma(v[u], x[l], acc[a + u]);
               }
 #pragma unroll
-              for (int u = 0; u < 8; ++u) Tt[a0 + u][lane] = acc[u];
-            }
-            __syncwarp();
-            for (int a = 0; a < JS; ++a) Jt[a][lane] = Jj[a * JS + lane];
-            __syncwarp();
-            // X = Tt Jj
-            for (int a0 = 0; a0 < JS; a0 += 8) {
-              T acc[8];
+            for (int a = 0; a < JS; a += 4) st4(&Tt[lane][a], &acc[a]);  // Tt[c][a] = T[a][c]
 #pragma unroll
-              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
-              for (int l = 0; l < JS; ++l) {
-                const T jv = Jt[l][lane];
+            for (int l = 0; l < JS; ++l) x[l] = Jj[l * JS + lane];      // column c of Jj
+            __syncwarp();
+            // X' = T Jj:  X'[a][c] = sum_l T[a][l] Jj[l][c] = sum_l Tt[l][a] Jj[l][c]
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u] = fma(Tt[a0 + u][l], jv, acc[u]);
+            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
+#pragma unroll
+            for (int l = 0; l < JS; ++l)
+#pragma unroll
+              for (int a = 0; a < JS; a += 4) {
+                T v[4];
+                ld4(&Tt[l][a], v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[a + u] = fma(v[u], x[l], acc[a + u]);
               }
 #pragma unroll
-              for (int u = 0; u < 8; ++u) X[a0 + u][lane] = acc[u];
+            for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = acc[a];
+            if (i != j) {
+              const int64_t rowj = pair_index(Pj, Qj, lane);
+#pragma unroll
+              for (int a = 0; a < JS; ++a) G[rowj * ld + pair_index(Pi, Qi, a)] = acc[a];
             }
-            __syncwarp();
-            for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = X[a][lane];
-            if (i != j)
-              for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pj, Qj, a) * ld + coli] = X[lane][a];
             __syncwarp();
           } else {
             const int v = w - gitems;
@@ -721,25 +802,27 @@ __global__ void __launch_bounds__(JTHREADS)
             rr_pair(j, r, NB, Pj, Qj);
             const T* Jj = Jbuf + (size_t)j * JS * JS;
             const int64_t colj = pair_index(Pj, Qj, lane);
-            for (int a = 0; a < JS; ++a) {
-              X[a][lane] = V[(int64_t)(rb * JS + a) * ld + colj];
-              Jt[a][lane] = Jj[a * JS + lane];
-            }
+#pragma unroll
+            for (int a = 0; a < JS; ++a) x[a] = V[(int64_t)(rb * JS + a) * ld + colj];  // X[a][c]
+#pragma unroll
+            for (int a = 0; a < JS; a += 4) st4(&Tt[lane][a], &x[a]);  // Tt[c][a] = X[a][c]
+#pragma unroll
+            for (int l = 0; l < JS; ++l) x[l] = Jj[l * JS + lane];
             __syncwarp();
-            for (int a0 = 0; a0 < JS; a0 += 8) {
-              T acc[8];
+            // X' = X Jj:  X'[a][c] = sum_l Tt[l][a] Jj[l][c]
 #pragma unroll
-              for (int u = 0; u < 8; ++u) acc[u] = (T)0;
-              for (int l = 0; l < JS; ++l) {
-                const T jv = Jt[l][lane];
+            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u] = fma(X[a0 + u][l], jv, acc[u]);
+            for (int l = 0; l < JS; ++l)
+#pragma unroll
+              for (int a = 0; a < JS; a += 4) {
+                T vv[4];
+                ld4(&Tt[l][a], vv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[a + u] = fma(vv[u], x[l], acc[a + u]);
               }
 #pragma unroll
-              for (int u = 0; u < 8; ++u) Tt[a0 + u][lane] = acc[u];
-            }
-            __syncwarp();
-            for (int a = 0; a < JS; ++a) V[(int64_t)(rb * JS + a) * ld + colj] = Tt[a][lane];
+            for (int a = 0; a < JS; ++a) V[(int64_t)(rb * JS + a) * ld + colj] = acc[a];
             __syncwarp();
           }
         }
@@ -814,7 +897,9 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   if (per_sm < 1) return SPM_ECUDA;
   const int hp = NB / 2;
   const int items = hp * (hp + 1) / 2 + (npad / JS) * hp;
-  // one CTA per SM: the grid barrier's arrival count stays small
+  // one CTA per SM: the grid barrier's arrival count stays small (two per SM
+  // measured slower: the barriers and the phase-1 CTAs lose more than the
+  // rotation products gain)
   int blocks = min(items, sms);
   blocks = max(blocks, hp);
   if (blocks > sms * per_sm) return SPM_EUNSUPPORTED;  // too large for one resident grid

@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, 1)
     int2* ss = seg_s + (size_t)b * CG;
     for (int i = tid; i < ncols; i += APPLY_THREADS) cp_async_elem8(ss + i, sg + i);
     const int e_beg = __ldg(&sg[0].x), e_end = __ldg(&sg[ncols - 1].y);
+    // columns past ncols (last group) get empty segments: no bounds test in the loop
+    for (int i = ncols + tid; i < CG; i += APPLY_THREADS) ss[i] = make_int2(e_end, e_end);
     const int cnt = min(e_end - e_beg, ent_cap);
     const uint32_t* src = entoff + __ldg(cptr + (int64_t)k * r1) + e_beg;
     uint32_t* es = ent_s + (size_t)b * ent_cap;
@@ -407,16 +409,16 @@ __global__ void __launch_bounds__(APPLY_THREADS, 1)
     if (GENT) es = eglob + base;  // very dense sketches: entries straight from global
 #pragma unroll
     for (int i = 0; i < CPW; ++i) {
-      const int cl = wc0 + i;
-      if (cl < ncols) {
-        const int2 se = ss[cl];
-        TACC a = (TACC)0;
-        for (int p = se.x - base; p < se.y - base; ++p) {
-          const uint32_t e0 = es[p];
-          a += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
-        }
-        acc[i] += a;
+      const int2 se = ss[wc0 + i];
+      TACC a = (TACC)0;
+      // a segment holds about two entries: a plain loop, not an unrolled one
+      // with a remainder (whose set-up would cost more than the entries)
+#pragma unroll 1
+      for (int p = se.x - base; p < se.y - base; ++p) {
+        const uint32_t e0 = es[p];
+        a += signed_val<TA, TACC>(t[e0 & ~SIGN_BIT], e0);
       }
+      acc[i] += a;
     }
     __syncthreads();
   }

@@ -44,6 +44,7 @@ def random_spec(rng, small=True):
 def make_matrix(spec):
     """A = U diag(sigma) V^T on the device (float32) and its sigma (float64)."""
     sigma = wl.batch_sigma(spec)
+    wl.load_torch_linalg()
     g = torch.Generator(device="cuda").manual_seed(spec["seed"])
     r = sigma.size
     U, Ru = torch.linalg.qr(torch.randn(spec["m"], r, generator=g, device="cuda"))

@@ -27,6 +27,18 @@ import math
 import numpy as np
 
 
+def load_torch_linalg():
+    """Load torch's CUDA linear-algebra library by absolute path before the first
+    device QR (its lazy load by name fails under some profilers' injection)."""
+    import ctypes
+    import os
+
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
 def _rng(seed):
     return np.random.Generator(np.random.PCG64(int(seed)))
 
@@ -78,6 +90,7 @@ def noisy_exp_torch(m, n, seed=1002, noise=1e-3, tau=200.0, device="cuda", chunk
     in row chunks so that no m x n float64 temporary exists.
     """
     import torch
+    load_torch_linalg()
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     sigma = torch.tensor(exp_decay_sigma(min(m, n), tau), dtype=torch.float32, device=device)

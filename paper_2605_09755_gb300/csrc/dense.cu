@@ -479,18 +479,18 @@ int symmetrize(int64_t r, void* A, int64_t lda, int dt, cudaStream_t st) {
 // ------------------------------------------------------------------ Jacobi eig
 // Block cyclic Jacobi for the symmetric eigenproblem G = V diag(lam) V^T.
 //
-// G is padded to NB blocks of JB = 32 (NB even) with zero rows/columns, which
+// G is padded to NB blocks of JB = 16 (NB even) with zero rows/columns, which
 // never couple to the real ones.  A sweep runs NB - 1 rounds of the
 // round-robin ("chess tournament") pairing of the blocks.  In a round:
-//   phase 1: CTA c < NB/2 takes block pair c, loads the 64 x 64 subproblem
+//   phase 1: CTA c < NB/2 takes block pair c, loads the 32 x 32 subproblem
 //            [G_PP G_PQ; G_QP G_QQ] into shared memory and diagonalises it by
-//            cyclic 2 x 2 Jacobi (a few inner sweeps), accumulating the 64 x 64
+//            one cyclic sweep of 2 x 2 rotations, accumulating the 32 x 32
 //            rotation J_c;
-//   phase 2: every CTA applies the rotations as small dense products:
+//   phase 2: every warp applies the rotations as small dense products:
 //            G[i, j] <- J_i^T G[i, j] J_j for every pair of block pairs (each
-//            64 x 64 tile is read and written by one CTA only, so in place), and
+//            32 x 32 tile is read and written by one warp only, so in place), and
 //            V[:, j] <- V[:, j] J_j.
-// One bounded grid barrier separates the phases; the kernel is launched
+// Bounded grid barriers separate the phases; the kernel is launched
 // cooperatively so that all CTAs are resident.  A sweep starts with the
 // off-diagonal mass test.
 __device__ __forceinline__ int rr_player(int pos, int r, int np) {
@@ -635,37 +635,6 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
   }
 }
 
-// C (JS x JS, smem) = op(X) * Y with op = transpose when tx; 256 threads on a
-// 16 x 16 grid, each (JS/16)^2 outputs.
-template <typename T>
-__device__ __forceinline__ void tile_mm(const T (*X)[JLD], const T (*Y)[JLD], T (*C)[JLD], bool tx) {
-  constexpr int R = JS / 16;
-  const int tid = threadIdx.x, ty = tid / 16, tx4 = tid % 16;
-  T acc[R][R];
-#pragma unroll
-  for (int a = 0; a < R; ++a)
-#pragma unroll
-    for (int b = 0; b < R; ++b) acc[a][b] = (T)0;
-#pragma unroll 4
-  for (int l = 0; l < JS; ++l) {
-    T xa[R], yb[R];
-#pragma unroll
-    for (int a = 0; a < R; ++a) xa[a] = tx ? X[l][ty + 16 * a] : X[ty + 16 * a][l];
-#pragma unroll
-    for (int b = 0; b < R; ++b) yb[b] = Y[l][tx4 + 16 * b];
-#pragma unroll
-    for (int a = 0; a < R; ++a)
-#pragma unroll
-      for (int b = 0; b < R; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < R; ++a)
-#pragma unroll
-    for (int b = 0; b < R; ++b) C[ty + 16 * a][tx4 + 16 * b] = acc[a][b];
-  __syncthreads();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(JTHREADS)
     k_block_jacobi(int n, int NB, T* __restrict__ G, T* __restrict__ V, T* __restrict__ Jbuf,
@@ -674,8 +643,6 @@ __global__ void __launch_bounds__(JTHREADS)
   extern __shared__ __align__(16) unsigned char jsm[];
   T(*S0)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm);
   T(*S1)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + sizeof(T) * JS * JLD);
-  T(*S2)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + 2 * sizeof(T) * JS * JLD);
-  T(*S3)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + 3 * sizeof(T) * JS * JLD);
   __shared__ T cs[JB], sn[JB];
   __shared__ double red2[2];
   const unsigned nb = gridDim.x;

@@ -62,7 +62,7 @@ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 // call's stream and released by cudaFreeAsync when the arena dies.
 struct Arena {
   cudaStream_t stream;
-  void* ptrs[64];
+  void* ptrs[128];
   int count = 0;
   bool failed = false;
   explicit Arena(cudaStream_t s) : stream(s) {}
@@ -72,7 +72,7 @@ struct Arena {
   template <typename T>
   T* alloc(int64_t elems) {
     if (elems <= 0) elems = 1;
-    if (count >= 64) { failed = true; return nullptr; }
+    if (count >= 128) { failed = true; return nullptr; }
     void* p = nullptr;
     // round to 256 B so that every TMA base is aligned
     size_t bytes = (size_t)round_up(elems * (int64_t)sizeof(T), 256);

@@ -5,6 +5,7 @@
 // (split-precision conversion, norms, sign convention).
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -506,7 +507,12 @@ __device__ __forceinline__ void rr_pair(int i, int r, int np, int& p, int& q) {
 static constexpr int JB = 16;          // block size
 static constexpr int JS = 2 * JB;      // subproblem size
 static constexpr int JLD = JS + 1;     // padded shared-memory row
-static constexpr int JTHREADS = 256;
+// threads per CTA (512 in FP32 was measured slower: register spills in the
+// rotation products outweigh the single wave of warp items)
+template <typename T>
+struct JT {
+  static constexpr int v = 256;
+};
 static constexpr int JL4 = JS + 4;     // 16-byte aligned rows for vector shared loads
 
 __device__ __forceinline__ void ld4(const float* p, float v[4]) {
@@ -570,15 +576,14 @@ template <typename T>
 __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inner, double tol2) {
   const int tid = threadIdx.x;
   __shared__ double red[2];
-  __shared__ unsigned char pp[JB], qq[JB];
-  for (int e = tid; e < JS * JS; e += JTHREADS) J[e / JS][e % JS] = (e / JS == e % JS) ? (T)1 : (T)0;
+  for (int e = tid; e < JS * JS; e += JT<T>::v) J[e / JS][e % JS] = (e / JS == e % JS) ? (T)1 : (T)0;
   __syncthreads();
   for (int sw = 0; sw < max_inner; ++sw) {
     if (max_inner > 1) {
       if (tid < 2) red[tid] = 0.0;
       __syncthreads();
       double off = 0.0, tot = 0.0;
-      for (int e = tid; e < JS * JS; e += JTHREADS) {
+      for (int e = tid; e < JS * JS; e += JT<T>::v) {
         const double v = (double)M[e / JS][e % JS];
         tot += v * v;
         if (e / JS != e % JS) off += v * v;
@@ -591,24 +596,25 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
       if (done) break;
     }
     for (int r = 0; r < JS - 1; ++r) {
+      // XOR ordering: round x = r + 1 pairs i with i ^ x (all pairs once per
+      // sweep); pair t's low member is t with a 0 inserted at the top set bit
+      // of x.  Indices come from this formula, not from a table, so the loads
+      // of M and J do not wait on index loads.
+      const int x = r + 1, hb = 31 - __clz(x);
+      auto low = [&](int t) { return ((t >> hb) << (hb + 1)) | (t & ((1 << hb) - 1)); };
       if (tid < JB) {
-        // XOR ordering: round x = r + 1 pairs i with i ^ x (all pairs once per
-        // sweep); the low member has a 0 at the top set bit of x
-        const int x = r + 1, hb = 31 - __clz(x);
-        const int p = ((tid >> hb) << (hb + 1)) | (tid & ((1 << hb) - 1)), q = p ^ x;
+        const int p = low(tid), q = p ^ x;
         T c, s;
         rot_params<T>(M[p][p], M[q][q], M[p][q], c, s);
-        pp[tid] = (unsigned char)p;
-        qq[tid] = (unsigned char)q;
         cs[tid] = c;
         sn[tid] = s;
       }
       __syncthreads();
-      for (int w = tid; w < JB * JB; w += JTHREADS) {
+      for (int w = tid; w < JB * JB; w += JT<T>::v) {
         const int bi = w / JB, bj = w % JB;
-        const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
-        const T ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
+        const int pi = low(bi), qi = pi ^ x, pj = low(bj), qj = pj ^ x;
         const T m00 = M[pi][pj], m01 = M[pi][qj], m10 = M[qi][pj], m11 = M[qi][qj];
+        const T ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
         const T t00 = ci * m00 - si * m10, t01 = ci * m01 - si * m11;
         const T t10 = si * m00 + ci * m10, t11 = si * m01 + ci * m11;
         T n00 = cj * t00 - sj * t01, n01 = sj * t00 + cj * t01;
@@ -622,11 +628,11 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
         M[qi][pj] = n10;
         M[qi][qj] = n11;
       }
-      for (int w = tid; w < JS * JB; w += JTHREADS) {
+      for (int w = tid; w < JS * JB; w += JT<T>::v) {
         const int row = w / JB, bj = w % JB;
-        const int pj = pp[bj], qj = qq[bj];
-        const T cj = cs[bj], sj = sn[bj];
+        const int pj = low(bj), qj = pj ^ x;
         const T vp = J[row][pj], vq = J[row][qj];
+        const T cj = cs[bj], sj = sn[bj];
         J[row][pj] = cj * vp - sj * vq;
         J[row][qj] = sj * vp + cj * vq;
       }
@@ -636,7 +642,7 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
 }
 
 template <typename T>
-__global__ void __launch_bounds__(JTHREADS)
+__global__ void __launch_bounds__(JT<T>::v)
     k_block_jacobi(int n, int NB, T* __restrict__ G, T* __restrict__ V, T* __restrict__ Jbuf,
                    int max_sweeps, double tol2, int max_inner, double tol2_inner, GridBar gb,
                    double* __restrict__ offacc, int* __restrict__ status, int* __restrict__ sweeps_out) {
@@ -654,8 +660,8 @@ __global__ void __launch_bounds__(JTHREADS)
   for (; sweep < max_sweeps; ++sweep) {
     // off-diagonal mass
     double off = 0.0, tot = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)JTHREADS + tid; e < (int64_t)npad * npad;
-         e += (int64_t)nb * JTHREADS) {
+    for (int64_t e = blockIdx.x * (int64_t)JT<T>::v + tid; e < (int64_t)npad * npad;
+         e += (int64_t)nb * JT<T>::v) {
       const double v = (double)G[e];
       tot += v * v;
       if (e / npad != e % npad) off += v * v;
@@ -682,14 +688,14 @@ __global__ void __launch_bounds__(JTHREADS)
       for (int c = blockIdx.x; c < hp; c += nb) {
         int P, Q;
         rr_pair(c, r, NB, P, Q);
-        for (int e = tid; e < JS * JS; e += JTHREADS) {
+        for (int e = tid; e < JS * JS; e += JT<T>::v) {
           const int a = e / JS, b = e % JS;
           S0[a][b] = G[(int64_t)pair_index(P, Q, a) * ld + pair_index(P, Q, b)];
         }
         __syncthreads();
         inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
         T* Jc = Jbuf + (size_t)c * JS * JS;
-        for (int e = tid; e < JS * JS; e += JTHREADS) Jc[e] = S1[e / JS][e % JS];
+        for (int e = tid; e < JS * JS; e += JT<T>::v) Jc[e] = S1[e / JS][e % JS];
         __syncthreads();
       }
       if (!grid_sync(gb, nb, status)) return;
@@ -703,8 +709,8 @@ __global__ void __launch_bounds__(JTHREADS)
         T(*Tt)[JL4] = Ja + JS;
         const int gitems = hp * (hp + 1) / 2;  // tile pairs i <= j; G_ji is the transpose
         const int vitems = (npad / JS) * hp;
-        const int nwarps = (int)nb * (JTHREADS / 32);
-        for (int w = (int)blockIdx.x * (JTHREADS / 32) + warp; w < gitems + vitems; w += nwarps) {
+        const int nwarps = (int)nb * (JT<T>::v / 32);
+        for (int w = (int)blockIdx.x * (JT<T>::v / 32) + warp; w < gitems + vitems; w += nwarps) {
           T x[JS], acc[JS];
           if (w < gitems) {
             // w -> (i, j), i <= j, row-wise over the upper triangle of pair indices
@@ -857,7 +863,9 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   int dev = 0, sms = 0, per_sm = 0;
   SPM_CUDA_TRY(cudaGetDevice(&dev));
   SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int smem = (int)((JTHREADS / 32) * 3 * sizeof(T) * JS * JLD);
+  constexpr int JTHREADS = JT<T>::v;
+  // phase 1: 2 JS x JLD tiles; phase 2: per warp 2 JS x JL4 tiles
+  const int smem = (int)std::max(2 * sizeof(T) * JS * JLD, (JTHREADS / 32) * 2 * sizeof(T) * JS * JL4);
   auto kern = k_block_jacobi<T>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JTHREADS, smem));
@@ -867,7 +875,9 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   // one CTA per SM: the grid barrier's arrival count stays small (two per SM
   // measured slower: the barriers and the phase-1 CTAs lose more than the
   // rotation products gain)
-  int blocks = min(items, sms);
+  // (items count warps: small problems take only the CTAs they can fill, which
+  // also keeps their grid barriers cheap and leaves SMs to concurrent work)
+  int blocks = min((items + JTHREADS / 32 - 1) / (JTHREADS / 32), sms);
   blocks = max(blocks, hp);
   if (blocks > sms * per_sm) return SPM_EUNSUPPORTED;  // too large for one resident grid
   const bool is64 = std::is_same<T, double>::value;

@@ -273,15 +273,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (ok && iters > 0) {
       const int row = m0 + quarter * 32 + lane;
       float* D = p.D + (int64_t)blockIdx.z * p.split_stride;
+      if (p.d_cs == 1) {
+        // row-major output: each 32 x 32 block goes through shared memory (the
+        // drained stage ring) so that a warp stores one 128-byte row segment at a time
+        float(*st)[33] = reinterpret_cast<float(*)[33]>(tiles + quarter * 32 * 33 * sizeof(float));
+        const int rbase = m0 + quarter * 32;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-        if (row < p.M) {
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < p.N) D[(int64_t)row * p.d_rs + (int64_t)col * p.d_cs] = p.alpha * __uint_as_float(v[j]);
+          for (int j = 0; j < 32; ++j) st[lane][j] = p.alpha * __uint_as_float(v[j]);
+          __syncwarp();
+          const int col = n0 + c0 + lane;
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r)
+            if (rbase + r < p.M && col < p.N) D[(int64_t)(rbase + r) * p.d_rs + col] = st[r][lane];
+          __syncwarp();
+        }
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+          if (row < p.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = n0 + c0 + j;
+              if (col < p.N) D[(int64_t)row * p.d_rs + (int64_t)col * p.d_cs] = p.alpha * __uint_as_float(v[j]);
+            }
           }
         }
       }

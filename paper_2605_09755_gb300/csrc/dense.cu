@@ -641,14 +641,74 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
   }
 }
 
+// Where block X sits in round r: pair index i and half h (0 = the lower block).
+__device__ __forceinline__ void rr_locate(int X, int r, int np, int& i, int& h) {
+  const int pos = (X == 0) ? 0 : (((X - 1 - r) % (np - 1)) + (np - 1)) % (np - 1) + 1;
+  i = min(pos, np - 1 - pos);
+  int P, Q;
+  rr_pair(i, r, np, P, Q);
+  h = (X == P) ? 0 : 1;
+}
+
+// Subproblem of pair c of round r + 1, built from G^(r) and the round-r
+// rotations (the rounds' products G^(r+1) = J^T G^(r) J restricted to the
+// pair's blocks): quadrant (X, Y) = J_iX[:, hX]^T G^(r)[pair iX, pair iY] J_iY[:, hY].
+// Uses the shared tiles T (32 x 33) and W (32 x 17) after S0, S1.
+template <typename T>
+__device__ void build_next_subproblem(const T* __restrict__ Gc, int64_t ld, const T* __restrict__ Jc,
+                                      int c, int r, int NB, T (*S0)[JLD], T (*Tt)[JLD], T (*W)[JB + 1]) {
+  const int tid = threadIdx.x;
+  int P2, Q2;
+  rr_pair(c, r + 1, NB, P2, Q2);
+  int ib[2], hb[2];
+  rr_locate(P2, r, NB, ib[0], hb[0]);
+  rr_locate(Q2, r, NB, ib[1], hb[1]);
+  int Pb[2], Qb[2];
+  rr_pair(ib[0], r, NB, Pb[0], Qb[0]);
+  rr_pair(ib[1], r, NB, Pb[1], Qb[1]);
+  // quadrants (0,0), (0,1), (1,1); (1,0) is the transpose of (0,1)
+  for (int qd = 0; qd < 3; ++qd) {
+    const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
+    for (int e = tid; e < JS * JS; e += JT<T>::v) {
+      const int a = e / JS, bb = e % JS;
+      Tt[a][bb] = Gc[(int64_t)pair_index(Pb[X], Qb[X], a) * ld + pair_index(Pb[Y], Qb[Y], bb)];
+    }
+    __syncthreads();
+    // W = T J_iY[:, hY]   (32 x 16)
+    const T* JY = Jc + (size_t)ib[Y] * JS * JS;
+    for (int e = tid; e < JS * JB; e += JT<T>::v) {
+      const int a = e / JB, bb = e % JB;
+      T acc = (T)0;
+#pragma unroll 8
+      for (int l = 0; l < JS; ++l) acc = fma(Tt[a][l], __ldg(JY + l * JS + hb[Y] * JB + bb), acc);
+      W[a][bb] = acc;
+    }
+    __syncthreads();
+    // S0 quadrant = J_iX[:, hX]^T W   (16 x 16)
+    const T* JX = Jc + (size_t)ib[X] * JS * JS;
+    for (int e = tid; e < JB * JB; e += JT<T>::v) {
+      const int a2 = e / JB, bb = e % JB;
+      T acc = (T)0;
+#pragma unroll 8
+      for (int l = 0; l < JS; ++l) acc = fma(__ldg(JX + l * JS + hb[X] * JB + a2), W[l][bb], acc);
+      S0[X * JB + a2][Y * JB + bb] = acc;
+      if (qd == 1) S0[JB + bb][a2] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(JT<T>::v)
-    k_block_jacobi(int n, int NB, T* __restrict__ G, T* __restrict__ V, T* __restrict__ Jbuf,
-                   int max_sweeps, double tol2, int max_inner, double tol2_inner, GridBar gb,
-                   double* __restrict__ offacc, int* __restrict__ status, int* __restrict__ sweeps_out) {
+    k_block_jacobi(int n, int NB, T* __restrict__ G, T* __restrict__ Gb, T* __restrict__ V,
+                   T* __restrict__ Jbuf, int max_sweeps, double tol2, int max_inner,
+                   double tol2_inner, GridBar gb, double* __restrict__ offacc,
+                   int* __restrict__ status, int* __restrict__ sweeps_out) {
   extern __shared__ __align__(16) unsigned char jsm[];
   T(*S0)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm);
-  T(*S1)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm + sizeof(T) * JS * JLD);
+  T(*S1)[JLD] = S0 + JS;
+  T(*Tt2)[JLD] = S0 + 2 * JS;
+  T(*W2)[JB + 1] = reinterpret_cast<T(*)[JB + 1]>(jsm + 3 * sizeof(T) * JS * JLD);
   __shared__ T cs[JB], sn[JB];
   __shared__ double red2[2];
   const unsigned nb = gridDim.x;
@@ -656,13 +716,21 @@ __global__ void __launch_bounds__(JT<T>::v)
   const int npad = NB * JB;
   const int hp = NB / 2;
   const int64_t ld = npad;
+  // CTAs [0, L) build and solve the next round's subproblems while CTAs
+  // [p2_first, nb) apply the current round's rotations (all CTAs when too few)
+  const int L = max(1, min(hp, (int)nb / 2));
+  const int p2_first = ((int)nb > L) ? L : 0;
+  const int nworkers = (int)nb - p2_first, worker = (int)blockIdx.x - p2_first;
+  const size_t jstride = (size_t)hp * JS * JS;
+  T* Gc = G;
+  T* Gn = Gb;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     // off-diagonal mass
     double off = 0.0, tot = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)JT<T>::v + tid; e < (int64_t)npad * npad;
          e += (int64_t)nb * JT<T>::v) {
-      const double v = (double)G[e];
+      const double v = (double)Gc[e];
       tot += v * v;
       if (e / npad != e % npad) off += v * v;
     }
@@ -683,22 +751,35 @@ __global__ void __launch_bounds__(JT<T>::v)
     const double offv = *((volatile double*)&offacc[2 * (sweep & 1)]);
     const double totv = *((volatile double*)&offacc[2 * (sweep & 1) + 1]);
     if (offv <= tol2 * totv) break;
-    for (int r = 0; r < NB - 1; ++r) {
-      // ---------------- phase 1: subproblems
-      for (int c = blockIdx.x; c < hp; c += nb) {
-        int P, Q;
-        rr_pair(c, r, NB, P, Q);
-        for (int e = tid; e < JS * JS; e += JT<T>::v) {
-          const int a = e / JS, b = e % JS;
-          S0[a][b] = G[(int64_t)pair_index(P, Q, a) * ld + pair_index(P, Q, b)];
-        }
-        __syncthreads();
-        inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
-        T* Jc = Jbuf + (size_t)c * JS * JS;
-        for (int e = tid; e < JS * JS; e += JT<T>::v) Jc[e] = S1[e / JS][e % JS];
-        __syncthreads();
+    // round 0 subproblems straight from G
+    for (int c = blockIdx.x; c < hp; c += nb) {
+      int P, Q;
+      rr_pair(c, 0, NB, P, Q);
+      for (int e = tid; e < JS * JS; e += JT<T>::v) {
+        const int a = e / JS, b = e % JS;
+        S0[a][b] = Gc[(int64_t)pair_index(P, Q, a) * ld + pair_index(P, Q, b)];
       }
-      if (!grid_sync(gb, nb, status)) return;
+      __syncthreads();
+      inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
+      T* Jo = Jbuf + (size_t)c * JS * JS;
+      for (int e = tid; e < JS * JS; e += JT<T>::v) Jo[e] = S1[e / JS][e % JS];
+      __syncthreads();
+    }
+    if (!grid_sync(gb, nb, status)) return;
+    for (int r = 0; r < NB - 1; ++r) {
+      const T* Jc = Jbuf + (size_t)(r & 1) * jstride;
+      T* Jn = Jbuf + (size_t)((r + 1) & 1) * jstride;
+      // ---------------- lookahead: round r + 1 subproblems from G^(r) and J^(r)
+      if ((int)blockIdx.x < L && r + 1 < NB - 1) {
+        for (int c = blockIdx.x; c < hp; c += L) {
+          build_next_subproblem<T>(Gc, ld, Jc, c, r, NB, S0, Tt2, W2);
+          inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
+          T* Jo = Jn + (size_t)c * JS * JS;
+          for (int e = tid; e < JS * JS; e += JT<T>::v) Jo[e] = S1[e / JS][e % JS];
+          __syncthreads();
+        }
+      }
+      if ((int)blockIdx.x >= p2_first) {
       // ---------------- phase 2: G <- J^T G J (tile pairs), V <- V J
       // One warp per item; lane c keeps column c of the tile (and of J_j) in
       // registers, and each product reads its other operand row by row as
@@ -709,8 +790,8 @@ __global__ void __launch_bounds__(JT<T>::v)
         T(*Tt)[JL4] = Ja + JS;
         const int gitems = hp * (hp + 1) / 2;  // tile pairs i <= j; G_ji is the transpose
         const int vitems = (npad / JS) * hp;
-        const int nwarps = (int)nb * (JT<T>::v / 32);
-        for (int w = (int)blockIdx.x * (JT<T>::v / 32) + warp; w < gitems + vitems; w += nwarps) {
+        const int nwarps = nworkers * (JT<T>::v / 32);
+        for (int w = worker * (JT<T>::v / 32) + warp; w < gitems + vitems; w += nwarps) {
           T x[JS], acc[JS];
           if (w < gitems) {
             // w -> (i, j), i <= j, row-wise over the upper triangle of pair indices
@@ -722,12 +803,12 @@ __global__ void __launch_bounds__(JT<T>::v)
             int Pi, Qi, Pj, Qj;
             rr_pair(i, r, NB, Pi, Qi);
             rr_pair(j, r, NB, Pj, Qj);
-            const T* Ji = Jbuf + (size_t)i * JS * JS;
-            const T* Jj = Jbuf + (size_t)j * JS * JS;
+            const T* Ji = Jc + (size_t)i * JS * JS;
+            const T* Jj = Jc + (size_t)j * JS * JS;
             const int64_t colj = pair_index(Pj, Qj, lane);
 #pragma unroll
             for (int a = 0; a < JS; ++a) {
-              x[a] = G[(int64_t)pair_index(Pi, Qi, a) * ld + colj];  // X[a][c]
+              x[a] = Gc[(int64_t)pair_index(Pi, Qi, a) * ld + colj];  // X[a][c]
               Ja[a][lane] = Ji[a * JS + lane];
             }
             __syncwarp();
@@ -761,11 +842,11 @@ __global__ void __launch_bounds__(JT<T>::v)
                 for (int u = 0; u < 4; ++u) acc[a + u] = fma(v[u], x[l], acc[a + u]);
               }
 #pragma unroll
-            for (int a = 0; a < JS; ++a) G[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = acc[a];
+            for (int a = 0; a < JS; ++a) Gn[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = acc[a];
             if (i != j) {
               const int64_t rowj = pair_index(Pj, Qj, lane);
 #pragma unroll
-              for (int a = 0; a < JS; ++a) G[rowj * ld + pair_index(Pi, Qi, a)] = acc[a];
+              for (int a = 0; a < JS; ++a) Gn[rowj * ld + pair_index(Pi, Qi, a)] = acc[a];
             }
             __syncwarp();
           } else {
@@ -773,7 +854,7 @@ __global__ void __launch_bounds__(JT<T>::v)
             const int rb = v / hp, j = v % hp;
             int Pj, Qj;
             rr_pair(j, r, NB, Pj, Qj);
-            const T* Jj = Jbuf + (size_t)j * JS * JS;
+            const T* Jj = Jc + (size_t)j * JS * JS;
             const int64_t colj = pair_index(Pj, Qj, lane);
 #pragma unroll
             for (int a = 0; a < JS; ++a) x[a] = V[(int64_t)(rb * JS + a) * ld + colj];  // X[a][c]
@@ -800,9 +881,17 @@ __global__ void __launch_bounds__(JT<T>::v)
           }
         }
       }
+      }
       if (!grid_sync(gb, nb, status)) return;
+      T* tmp = Gc;
+      Gc = Gn;
+      Gn = tmp;
     }
   }
+  // the eigenvalues are read from G's diagonal
+  if (Gc != G)
+    for (int i = blockIdx.x * JT<T>::v + tid; i < npad; i += nb * JT<T>::v)
+      G[(int64_t)i * ld + i] = Gc[(int64_t)i * ld + i];
   if (blockIdx.x == 0 && tid == 0 && sweeps_out) atomicMax(sweeps_out, sweep);
 }
 
@@ -854,7 +943,8 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   Arena ar(st);
   SPM_ALLOC(ar, T, G, (int64_t)npad * npad);
   SPM_ALLOC(ar, T, Vw, (int64_t)npad * npad);
-  SPM_ALLOC(ar, T, Jbuf, (int64_t)(NB / 2) * JS * JS);
+  SPM_ALLOC(ar, T, Gb, (int64_t)npad * npad);            // second buffer of G (rounds alternate)
+  SPM_ALLOC(ar, T, Jbuf, 2 * (int64_t)(NB / 2) * JS * JS);  // this round's and the next round's J
   SPM_ALLOC(ar, unsigned, bar, 2);
   SPM_ALLOC(ar, double, offacc, 4);
   SPM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
@@ -864,8 +954,9 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   SPM_CUDA_TRY(cudaGetDevice(&dev));
   SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   constexpr int JTHREADS = JT<T>::v;
-  // phase 1: 2 JS x JLD tiles; phase 2: per warp 2 JS x JL4 tiles
-  const int smem = (int)std::max(2 * sizeof(T) * JS * JLD, (JTHREADS / 32) * 2 * sizeof(T) * JS * JL4);
+  // subproblems: 3 JS x JLD tiles and a JS x (JB + 1) one; products: per warp 2 JS x JL4 tiles
+  const int smem = (int)std::max(3 * sizeof(T) * JS * JLD + sizeof(T) * JS * (JB + 1),
+                                 (JTHREADS / 32) * 2 * sizeof(T) * JS * JL4);
   auto kern = k_block_jacobi<T>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JTHREADS, smem));
@@ -888,7 +979,7 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   int max_inner = 1;  // one inner sweep per round: the outer sweeps converge the rest
   GridBar gb{bar, bar + 1};
   int NBv = NB;
-  void* args[] = {(void*)&n, (void*)&NBv, (void*)&G, (void*)&Vw, (void*)&Jbuf,
+  void* args[] = {(void*)&n, (void*)&NBv, (void*)&G, (void*)&Gb, (void*)&Vw, (void*)&Jbuf,
                   (void*)&max_sweeps, (void*)&tol2, (void*)&max_inner, (void*)&tol2i,
                   (void*)&gb, (void*)&offacc, (void*)&status, (void*)&sweeps};
   SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(JTHREADS), args, smem, st));

@@ -573,7 +573,8 @@ __device__ __forceinline__ int pair_index(int P, int Q, int a) {
 // rotations (one thread per pair), then every thread updates whole 2 x 2
 // blocks of M and row pairs of J from the tables.
 template <typename T>
-__device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inner, double tol2) {
+__device__ void inner_jacobi(T (*__restrict__ M)[JLD], T (*__restrict__ J)[JLD], T* __restrict__ cs,
+                             T* __restrict__ sn, int max_inner, double tol2) {
   const int tid = threadIdx.x;
   __shared__ double red[2];
   for (int e = tid; e < JS * JS; e += JT<T>::v) J[e / JS][e % JS] = (e / JS == e % JS) ? (T)1 : (T)0;
@@ -610,10 +611,15 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
         sn[tid] = s;
       }
       __syncthreads();
-      for (int w = tid; w < JB * JB; w += JT<T>::v) {
-        const int bi = w / JB, bj = w % JB;
+      // all loads of a thread (its 2 x 2 block of M and its J row pairs) are
+      // issued before any store, so their latencies overlap
+      static_assert(JB * JB == JT<T>::v && JS * JB == 2 * JT<T>::v, "one block, two J items per thread");
+      {
+        const int bi = tid / JB, bj = tid % JB;
         const int pi = low(bi), qi = pi ^ x, pj = low(bj), qj = pj ^ x;
+        const int row0 = tid / JB, row1 = row0 + JS / 2;
         const T m00 = M[pi][pj], m01 = M[pi][qj], m10 = M[qi][pj], m11 = M[qi][qj];
+        const T j0p = J[row0][pj], j0q = J[row0][qj], j1p = J[row1][pj], j1q = J[row1][qj];
         const T ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
         const T t00 = ci * m00 - si * m10, t01 = ci * m01 - si * m11;
         const T t10 = si * m00 + ci * m10, t11 = si * m01 + ci * m11;
@@ -627,14 +633,10 @@ __device__ void inner_jacobi(T (*M)[JLD], T (*J)[JLD], T* cs, T* sn, int max_inn
         M[pi][qj] = n01;
         M[qi][pj] = n10;
         M[qi][qj] = n11;
-      }
-      for (int w = tid; w < JS * JB; w += JT<T>::v) {
-        const int row = w / JB, bj = w % JB;
-        const int pj = low(bj), qj = pj ^ x;
-        const T vp = J[row][pj], vq = J[row][qj];
-        const T cj = cs[bj], sj = sn[bj];
-        J[row][pj] = cj * vp - sj * vq;
-        J[row][qj] = sj * vp + cj * vq;
+        J[row0][pj] = cj * j0p - sj * j0q;
+        J[row0][qj] = sj * j0p + cj * j0q;
+        J[row1][pj] = cj * j1p - sj * j1q;
+        J[row1][qj] = sj * j1p + cj * j1q;
       }
       __syncthreads();
     }
@@ -653,11 +655,15 @@ __device__ __forceinline__ void rr_locate(int X, int r, int np, int& i, int& h) 
 // Subproblem of pair c of round r + 1, built from G^(r) and the round-r
 // rotations (the rounds' products G^(r+1) = J^T G^(r) J restricted to the
 // pair's blocks): quadrant (X, Y) = J_iX[:, hX]^T G^(r)[pair iX, pair iY] J_iY[:, hY].
-// Uses the shared tiles T (32 x 33) and W (32 x 17) after S0, S1.
+// The three tiles and two rotations are staged in shared memory with one round
+// of loads (buf: 5 JS x JLD tiles, then 3 JS x (JB + 1) products).
 template <typename T>
 __device__ void build_next_subproblem(const T* __restrict__ Gc, int64_t ld, const T* __restrict__ Jc,
-                                      int c, int r, int NB, T (*S0)[JLD], T (*Tt)[JLD], T (*W)[JB + 1]) {
+                                      int c, int r, int NB, T (*S0)[JLD], unsigned char* buf) {
   const int tid = threadIdx.x;
+  T(*Tl)[JLD] = reinterpret_cast<T(*)[JLD]>(buf);            // 3 tiles: (P,P), (P,Q), (Q,Q)
+  T(*Jl)[JLD] = Tl + 3 * JS;                                   // J_iP, J_iQ
+  T(*Wl)[JB + 1] = reinterpret_cast<T(*)[JB + 1]>(buf + 5 * sizeof(T) * JS * JLD);  // 3 x (JS x JB)
   int P2, Q2;
   rr_pair(c, r + 1, NB, P2, Q2);
   int ib[2], hb[2];
@@ -666,36 +672,38 @@ __device__ void build_next_subproblem(const T* __restrict__ Gc, int64_t ld, cons
   int Pb[2], Qb[2];
   rr_pair(ib[0], r, NB, Pb[0], Qb[0]);
   rr_pair(ib[1], r, NB, Pb[1], Qb[1]);
-  // quadrants (0,0), (0,1), (1,1); (1,0) is the transpose of (0,1)
-  for (int qd = 0; qd < 3; ++qd) {
-    const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
-    for (int e = tid; e < JS * JS; e += JT<T>::v) {
-      const int a = e / JS, bb = e % JS;
-      Tt[a][bb] = Gc[(int64_t)pair_index(Pb[X], Qb[X], a) * ld + pair_index(Pb[Y], Qb[Y], bb)];
+  for (int e = tid; e < JS * JS; e += JT<T>::v) {
+    const int a = e / JS, bb = e % JS;
+#pragma unroll
+    for (int qd = 0; qd < 3; ++qd) {
+      const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
+      Tl[qd * JS + a][bb] = Gc[(int64_t)pair_index(Pb[X], Qb[X], a) * ld + pair_index(Pb[Y], Qb[Y], bb)];
     }
-    __syncthreads();
-    // W = T J_iY[:, hY]   (32 x 16)
-    const T* JY = Jc + (size_t)ib[Y] * JS * JS;
-    for (int e = tid; e < JS * JB; e += JT<T>::v) {
-      const int a = e / JB, bb = e % JB;
-      T acc = (T)0;
-#pragma unroll 8
-      for (int l = 0; l < JS; ++l) acc = fma(Tt[a][l], __ldg(JY + l * JS + hb[Y] * JB + bb), acc);
-      W[a][bb] = acc;
-    }
-    __syncthreads();
-    // S0 quadrant = J_iX[:, hX]^T W   (16 x 16)
-    const T* JX = Jc + (size_t)ib[X] * JS * JS;
-    for (int e = tid; e < JB * JB; e += JT<T>::v) {
-      const int a2 = e / JB, bb = e % JB;
-      T acc = (T)0;
-#pragma unroll 8
-      for (int l = 0; l < JS; ++l) acc = fma(__ldg(JX + l * JS + hb[X] * JB + a2), W[l][bb], acc);
-      S0[X * JB + a2][Y * JB + bb] = acc;
-      if (qd == 1) S0[JB + bb][a2] = acc;
-    }
-    __syncthreads();
+    Jl[a][bb] = Jc[(size_t)ib[0] * JS * JS + e];
+    Jl[JS + a][bb] = Jc[(size_t)ib[1] * JS * JS + e];
   }
+  __syncthreads();
+  // W_qd = T_qd J_iY[:, hY]   (32 x 16 each)
+  for (int e = tid; e < 3 * JS * JB; e += JT<T>::v) {
+    const int qd = e / (JS * JB), a = (e / JB) % JS, bb = e % JB;
+    const int Y = (qd == 0) ? 0 : 1;
+    T acc = (T)0;
+#pragma unroll 8
+    for (int l = 0; l < JS; ++l) acc = fma(Tl[qd * JS + a][l], Jl[Y * JS + l][hb[Y] * JB + bb], acc);
+    Wl[qd * JS + a][bb] = acc;
+  }
+  __syncthreads();
+  // S0 quadrant = J_iX[:, hX]^T W_qd   (16 x 16 each); (Q, P) is the transpose of (P, Q)
+  for (int e = tid; e < 3 * JB * JB; e += JT<T>::v) {
+    const int qd = e / (JB * JB), a2 = (e / JB) % JB, bb = e % JB;
+    const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
+    T acc = (T)0;
+#pragma unroll 8
+    for (int l = 0; l < JS; ++l) acc = fma(Jl[X * JS + l][hb[X] * JB + a2], Wl[qd * JS + l][bb], acc);
+    S0[X * JB + a2][Y * JB + bb] = acc;
+    if (qd == 1) S0[JB + bb][a2] = acc;
+  }
+  __syncthreads();
 }
 
 template <typename T>
@@ -707,8 +715,7 @@ __global__ void __launch_bounds__(JT<T>::v)
   extern __shared__ __align__(16) unsigned char jsm[];
   T(*S0)[JLD] = reinterpret_cast<T(*)[JLD]>(jsm);
   T(*S1)[JLD] = S0 + JS;
-  T(*Tt2)[JLD] = S0 + 2 * JS;
-  T(*W2)[JB + 1] = reinterpret_cast<T(*)[JB + 1]>(jsm + 3 * sizeof(T) * JS * JLD);
+  unsigned char* bbuf = jsm + 2 * sizeof(T) * JS * JLD;  // staging of build_next_subproblem
   __shared__ T cs[JB], sn[JB];
   __shared__ double red2[2];
   const unsigned nb = gridDim.x;
@@ -772,7 +779,7 @@ __global__ void __launch_bounds__(JT<T>::v)
       // ---------------- lookahead: round r + 1 subproblems from G^(r) and J^(r)
       if ((int)blockIdx.x < L && r + 1 < NB - 1) {
         for (int c = blockIdx.x; c < hp; c += L) {
-          build_next_subproblem<T>(Gc, ld, Jc, c, r, NB, S0, Tt2, W2);
+          build_next_subproblem<T>(Gc, ld, Jc, c, r, NB, S0, bbuf);
           inner_jacobi<T>(S0, S1, cs, sn, max_inner, tol2_inner);
           T* Jo = Jn + (size_t)c * JS * JS;
           for (int e = tid; e < JS * JS; e += JT<T>::v) Jo[e] = S1[e / JS][e % JS];
@@ -954,8 +961,8 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   SPM_CUDA_TRY(cudaGetDevice(&dev));
   SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   constexpr int JTHREADS = JT<T>::v;
-  // subproblems: 3 JS x JLD tiles and a JS x (JB + 1) one; products: per warp 2 JS x JL4 tiles
-  const int smem = (int)std::max(3 * sizeof(T) * JS * JLD + sizeof(T) * JS * (JB + 1),
+  // subproblems: 7 JS x JLD tiles and 3 JS x (JB + 1) ones; products: per warp 2 JS x JL4 tiles
+  const int smem = (int)std::max(7 * sizeof(T) * JS * JLD + 3 * sizeof(T) * JS * (JB + 1),
                                  (JTHREADS / 32) * 2 * sizeof(T) * JS * JL4);
   auto kern = k_block_jacobi<T>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -194,4 +194,8 @@ struct spm_sketch {
                           // relative to the chunk's first entry
   uint32_t* entoff;       // n*s: (j mod 512) * 33 | sign bit -- shared-memory offset of the
                           // entry's column in the transposed A tile
+  uint32_t* entacc;       // n*s (sparse sign, r1 <= 65535): tile offset (j mod 512) * 33 in
+                          // bits 0..14, accumulator offset (c mod cg) * 33 in bits 15..30,
+                          // sign in bit 31 (the shared-accumulator apply kernel); or null
+  int32_t acc_cg;         // column-group size of entacc (at most SACC_MAX_CG)
 };

@@ -12,6 +12,8 @@
 //   The segments of chunk k form the contiguous range [k*CHUNK*s, ...).
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "rng.cuh"
 
@@ -23,6 +25,8 @@ static constexpr int APPLY_WARPS = 32;
 static constexpr int APPLY_THREADS = APPLY_WARPS * 32;
 static constexpr int APPLY_TILE_LD = APPLY_ROWS + 1;   // padded: conflict-free
 static constexpr uint32_t SIGN_BIT = 0x80000000u;
+static constexpr int SACC_MAX_CG = 1100;   // accumulator columns per CTA (x 33 floats)
+static constexpr int SACC_MAX_S = 8;       // entries of one chunk staged: CHUNK * s words
 
 // ------------------------------------------------------------------ a1: generation
 __global__ void k_sketch_gen(int64_t n, uint32_t r1, int s, uint32_t k0, uint32_t k1,
@@ -156,6 +160,32 @@ __global__ void k_apply_tables(int64_t nnz, int r1, int nchunks, const int64_t* 
     const uint32_t v = ent[e];
     const uint32_t jj = (v & ~SIGN_BIT) % (uint32_t)CHUNK;
     entoff[e] = (jj * (uint32_t)APPLY_TILE_LD) | (v & SIGN_BIT);
+  }
+}
+
+// Entry words of the shared-accumulator apply: tile offset, accumulator offset
+// of the column inside its group of cg columns, sign.  ent[] is sorted by
+// column inside each chunk, so the column of entry e is found by bisection of
+// the chunk's segment starts.
+__global__ void k_acc_tables(int64_t nnz, int r1, int nchunks, int cg,
+                             const int64_t* __restrict__ cptr, const uint32_t* __restrict__ ent,
+                             uint32_t* __restrict__ entacc) {
+  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += gsz) {
+    const uint32_t v = ent[e];
+    const uint32_t j = v & ~SIGN_BIT;
+    const int64_t k = (int64_t)j / CHUNK;
+    const int64_t* cp = cptr + k * r1;
+    int lo = 0, hi = r1 - 1;  // last column c with cp[c] <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cp[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t c = (uint32_t)lo;
+    const uint32_t jj = j % (uint32_t)CHUNK;
+    entacc[e] = (jj * (uint32_t)APPLY_TILE_LD) | (((c % (uint32_t)cg) * (uint32_t)APPLY_TILE_LD) << 15) |
+                (v & SIGN_BIT);
   }
 }
 
@@ -455,6 +485,124 @@ __global__ void __launch_bounds__(APPLY_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ A S, shared accumulators
+// FP32 A, sparse sign S with s <= 8.  One CTA: 32 rows of A (lane = row) x a
+// group of cg output columns, whose accumulators live in shared memory
+// (acc[c][33], FP32).  Per chunk of 512 columns of A, each warp walks a flat,
+// contiguous list of the entries of its own columns (the chunk's CSC segment
+// of those columns) and adds sign * tile[jj][lane] into acc[c][lane]: one
+// entry word, one tile value and one accumulator read-modify-write per entry,
+// no per-column loop.  A column belongs to one warp, so there are no races.
+// The next chunk's tile and entry words are loaded into registers while the
+// current chunk is processed.
+template <typename TO>
+__global__ void __launch_bounds__(APPLY_THREADS, 1)
+    k_sketch_apply_sacc(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, int r1,
+                        int nchunks, int cg, int ngroups, const int64_t* __restrict__ cptr,
+                        const uint32_t* __restrict__ entacc, TO* __restrict__ out, int64_t ldo,
+                        double scale, double* __restrict__ fro2, TO* __restrict__ out_lo,
+                        int ent_cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);                       // CHUNK x 33
+  float* acc = tile + CHUNK * APPLY_TILE_LD;                               // cg x 33
+  uint32_t* es = reinterpret_cast<uint32_t*>(acc + (size_t)cg * APPLY_TILE_LD);  // ent_cap
+  int* wb = reinterpret_cast<int*>(es + ent_cap);  // 2 x 33 warp bounds (this chunk, next chunk)
+  constexpr int PER = CHUNK * APPLY_ROWS / APPLY_THREADS;                  // 16 tile values per thread
+  constexpr int EPER = (CHUNK * SACC_MAX_S) / APPLY_THREADS;               // 4 entry words per thread
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rb = blockIdx.x / ngroups;
+  const int g = blockIdx.x % ngroups;
+  const int64_t row0 = rb * APPLY_ROWS;
+  const int nrows = (int)min64(APPLY_ROWS, m - row0);
+  const int c0 = g * cg;
+  const int ncols = min(cg, r1 - c0);
+  const bool do_fro = (fro2 != nullptr) && (g == 0);
+  for (int i = tid; i < cg * APPLY_TILE_LD; i += APPLY_THREADS) acc[i] = 0.f;
+  double fro_local = 0.0;
+
+  float tv[PER];
+  uint32_t ev[EPER];
+  int e_cnt = 0;
+  // load chunk k into registers (tile values: element q = tid + 1024 u is row q / 512,
+  // column q % 512, so a warp reads 32 consecutive floats of one row)
+  auto load = [&](int k) {
+    const int64_t j0 = (int64_t)k * CHUNK;
+    const int wcnt = (int)min64(CHUNK, n - j0);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int q = tid + APPLY_THREADS * u;
+      const int r = q / CHUNK, jj = q % CHUNK;
+      tv[u] = (r < nrows && jj < wcnt) ? __ldcs(A + (row0 + r) * lda + j0 + jj) : 0.f;
+    }
+    const int64_t base = __ldg(cptr + (int64_t)k * r1 + c0);
+    const int64_t end = __ldg(cptr + (int64_t)k * r1 + c0 + ncols);
+    e_cnt = (int)(end - base);
+#pragma unroll
+    for (int u = 0; u < EPER; ++u) {
+      const int q = tid + APPLY_THREADS * u;
+      ev[u] = (q < e_cnt) ? __ldg(entacc + base + q) : 0u;
+    }
+    // warp w owns columns [c0 + w cg / 32, c0 + (w + 1) cg / 32)
+    if (tid <= APPLY_WARPS) {
+      const int cw = min(ncols, (int)(((int64_t)tid * ncols) / APPLY_WARPS));
+      wb[APPLY_WARPS + 1 + tid] = (int)(__ldg(cptr + (int64_t)k * r1 + c0 + cw) - base);
+    }
+  };
+  load(0);
+  for (int k = 0; k < nchunks; ++k) {
+    // registers -> shared (tile transposed: tile[jj][row])
+    float part = 0.f;  // |A|_F^2: one FP64 add per chunk
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int q = tid + APPLY_THREADS * u;
+      tile[(q % CHUNK) * APPLY_TILE_LD + q / CHUNK] = tv[u];
+      part = fmaf(tv[u], tv[u], part);
+    }
+    if (do_fro) fro_local += (double)part;
+#pragma unroll
+    for (int u = 0; u < EPER; ++u) {
+      const int q = tid + APPLY_THREADS * u;
+      if (q < e_cnt) es[q] = ev[u];
+    }
+    if (tid <= APPLY_WARPS) wb[tid] = wb[APPLY_WARPS + 1 + tid];
+    __syncthreads();
+    if (k + 1 < nchunks) load(k + 1);  // in flight while this chunk is reduced
+    {
+      const int p0 = wb[warp], p1 = wb[warp + 1];
+      const float* tl = tile + lane;
+      float* al = acc + lane;
+#pragma unroll 4
+      for (int p = p0; p < p1; ++p) {
+        const uint32_t e = es[p];
+        const float v = __int_as_float(__float_as_int(tl[e & 0x7FFFu]) ^ (int)(e & SIGN_BIT));
+        float* a = al + ((e >> 15) & 0xFFFFu);
+        *a += v;
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: acc[c][r] -> out[row0 + r][c0 + c], consecutive threads on consecutive c
+  for (int q = tid; q < nrows * ncols; q += APPLY_THREADS) {
+    const int r = q / ncols, c = q % ncols;
+    const float v = acc[c * APPLY_TILE_LD + r] * (float)scale;
+    const TO h = cvt_out<TO>(v);
+    out[(row0 + r) * ldo + c0 + c] = h;
+    if (out_lo) out_lo[(row0 + r) * ldo + c0 + c] = cvt_out<TO>(v - (float)as_double(h));
+  }
+  if (do_fro) {
+    for (int o = 16; o > 0; o >>= 1) fro_local += __shfl_xor_sync(0xFFFFFFFFu, fro_local, o);
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem_raw);
+    if (lane == 0) red[warp] = fro_local;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < APPLY_WARPS; ++w) sum += red[w];
+      atomicAdd(fro2, sum);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ S^T X
 // One CTA per (output row c, strip of 256 columns of X); c varies fastest so
 // that all CTAs of one strip run together and re-reads of X rows hit L2.
@@ -501,9 +649,38 @@ int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint
   return SPM_OK;
 }
 
+// Shared-accumulator apply (FP32 A, FP32 or BF16 out); SPM_EUNSUPPORTED when
+// the sketch has no entacc table or the CTA's shared memory would not fit.
+template <typename TO>
+static int launch_apply_sacc(const spm_sketch* S, const float* A, int64_t m, int64_t lda, TO* out,
+                             int64_t ldo, double* fro2, cudaStream_t st, TO* out_lo) {
+  if (!S->entacc || S->kind != SPM_SKETCH_SPARSE_SIGN || S->s > SACC_MAX_S) return SPM_EUNSUPPORTED;
+  const int64_t nch = nchunks_of(S->n);
+  const int cg = S->acc_cg;
+  const int ngroups = (int)cdiv(S->r1, cg);
+  const int ent_cap = CHUNK * S->s;
+  const size_t smem = ((size_t)CHUNK * APPLY_TILE_LD + (size_t)cg * APPLY_TILE_LD) * sizeof(float) +
+                      (size_t)ent_cap * sizeof(uint32_t) + 2 * (APPLY_WARPS + 1) * sizeof(int);
+  if (smem > 227 * 1024) return SPM_EUNSUPPORTED;
+  const int64_t grid = cdiv(m, APPLY_ROWS) * ngroups;
+  if (grid > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  const double scale = 1.0 / sqrt((double)S->s);
+  auto kern = k_sketch_apply_sacc<TO>;
+  SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)grid, APPLY_THREADS, smem, st>>>(A, m, S->n, lda, (int)S->r1, (int)nch, cg, ngroups,
+                                                    S->bucket_ptr, S->entacc, out, ldo, scale, fro2,
+                                                    out_lo, ent_cap);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
 template <typename TA, typename TACC, typename TO, int CPW, int NBUF>
 static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda, TO* out,
                         int64_t ldo, double* fro2, cudaStream_t st, TO* out_lo = nullptr) {
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TACC, float>::value) {
+    const int rc = launch_apply_sacc<TO>(S, A, m, lda, out, ldo, fro2, st, out_lo);
+    if (rc != SPM_EUNSUPPORTED) return rc;
+  }
   const int64_t nch = nchunks_of(S->n);
   constexpr int CG = APPLY_WARPS * CPW;
   const int col_groups = (int)cdiv(S->r1, CG);
@@ -648,6 +825,15 @@ int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64
         nnz, (int)r1, (int)nch, S->bucket_ptr, S->bucket_ent, S->seg, S->entoff);
     if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
   }
+  if (kind == SPM_SKETCH_SPARSE_SIGN && s <= SACC_MAX_S && r1 <= 65535) {
+    const int64_t ng = cdiv(r1, SACC_MAX_CG);
+    S->acc_cg = (int32_t)cdiv(r1, ng);
+    if (cudaMallocAsync((void**)&S->entacc, nnz * sizeof(uint32_t), st) != cudaSuccess)
+      return fail(SPM_ENOMEM);
+    k_acc_tables<<<(unsigned)min64(cdiv(nnz, 256), 152 * 16), 256, 0, st>>>(
+        nnz, (int)r1, (int)nch, S->acc_cg, S->bucket_ptr, S->bucket_ent, S->entacc);
+    if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
+  }
   *out = S;
   return SPM_OK;
 }
@@ -660,6 +846,7 @@ int spm_sketch_destroy(spm_sketch* S) {
   if (S->bucket_ptr) cudaFreeAsync(S->bucket_ptr, S->stream);
   if (S->seg) cudaFreeAsync(S->seg, S->stream);
   if (S->entoff) cudaFreeAsync(S->entoff, S->stream);
+  if (S->entacc) cudaFreeAsync(S->entacc, S->stream);
   delete S;
   return SPM_OK;
 }

@@ -89,6 +89,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// The same load into the same shared-memory offset of every CTA in `mask` of
+// the cluster; each destination's barrier at `bar` receives the bytes.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
 // byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
 // value 1 in bits 46-48, swizzle mode 2 (128-byte) in bits 61-63.
@@ -130,6 +146,14 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
+// arrive (when the MMAs complete) on the barrier at `bar` of every CTA in mask
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
@@ -145,7 +169,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN, bool A_MN, bool B_MN>
+// CL = 2: the two CTAs of a cluster take neighbouring M tiles of the same N
+// tile; each loads half of the shared B tile and multicasts it to both, and
+// a stage is refilled only after both CTAs' MMAs have released it.
+template <int BN, bool A_MN, bool B_MN, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
               const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
@@ -171,10 +198,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
   const int iters = (kt1 - kt0) * p.npass;
 
+  uint32_t crank = 0;
+  if (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  constexpr uint16_t cmask = (uint16_t)((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, CL);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -190,6 +220,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (CL > 1) cluster_sync_all();  // peers' barriers exist before any multicast reaches them
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0) {
@@ -218,11 +249,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[q], m0 + 64 * b, k0, fb);
         }
-        if (!B_MN) {
-          tma_load_2d(sb, tb[q], k0, n0, fb);
-        } else {
+        if (CL == 1) {
+          if (!B_MN) {
+            tma_load_2d(sb, tb[q], k0, n0, fb);
+          } else {
 #pragma unroll
-          for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[q], n0 + 64 * b, k0, fb);
+            for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[q], n0 + 64 * b, k0, fb);
+          }
+        } else {
+          if (!B_MN) {
+            constexpr int HB = BN / CL;  // rows of the B tile this CTA fetches
+            tma_load_2d_mc(sb + crank * HB * 128, tb[q], k0, n0 + (int)crank * HB, fb, cmask);
+          } else {
+#pragma unroll
+            for (int b = 0; b < BN / 64; ++b)
+              if (b % CL == (int)crank) tma_load_2d_mc(sb + b * 8192, tb[q], n0 + 64 * b, k0, fb, cmask);
+          }
         }
         issued = it + 1;
       }
@@ -260,7 +302,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bd = smem_desc(sb + kk * 2048, 8192, 1024);
           tc_mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
         }
-        tc_commit(empty0 + 8 * s);
+        if (CL == 1)
+          tc_commit(empty0 + 8 * s);
+        else
+          tc_commit_mc(empty0 + 8 * s, cmask);
       }
       tc_commit(done);  // fires once every MMA above has completed
       (void)ok;
@@ -309,10 +354,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // the MMA thread's final commit must have fired before the columns go back
+  // and (in a cluster) before the peer may exit: every arrival this CTA's MMAs
+  // make on the peer's barriers precedes it
+  if (warp == 1 && lane == 0) mbar_wait(done, 0, p.status);
+  __syncthreads();
+  if (CL > 1) cluster_sync_all();
   if (warp == 1) {
-    // the MMA thread's final commit must have fired before the columns go back
-    if (lane == 0) mbar_wait(done, 0, p.status);
-    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)BN)
@@ -388,24 +436,40 @@ static int make_map(CUtensorMap* map, const TcOp& op, int64_t rows_mn, int64_t k
   return r == CUDA_SUCCESS ? SPM_OK : SPM_EINVAL;
 }
 
-template <int BN, bool A_MN, bool B_MN>
+template <int BN, bool A_MN, bool B_MN, int CL>
 static int launch_tc(const CUtensorMap* ta, const CUtensorMap* tb, const TcParams& p, dim3 grid,
                      cudaStream_t st) {
-  auto kern = k_gemm_tc<BN, A_MN, B_MN>;
+  auto kern = k_gemm_tc<BN, A_MN, B_MN, CL>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcCfg<BN>::SMEM));
-  kern<<<grid, TC_THREADS, TcCfg<BN>::SMEM, st>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p);
+  if (CL == 1) {
+    kern<<<grid, TC_THREADS, TcCfg<BN>::SMEM, st>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = TcCfg<BN>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SPM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p));
+  }
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }
 
-template <int BN>
+template <int BN, int CL>
 static int launch_bn(bool amn, bool bmn, const CUtensorMap* ta, const CUtensorMap* tb,
                      const TcParams& p, dim3 grid, cudaStream_t st) {
-  if (!amn && !bmn) return launch_tc<BN, false, false>(ta, tb, p, grid, st);
-  if (!amn && bmn) return launch_tc<BN, false, true>(ta, tb, p, grid, st);
-  if (amn && !bmn) return launch_tc<BN, true, false>(ta, tb, p, grid, st);
-  return launch_tc<BN, true, true>(ta, tb, p, grid, st);
+  if (!amn && !bmn) return launch_tc<BN, false, false, CL>(ta, tb, p, grid, st);
+  if (!amn && bmn) return launch_tc<BN, false, true, CL>(ta, tb, p, grid, st);
+  if (amn && !bmn) return launch_tc<BN, true, false, CL>(ta, tb, p, grid, st);
+  return launch_tc<BN, true, true, CL>(ta, tb, p, grid, st);
 }
 
 int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
@@ -422,18 +486,19 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   for (int q = 0; q < npass; ++q)
     if (A[q].mn_major != A[0].mn_major || B[q].mn_major != B[0].mn_major) return SPM_EINVAL;
   const int BN = (N >= 192) ? 256 : 128;
+  const int CL = (cdiv(M, TC_BM) >= 2) ? 2 : 1;  // pairs of M tiles share their B tile
   CUtensorMap ta[3], tb[3];
   for (int q = 0; q < 3; ++q) {
     const int qq = q < npass ? q : 0;
     SPM_TRY(make_map(&ta[q], A[qq], M, K, TC_BM));
-    SPM_TRY(make_map(&tb[q], B[qq], N, K, BN));
+    SPM_TRY(make_map(&tb[q], B[qq], N, K, BN / CL));
   }
   const int k_tiles = (int)cdiv(K, TC_BK);
   if (splitk < 1) splitk = 1;
   if (splitk > k_tiles) splitk = k_tiles;
   const int kt_per = (int)cdiv(k_tiles, splitk);
   splitk = (int)cdiv(k_tiles, kt_per);
-  const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
+  const int64_t mt = round_up(cdiv(M, TC_BM), CL), nt = cdiv(N, BN);
   if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
   TcParams p{};
   p.M = (int)M;
@@ -458,10 +523,14 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
     p.d_cs = 1;
     p.split_stride = M * N;
   }
-  if (BN == 256)
-    SPM_TRY(launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+  if (BN == 256 && CL == 2)
+    SPM_TRY((launch_bn<256, 2>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+  else if (BN == 256)
+    SPM_TRY((launch_bn<256, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+  else if (CL == 2)
+    SPM_TRY((launch_bn<128, 2>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   else
-    SPM_TRY(launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+    SPM_TRY((launch_bn<128, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
     const int64_t total = M * N;
     const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
@@ -551,9 +620,9 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   }
   dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
   if (BN == 256)
-    SPM_TRY(launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+    SPM_TRY((launch_bn<256, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   else
-    SPM_TRY(launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st));
+    SPM_TRY((launch_bn<128, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
     const int64_t total = M * N;
     const int blocks = (int)min64(cdiv(total, 256), 152 * 8);

@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 METRIC = "time to rank-k approx at fixed rel. residual vs plain FP64 GPU; HBM GB/s"
 
 # DRAM bytes (read + write) per launch at the 65536 x 16384 size, from one ncu capture of the
-# same kernel on 8192 rows scaled by the rows (profiles/k_sketch_apply_8192x16384_r2000.md)
-NCU_TRAFFIC = {"k_sketch_apply": 8 * (541.1e6 + 54.0e6)}
+# same kernel on 8192 rows scaled by the rows (profiles/k_sketch_apply_sacc_8192x16384_r2000.md)
+NCU_TRAFFIC = {"k_sketch_apply": 8 * (537.8e6 + 12.0e6)}
 
 
 def parse():
@@ -411,7 +411,7 @@ def main():
     else:
         ach = apply_bytes / (apply_ms * 1e-3) / 1e9
         default_size = (m, n, r1, a.s) == (65536, 16384, 2000, 8)
-        roof = {"kernel": "k_sketch_apply", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+        roof = {"kernel": "k_sketch_apply_sacc", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
                 "unit": "GB/s", "frac": ach / hbm_peak,
                 "traffic": NCU_TRAFFIC["k_sketch_apply"] if default_size else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}

@@ -1014,12 +1014,14 @@ __global__ void k_line_norms(int64_t rows, int64_t cols, const T* __restrict__ X
   const int64_t len = by_col ? rows : cols;
   __shared__ double red[256];
   for (int64_t l = blockIdx.x; l < nl; l += gridDim.x) {
-    double s = 0.0;
+    // per-thread partial sums in T (FP32 for FP32 data: len / 256 terms each),
+    // combined in FP64
+    T sp = (T)0;
     for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
-      const double v = by_col ? ldd<T>(X + t * rs + l * cs) : ldd<T>(X + l * rs + t * cs);
-      s += v * v;
+      const T v = by_col ? X[t * rs + l * cs] : X[l * rs + t * cs];
+      sp = fma(v, v, sp);
     }
-    red[threadIdx.x] = s;
+    red[threadIdx.x] = (double)sp;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
       if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -1043,20 +1045,25 @@ int norms(int64_t rows, int64_t cols, View X, bool by_col, double* out, cudaStre
 template <typename T>
 __global__ void k_scale_lines(int64_t rows, int64_t cols, T* __restrict__ X, int64_t rs, int64_t cs,
                               bool by_rows, const double* __restrict__ s, bool inv) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cols, j = e % cols;
-    double f = s[by_rows ? i : j];
+  // blockIdx.y walks the lines (rows or columns), threads the other index; the
+  // factor is formed once per line and applied in T
+  const int64_t nl = by_rows ? rows : cols, len = by_rows ? cols : rows;
+  for (int64_t l = blockIdx.y; l < nl; l += gridDim.y) {
+    double f = s[l];
     if (inv) f = (f != 0.0) ? 1.0 / f : 0.0;
-    T* p = X + i * rs + j * cs;
-    *p = (T)((double)*p * f);
+    const T ft = (T)f;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      T* p = by_rows ? X + l * rs + t * cs : X + t * rs + l * cs;
+      *p = *p * ft;
+    }
   }
 }
 
 int scale_lines(int64_t rows, int64_t cols, MView X, bool rows_not_cols, const double* s, bool inv,
                 cudaStream_t st) {
-  const int g = grid_for(rows * cols);
+  const int64_t nl = rows_not_cols ? rows : cols, len = rows_not_cols ? cols : rows;
+  const dim3 g((unsigned)min64(cdiv(len, 256), 64), (unsigned)min64(nl, 65535));
   if (X.dt == DT_F32) k_scale_lines<float><<<g, 256, 0, st>>>(rows, cols, (float*)X.p, X.rs, X.cs, rows_not_cols, s, inv);
   else if (X.dt == DT_F64) k_scale_lines<double><<<g, 256, 0, st>>>(rows, cols, (double*)X.p, X.rs, X.cs, rows_not_cols, s, inv);
   else return SPM_EINVAL;
@@ -1068,14 +1075,15 @@ template <typename T>
 __global__ void k_sumsq(int64_t rows, int64_t cols, const T* __restrict__ X, int64_t rs, int64_t cs,
                         double* acc) {
   __shared__ double red[256];
-  double s = 0.0;
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = ldd<T>(X + (e / cols) * rs + (e % cols) * cs);
-    s += v * v;
-  }
-  red[threadIdx.x] = s;
+  // rows from blockIdx.y, per-thread partial sums in T, combined in FP64
+  T sp = (T)0;
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const T v = X[i * rs + j * cs];
+      sp = fma(v, v, sp);
+    }
+  red[threadIdx.x] = (double)sp;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -1085,7 +1093,7 @@ __global__ void k_sumsq(int64_t rows, int64_t cols, const T* __restrict__ X, int
 }
 
 int sumsq(int64_t rows, int64_t cols, View X, double* acc, cudaStream_t st) {
-  const int g = grid_for(rows * cols);
+  const dim3 g((unsigned)min64(cdiv(cols, 256), 16), (unsigned)min64(rows, 1024));
   if (X.dt == DT_F32) k_sumsq<float><<<g, 256, 0, st>>>(rows, cols, (const float*)X.p, X.rs, X.cs, acc);
   else if (X.dt == DT_F64) k_sumsq<double><<<g, 256, 0, st>>>(rows, cols, (const double*)X.p, X.rs, X.cs, acc);
   else return SPM_EINVAL;
@@ -1100,16 +1108,16 @@ __global__ void k_sign_flags(int64_t m, int64_t k, const T* __restrict__ U, int6
   __shared__ double bv[256];
   __shared__ int64_t bi[256];
   for (int64_t j = blockIdx.x; j < k; j += gridDim.x) {
-    double best = -1.0;
+    T best = (T)-1;
     int64_t idx = 0;
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const double v = fabs((double)U[i * rs + j * cs]);
+      const T v = fabs(U[i * rs + j * cs]);
       if (v > best) {
         best = v;
         idx = i;
       }
     }
-    bv[threadIdx.x] = best;
+    bv[threadIdx.x] = (double)best;
     bi[threadIdx.x] = idx;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {

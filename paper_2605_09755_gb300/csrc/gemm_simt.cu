@@ -9,10 +9,18 @@ namespace spm {
 
 static constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16, SG_THREADS = 256;
 
-template <typename T>
-__device__ __forceinline__ double ld_as_double(const T* p) { return (double)*p; }
+// Load one element converted straight to the accumulator type (an FP32
+// product never goes through FP64, whose conversions are slow on this part).
+template <typename TACC, typename T>
+__device__ __forceinline__ TACC ld_as(const T* p) {
+  return (TACC)*p;
+}
 template <>
-__device__ __forceinline__ double ld_as_double<__nv_bfloat16>(const __nv_bfloat16* p) {
+__device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const __nv_bfloat16* p) {
   return (double)__bfloat162float(*p);
 }
 
@@ -43,7 +51,7 @@ __global__ void __launch_bounds__(SG_THREADS)
       const int kk = a_kfast ? (e % SG_BK) : (e / SG_BM);
       const int ii = a_kfast ? (e / SG_BK) : (e % SG_BM);
       const int64_t gi = row0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < M && gk < K) ? (TACC)ld_as_double(A + gi * ars + gk * acs) : (TACC)0;
+      As[kk][ii] = (gi < M && gk < K) ? ld_as<TACC>(A + gi * ars + gk * acs) : (TACC)0;
     }
 #pragma unroll
     for (int q = 0; q < (SG_BN * SG_BK) / SG_THREADS; ++q) {
@@ -51,7 +59,7 @@ __global__ void __launch_bounds__(SG_THREADS)
       const int kk = b_nfast ? (e / SG_BN) : (e % SG_BK);
       const int jj = b_nfast ? (e % SG_BN) : (e / SG_BK);
       const int64_t gj = col0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < K) ? (TACC)ld_as_double(B + gk * brs + gj * bcs) : (TACC)0;
+      Bs[kk][jj] = (gj < N && gk < K) ? ld_as<TACC>(B + gk * brs + gj * bcs) : (TACC)0;
     }
     __syncthreads();
 #pragma unroll
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(SG_THREADS)
       if (gj >= N) continue;
       TC* c = C + gi * crs + gj * ccs;
       TACC v = alpha * acc[i][j];
-      if (beta != (TACC)0) v += beta * (TACC)ld_as_double(c);
+      if (beta != (TACC)0) v += beta * ld_as<TACC>(c);
       *c = (TC)v;
     }
   }

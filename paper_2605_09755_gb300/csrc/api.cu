@@ -41,9 +41,18 @@ struct Call {
 
 static int64_t pad8(int64_t x) { return round_up(x, 8); }
 
-static int auto_splitk(int64_t M, int64_t N, int64_t K) {
+// sym: only the tiles a symmetric product computes (clusters of two M tiles
+// that reach the upper triangle) count.
+static int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false) {
   const int BN = (N >= 192) ? 256 : 128;
-  const int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
+  int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
+  if (sym) {
+    const int64_t mt = cdiv(M, 128), cl = mt >= 2 ? 2 : 1;
+    tiles = 0;
+    for (int64_t j = 0; j < cdiv(N, BN); ++j)
+      for (int64_t c = 0; c < cdiv(mt, cl); ++c)
+        if (c * cl * 128 < (j + 1) * BN) tiles += cl;
+  }
   const int64_t kt = cdiv(K, 64);
   int64_t sk = cdiv(2 * 152, tiles);
   sk = min64(sk, max64(kt / 4, 1));
@@ -54,10 +63,10 @@ static int auto_splitk(int64_t M, int64_t N, int64_t K) {
 static int tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* Ahi,
                     const __nv_bfloat16* Alo, int64_t lda, bool a_mn, const __nv_bfloat16* Bhi,
                     const __nv_bfloat16* Blo, int64_t ldb, bool b_mn, int npass, float* D,
-                    int64_t d_rs, int64_t d_cs, cudaStream_t st) {
+                    int64_t d_rs, int64_t d_cs, cudaStream_t st, bool sym = false) {
   TcOp A[3] = {{Ahi, lda, a_mn}, {Ahi, lda, a_mn}, {Alo, lda, a_mn}};
   TcOp B[3] = {{Bhi, ldb, b_mn}, {Blo, ldb, b_mn}, {Bhi, ldb, b_mn}};
-  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K), st);
+  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K, sym), st, sym);
 }
 
 // ------------------------------------------------------------------ CholeskyQR
@@ -138,7 +147,7 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
     SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
                        mrowmajor(Qlo, DT_BF16, cp), C.st));
     // G = Y^T Y: A-op Y^T (M = c, K = m) and B-op (N = c, K = m) both MN-major
-    SPM_TRY(tc_split(c, c, m, Qhi, Qlo, cp, true, Qhi, Qlo, cp, true, 3, G, c, 1, C.st));
+    SPM_TRY(tc_split(c, c, m, Qhi, Qlo, cp, true, Qhi, Qlo, cp, true, 3, G, c, 1, C.st, true));
     if (sdt == DT_F64)
       SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F64, c), C.st));
     else
@@ -469,7 +478,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     SPM_TRY(split_bf16(r2, n, rowmajor(B, DT_F32, n), mrowmajor(Bhi, DT_BF16, np_),
                        mrowmajor(Blo, DT_BF16, np_), C.st));
     // G = B B^T: both operands B (r2 x n), K-major
-    SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st));
+    SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st, true));
     SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Gs, sdt, r2), C.st));
     SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
     SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st, C.status + 1));

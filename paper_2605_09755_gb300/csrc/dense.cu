@@ -549,8 +549,11 @@ __device__ __forceinline__ void rot_params(T app, T aqq, T apq, T& c, T& s) {
   s = t * c;
 }
 // FP32: approximate reciprocal intrinsics keep the rotation on the critical
-// path short.  Only the angle depends on them; c = rsqrt(1 + t^2), s = t c
-// keep the rotation orthogonal to rounding.
+// path short.  The angle (t) may carry their error; c must not: c^2 (1 + t^2)
+// has to be 1 to rounding, or every rotation scales its rows and the bias adds
+// up over the ~r^2 rotations of a solve (a uniform relative loss of ~1e-7 per
+// rotation shrank all eigenvalues by ~3e-4 at r = 600).  So the approximate
+// rsqrt gets one Newton-Raphson step, r' = r + r (1 - x r^2) / 2.
 template <>
 __device__ __forceinline__ void rot_params<float>(float app, float aqq, float apq, float& c, float& s) {
   c = 1.f;
@@ -559,7 +562,9 @@ __device__ __forceinline__ void rot_params<float>(float app, float aqq, float ap
   const float tau = (aqq - app) * __fdividef(0.5f, apq);
   const float at = fabsf(tau);
   const float t = copysignf(at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + sqrtf(fmaf(at, at, 1.f))), tau);
-  c = rsqrtf(fmaf(t, t, 1.f));
+  const float x = fmaf(t, t, 1.f);
+  const float r = rsqrtf(x);
+  c = fmaf(0.5f * r, fmaf(-(x * r), r, 1.f), r);
   s = t * c;
 }
 
@@ -914,19 +919,43 @@ __global__ void k_eye_pad(int n, int npad, const T* __restrict__ A, int64_t lda,
   }
 }
 
-// Sort the first n eigenvalues (diagonal of G) descending and gather eigenvector
-// columns; padded positions (>= n) hold the decoupled zero rows and are skipped.
+// Column norms of the accumulated rotations.  A rotation whose cosine rounds
+// to 1 (|t| < 2^-12 in FP32) is sqrt(1 + t^2) times an orthogonal one, and the
+// late sweeps consist of such rotations: to first order V = W D with W
+// orthogonal and D diagonal, and the same products turn G into D W^T G0 W D.
+// So each eigenvector is normalised and its eigenvalue divided by the squared
+// norm (the Rayleigh quotient of the unit vector): lamc[i] = G_ii / |v_i|^2,
+// inv[i] = 1 / |v_i|.  One thread per column, rows in order (coalesced).
 template <typename T>
-__global__ void k_eig_sort(int n, int64_t ldg, const T* __restrict__ G, const T* __restrict__ Vin,
-                           T* __restrict__ Vout, int64_t ldvo, T* __restrict__ lam) {
+__global__ void k_eig_colnorm(int n, int64_t ldg, const T* __restrict__ G, const T* __restrict__ V,
+                              T* __restrict__ lamc, T* __restrict__ inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int row = 0; row < n; ++row) {
+    const double v = (double)V[(int64_t)row * ldg + i];
+    s += v * v;
+  }
+  lamc[i] = (T)((double)G[(int64_t)i * ldg + i] / s);
+  inv[i] = (T)(1.0 / sqrt(s));
+}
+
+// Sort the first n (corrected) eigenvalues descending and gather the normalised
+// eigenvector columns; padded positions (>= n) hold the decoupled zero rows and
+// are skipped.
+template <typename T>
+__global__ void k_eig_sort(int n, int64_t ldg, const T* __restrict__ lamc, const T* __restrict__ inv,
+                           const T* __restrict__ Vin, T* __restrict__ Vout, int64_t ldvo,
+                           T* __restrict__ lam) {
   __shared__ int rk;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const T li = G[(int64_t)i * ldg + i];
+    const T li = lamc[i];
+    const T sc = inv[i];
     if (threadIdx.x == 0) rk = 0;
     __syncthreads();
     int cnt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const T lj = G[(int64_t)j * ldg + j];
+      const T lj = lamc[j];
       if (lj > li || (lj == li && j < i)) ++cnt;
     }
     atomicAdd(&rk, cnt);
@@ -934,7 +963,7 @@ __global__ void k_eig_sort(int n, int64_t ldg, const T* __restrict__ G, const T*
     const int pos = rk;
     if (threadIdx.x == 0) lam[pos] = li;
     for (int row = threadIdx.x; row < n; row += blockDim.x)
-      Vout[(int64_t)row * ldvo + pos] = Vin[(int64_t)row * ldg + i];
+      Vout[(int64_t)row * ldvo + pos] = Vin[(int64_t)row * ldg + i] * sc;
     __syncthreads();
   }
 }
@@ -954,6 +983,7 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   SPM_ALLOC(ar, T, Jbuf, 2 * (int64_t)(NB / 2) * JS * JS);  // this round's and the next round's J
   SPM_ALLOC(ar, unsigned, bar, 2);
   SPM_ALLOC(ar, double, offacc, 4);
+  SPM_ALLOC(ar, T, lamc, 2 * (int64_t)n);  // corrected eigenvalues, then inverse column norms
   SPM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
   k_eye_pad<T><<<grid_for((int64_t)npad * npad), 256, 0, st>>>(n, npad, A, lda, G, Vw);
   SPM_LAUNCH_CHECK();
@@ -991,7 +1021,9 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
                   (void*)&gb, (void*)&offacc, (void*)&status, (void*)&sweeps};
   SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(JTHREADS), args, smem, st));
   count_launch();
-  k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, npad, G, Vw, V, ldv, lam);
+  k_eig_colnorm<T><<<(unsigned)cdiv(n, 128), 128, 0, st>>>(n, npad, G, Vw, lamc, lamc + n);
+  SPM_LAUNCH_CHECK();
+  k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, npad, lamc, lamc + n, Vw, V, ldv, lam);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }

@@ -44,6 +44,7 @@ struct TcParams {
   float* D;
   int64_t d_rs, d_cs, split_stride;
   int* status;
+  int sym_upper;  // skip clusters whose tiles lie entirely below the diagonal
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -194,6 +195,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM;
   const int n0 = blockIdx.y * BN;
+  // symmetric output: a whole cluster below the diagonal leaves before it
+  // touches any barrier (the decision is the same for all its CTAs)
+  if (p.sym_upper && (int)(blockIdx.x / CL) * CL * TC_BM >= n0 + BN) return;
   const int kt0 = blockIdx.z * p.kt_per_split;
   const int kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
   const int iters = (kt1 - kt0) * p.npass;
@@ -472,8 +476,16 @@ static int launch_bn(bool amn, bool bmn, const CUtensorMap* ta, const CUtensorMa
   return launch_tc<BN, true, true, CL>(ta, tb, p, grid, st);
 }
 
+// strictly lower triangle of D (n x n) from the upper one
+__global__ void k_mirror_upper(int n, float* __restrict__ D, int64_t d_rs, int64_t d_cs) {
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < i; j += gridDim.x * blockDim.x)
+      D[(int64_t)i * d_rs + (int64_t)j * d_cs] = D[(int64_t)j * d_rs + (int64_t)i * d_cs];
+}
+
 int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
-            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st) {
+            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st, bool sym_upper) {
+  if (sym_upper && M != N) return SPM_EINVAL;
   if (M <= 0 || N <= 0) return SPM_OK;
   if (npass < 1 || npass > 3) return SPM_EINVAL;
   if (M > 0x7FFFFFFF || N > 0x7FFFFFFF || K > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
@@ -509,6 +521,7 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   p.npass = npass;
   p.alpha = alpha;
   p.status = nullptr;
+  p.sym_upper = sym_upper ? 1 : 0;
   dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
   Arena ar(st);
   if (splitk == 1) {
@@ -535,6 +548,11 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
     const int64_t total = M * N;
     const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
     k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, splitk, p.D, D, d_rs, d_cs);
+    SPM_LAUNCH_CHECK();
+  }
+  if (sym_upper) {
+    const dim3 g((unsigned)min64(cdiv(M, 256), 8), (unsigned)min64(M, 1024));
+    k_mirror_upper<<<g, 256, 0, st>>>((int)M, D, d_rs, d_cs);
     SPM_LAUNCH_CHECK();
   }
   return SPM_OK;

@@ -58,8 +58,12 @@ struct TcOp {
 // D(M x N, fp32) = alpha * sum_{q < npass} A[q] * B[q]^T, written at
 // D[i*d_rs + j*d_cs].  splitk > 1 splits K in equal chunks; partial sums are
 // reduced deterministically (fixed order) before D is written.
+// sym_upper (M == N, the product symmetric by construction, e.g. a Gram
+// matrix): only the output tiles that meet the upper triangle are computed and
+// the strictly lower triangle is then copied from the upper one.
 int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
-            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st);
+            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st,
+            bool sym_upper = false);
 bool tc_available();
 
 // ---------------------------------------------------------------- dense.cu

@@ -216,6 +216,28 @@ def test_rsvd_mixed_parity(spm, m, n, r1, r2, q):
     assert info["device_status"] == 0
 
 
+def test_rsvd_mixed_parity_wide(spm):
+    """r2 = 600: the Gram products span several clusters of output tiles, so the
+    symmetric Gram path (tiles below the diagonal skipped, then mirrored) is
+    exercised, and the FP32 eigensolver runs ~6000 rotations per index (its
+    eigenvector normalisation keeps the eigenvalues unbiased: before it, all
+    sigma came out ~3e-4 low here).  q = 0 keeps kappa(Y) ~ sigma_1 / sigma_600
+    ~ 30, so the single-precision basis keeps the tail.  Orthogonality: observed
+    ~4e-7 k (Frobenius), bound 2e-6 k."""
+    m, n, r1, r2, q = 3000, 1500, 1200, 600, 0
+    A, sigma = wl.noisy_exp_numpy(m, n, seed=1002, noise=1e-3 / np.sqrt(n))
+    U_o, s_o, Vt_o, _ = _oracle_rsvd(A, n, r1, 8, r2, q, r2)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(n, r1, 8, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A, torch.float32), r2, q, r2, precision=spm.PREC_MIXED)
+    U, sg, Vt = host(U), host(sg), host(Vt)
+    res = np.linalg.norm(A - (U * sg) @ Vt)
+    assert res <= 1.01 * res_o, (res, res_o)
+    assert np.max(np.abs(sg - s_o) / s_o) <= 1e-4, np.max(np.abs(sg - s_o) / s_o)
+    assert np.linalg.norm(U.T @ U - np.eye(r2)) <= 2e-6 * r2
+    assert info["device_status"] == 0
+
+
 @pytest.mark.parametrize("m,n,r1,r2,q", [(2000, 1000, 100, 50, 2), (1500, 1100, 1000, 700, 1)])
 def test_rsvd_fp32_parity(spm, m, n, r1, r2, q):
     """FP32 on CUDA cores: residual within 1% of the oracle's.

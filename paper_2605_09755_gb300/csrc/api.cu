@@ -167,6 +167,67 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
   return SPM_OK;
 }
 
+// D = X Y^T from three-part BF16 splits of both operands, keeping the six
+// terms of order >= 2^-16 (FP32-equivalent): (1,1) (1,2) (2,1) in one product,
+// (1,3) (2,2) (3,1) in a second one added on.  T: scratch of M x N floats.
+static int tc_six(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* const* X, int64_t ldx,
+                  bool x_mn, const __nv_bfloat16* const* Y, int64_t ldy, bool y_mn, float* D,
+                  int64_t ldd, bool sym, float* T, cudaStream_t st) {
+  const int sk = auto_splitk(M, N, K, sym);
+  TcOp a1[3] = {{X[0], ldx, x_mn}, {X[0], ldx, x_mn}, {X[1], ldx, x_mn}};
+  TcOp b1[3] = {{Y[0], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
+  TcOp a2[3] = {{X[0], ldx, x_mn}, {X[1], ldx, x_mn}, {X[2], ldx, x_mn}};
+  TcOp b2[3] = {{Y[2], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
+  SPM_TRY(gemm_tc(M, N, K, 3, a1, b1, 1.0f, D, ldd, 1, sk, st, sym));
+  SPM_TRY(gemm_tc(M, N, K, 3, a2, b2, 1.0f, T, N, 1, sk, st, sym));
+  return add2d_f32(M, N, D, ldd, T, N, st);
+}
+
+// Shifted CholeskyQR of the FP32 basis X (rows x c) on tensor cores with
+// FP32-equivalent products (tc_six): the Gram X^T X and X L^{-T}.  For the
+// sketch-side iterate Z = A~^T Y, conditioned like kappa(A~)^2, whose tail a
+// two-part split resolves too coarsely (the leading singular values moved by
+// ~1.6e-4 on the sigma_i = 1/i workload).  On return X holds Q and (Xhi, Xlo)
+// its two-part split (row-major, ld pad8(c)).
+static int orth_mixed6(Call& C, float* X, int64_t rows, int64_t c, int64_t ldx,
+                       __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int passes) {
+  Arena ar(C.st);  // scratch of this call only (freed in stream order on return)
+  const int sdt = C.small64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(sdt);
+  const int64_t cp = pad8(c);
+  SPM_ALLOC(ar, float, G, c * c);
+  SPM_ALLOC(ar, float, T, max64(c, rows) * c);
+  void* Gs = ar.alloc<unsigned char>(c * c * es);
+  void* Li = ar.alloc<unsigned char>(c * c * es);
+  if (!Gs || !Li) return SPM_ENOMEM;
+  SPM_ALLOC(ar, __nv_bfloat16, X3, rows * cp);
+  SPM_ALLOC(ar, __nv_bfloat16, L1, c * cp);
+  SPM_ALLOC(ar, __nv_bfloat16, L2, c * cp);
+  SPM_ALLOC(ar, __nv_bfloat16, L3, c * cp);
+  SPM_ALLOC(ar, int, defl, c);
+  const __nv_bfloat16* xs[3] = {Xhi, Xlo, X3};
+  const __nv_bfloat16* ls[3] = {L1, L2, L3};
+  for (int ps = 0; ps < passes; ++ps) {
+    SPM_TRY(split3_bf16(rows, c, X, DT_F32, ldx, Xhi, Xlo, X3, cp, C.st));
+    // G = X^T X: both operands X^T (M = N = c, K = rows), MN-major
+    SPM_TRY(tc_six(c, c, rows, xs, cp, true, xs, cp, true, G, c, true, T, C.st));
+    if (sdt == DT_F64)
+      SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F64, c), C.st));
+    else
+      SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F32, c), C.st));
+    if (ps == 0) SPM_TRY(add_trace_shift(c, Gs, c, sdt, shift_coef(false, rows, c), C.st));
+    SPM_TRY(cholesky_inv(c, Gs, c, Li, c, sdt, defl, C.status, C.st));
+    // X <- X L^{-T}: A-op X (M = rows, K = c) K-major; B-op L^{-1} row-major (K-major)
+    SPM_TRY(split3_bf16(c, c, Li, sdt, c, L1, L2, L3, cp, C.st));
+    SPM_TRY(tc_six(rows, c, c, xs, cp, false, ls, cp, false, X, ldx, false, T, C.st));
+    SPM_TRY(fill_deflated(rows, c, X, ldx, DT_F32, defl, 0x5EED0400u + ps, C.st));
+    C.cholqr_passes++;
+  }
+  SPM_TRY(split_bf16(rows, c, rowmajor(X, DT_F32, ldx), mrowmajor(Xhi, DT_BF16, cp),
+                     mrowmajor(Xlo, DT_BF16, cp), C.st));
+  return SPM_OK;
+}
+
 // ------------------------------------------------------------------ Algorithm 1
 // Result of the range finder, kept on the device for the finishing steps.
 struct RF {
@@ -303,16 +364,18 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
       SPM_TRY(tc_split(r1, r2, m, At, Alo, r1p, true, Qhi, Qlo, r2p, true, pp, Z, r2, 1, C.st));
     }
     if (C.reorth) {
-      // FP32 on CUDA cores: a split-BF16 Gram of this iterate (conditioned
-      // like kappa(A~)^2) moves the leading singular values by ~1.7e-4 on the
-      // sigma_i = 1/i workload; the FP32 Gram keeps them within 1e-4
+      // Z <- orth(Z) on tensor cores with FP32-equivalent products (shifted
+      // pass + one plain pass); (Zhi, Zlo) is then its split
       StageScope sc(C.timer, SPM_STAGE_ORTH);
-      SPM_TRY(orth_small_f32(C, Z, r1, r2, r2, 2));  // shifted pass + one plain pass
+      const int keep = C.cholqr_passes;
+      SPM_TRY(orth_mixed6(C, Z, r1, r2, r2, Zhi, Zlo, 2));
+      C.cholqr_passes = keep;
     }
     {
       StageScope sc(C.timer, SPM_STAGE_POWER);
-      SPM_TRY(split_bf16(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
-                         mrowmajor(Zlo, DT_BF16, r2p), C.st));
+      if (!C.reorth)
+        SPM_TRY(split_bf16(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
+                           mrowmajor(Zlo, DT_BF16, r2p), C.st));
       SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
     }
   }

@@ -165,6 +165,60 @@ int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStrea
   return SPM_OK;
 }
 
+// Three-part BF16 split x ~ p1 + p2 + p3 (24 significant bits: each part is
+// the BF16 rounding of what the previous parts leave), row-major outputs.
+template <typename TX>
+__global__ void k_split3(int64_t rows, int64_t cols, const TX* __restrict__ x, int64_t xrs,
+                         __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2,
+                         __nv_bfloat16* __restrict__ p3, int64_t prs) {
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const float v = (float)x[i * xrs + j];
+      const __nv_bfloat16 a = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(a);
+      const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+      p1[i * prs + j] = a;
+      p2[i * prs + j] = b;
+      p3[i * prs + j] = c;
+    }
+}
+
+int split3_bf16(int64_t rows, int64_t cols, const void* x, int dt, int64_t ldx, __nv_bfloat16* p1,
+                __nv_bfloat16* p2, __nv_bfloat16* p3, int64_t ldp, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return SPM_OK;
+  const int gx = (int)min64(cdiv(cols, 256), 64);
+  const int gy = (int)min64(rows, max64(1, (152 * 32) / gx));
+  if (dt == DT_F32)
+    k_split3<float><<<dim3(gx, gy), 256, 0, st>>>(rows, cols, (const float*)x, ldx, p1, p2, p3, ldp);
+  else if (dt == DT_F64)
+    k_split3<double><<<dim3(gx, gy), 256, 0, st>>>(rows, cols, (const double*)x, ldx, p1, p2, p3, ldp);
+  else
+    return SPM_EINVAL;
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+// D += T (rows x cols FP32, row-major)
+__global__ void k_add2d(int64_t rows, int64_t cols, float* __restrict__ D, int64_t ldd,
+                        const float* __restrict__ T, int64_t ldt) {
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols;
+         j += (int64_t)gridDim.x * blockDim.x)
+      D[i * ldd + j] += T[i * ldt + j];
+}
+
+int add2d_f32(int64_t rows, int64_t cols, float* D, int64_t ldd, const float* T, int64_t ldt,
+              cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return SPM_OK;
+  const int gx = (int)min64(cdiv(cols, 256), 64);
+  const int gy = (int)min64(rows, max64(1, (152 * 32) / gx));
+  k_add2d<<<dim3(gx, gy), 256, 0, st>>>(rows, cols, D, ldd, T, ldt);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
 // ------------------------------------------------------------------ Cholesky
 // Leaf size of the blocked Cholesky: 128 in FP32, 64 in FP64 (shared memory).
 template <typename T>

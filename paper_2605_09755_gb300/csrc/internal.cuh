@@ -71,6 +71,12 @@ bool tc_available();
 int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st);
 // hi = bf16(x), lo = bf16(x - hi)  (split-precision operands)
 int split_bf16(int64_t rows, int64_t cols, View x, MView hi, MView lo, cudaStream_t st);
+// x (row-major, FP32 or FP64, ld ldx) ~ p1 + p2 + p3 in BF16 (row-major, ld ldp)
+int split3_bf16(int64_t rows, int64_t cols, const void* x, int dt, int64_t ldx, __nv_bfloat16* p1,
+                __nv_bfloat16* p2, __nv_bfloat16* p3, int64_t ldp, cudaStream_t st);
+// D += T, FP32 row-major
+int add2d_f32(int64_t rows, int64_t cols, float* D, int64_t ldd, const float* T, int64_t ldt,
+              cudaStream_t st);
 // Cholesky G = L L^T of an r x r SPD matrix (row-major, ld), lower L in place,
 // and Linv = L^{-1} (row-major, ldi).  dt: F32 or F64.  Breakdown -> status.
 // Deflated columns (pivot <= tol * max diag) are flagged in defl[r] (may be

@@ -5,10 +5,13 @@
 //   * CTA 0 factors the diagonal tile (blocked by 16 inside the tile: a warp
 //     factors each 16 x 16 block in registers, then a panel solve and a
 //     trailing update in shared memory) and inverts it;
-//   * all CTAs form the panel L[ib][p] = G[ib][p] L_pp^{-T} (ib > p);
-//   * all CTAs apply the trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T;
-//     the tile (p + 1, p + 1) goes to CTA 0, which factors it right away.
-// Two bounded grid barriers per panel.  The off-diagonal tiles of L^{-1} then
+//   * the CTAs form the panel L[ib][p] = G[ib][p] L_pp^{-T} (ib > p), CTA 0
+//     the tile p + 1, each tile published by a flag;
+//   * the CTAs apply the trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T,
+//     each waiting only for the flags of its two panel tiles; the tile
+//     (p + 1, p + 1) goes to CTA 0, which factors it right away, so the
+//     diagonal chain does not wait for the rest of the panel.
+// One bounded grid barrier per panel.  The off-diagonal tiles of L^{-1} then
 // follow by recursive doubling: for a lower-triangular [L11 0; L21 L22],
 //   inv(L)_21 = -inv(L22) (L21 inv(L11)),
 // applied level by level over groups of 1, 2, 4, ... tiles, two products and
@@ -131,45 +134,55 @@ __device__ __forceinline__ double rsqrt_t(double d) { return 1.0 / sqrt(d); }
 // beyond b) in place into L, and write L^{-1} into inv.  Deflated columns get
 // flag 1 in defl[0..b) (global) and are e_j in L.
 template <typename T>
-__device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl, int* bad) {
+__device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl, int* bad) {
   __shared__ unsigned dfl16;
   __shared__ T rdg[CT];  // 1 / L_ii (1 for a deflated column)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int o = 0; o < CT; o += 16) {
-    // (1) one warp factors the 16 x 16 diagonal block in registers (lane = row)
+    // (1) one warp factors the 16 x 16 diagonal block in registers (lane = row).
+    // Branch-free: the pivot test is uniform and every per-lane choice is a
+    // select, so the column-to-column chain holds only the pivot broadcast,
+    // its rsqrt and the broadcasts of the new column.
     if (warp == 0) {
       T row[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) row[c] = (lane < 16 && c <= lane) ? a[o + lane][o + c] : (T)0;
       unsigned df = 0;
+      bool nonfinite = false;
+      T my_rdg = (T)1;
+      T dnext = __shfl_sync(0xFFFFFFFFu, row[0], 0);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const T d = __shfl_sync(0xFFFFFFFFu, row[c], c);
+        const T d = dnext;
         const bool fin = isfinite(d);
         const bool piv = fin && (d > thr);
-        if (!fin && lane == 0) *bad = 1;
-        if (piv) {
-          const T isd = rsqrt_t(d);
-          const T lc = (lane == c) ? d * isd : ((lane > c) ? row[c] * isd : (T)0);
-          if (lane == 0) rdg[o + c] = isd;
-          row[c] = lc;
+        nonfinite |= !fin;
+        const T isd = rsqrt_t(piv ? d : (T)1);
+        const T lc = piv ? ((lane == c) ? d * isd : ((lane > c) ? row[c] * isd : (T)0))
+                         : ((lane == c) ? (T)1 : (T)0);
+        my_rdg = (lane == c) ? (piv ? isd : (T)1) : my_rdg;
+        df |= piv ? 0u : (1u << c);
+        row[c] = lc;
+        const T nlc = piv ? -lc : (T)0;
+        // the next pivot, from lane c + 1's own entry (the same multiply-add
+        // as its update below), broadcast before the other lanes' updates
+        if (c + 1 < 16) dnext = __shfl_sync(0xFFFFFFFFu, fma(nlc, lc, row[c + 1]), c + 1);
 #pragma unroll
-          for (int k = c + 1; k < 16; ++k) {
-            const T lkc = __shfl_sync(0xFFFFFFFFu, lc, k);
-            if (lane >= k) row[k] -= lc * lkc;
-          }
-        } else {
-          row[c] = (lane == c) ? (T)1 : (T)0;
-          if (lane == 0) rdg[o + c] = (T)1;
-          df |= 1u << c;
+        for (int k = c + 1; k < 16; ++k) {
+          const T lkc = __shfl_sync(0xFFFFFFFFu, lc, k);
+          row[k] = fma((lane >= k) ? nlc : (T)0, lkc, row[k]);
         }
       }
       if (lane < 16) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) a[o + lane][o + c] = (c <= lane) ? row[c] : (T)0;
+        rdg[o + lane] = my_rdg;
         if (defl && o + lane < b) defl[o + lane] = (df >> lane) & 1u;
       }
-      if (lane == 0) dfl16 = df;
+      if (lane == 0) {
+        dfl16 = df;
+        if (nonfinite) *bad = 1;
+      }
     }
     __syncthreads();
     const int nbelow = CT - o - 16;
@@ -204,38 +217,78 @@ __device__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T thr, int* defl,
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular tile: thread c owns column c and runs the
-  // forward substitution x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii down it
-  // (1 / L_ii from the table, so the dependent chain holds no division)
-  // with the column in registers (x_k = 0 above the diagonal comes out of the
-  // same formula); four partial sums shorten the dependent chain.
-  if (tid < CT) {
-    const int c = tid;
-    T x[CT];
+  // inverse of the lower-triangular tile by blocks, with
+  //   inv([A 0; B C]) = [inv(A) 0; -inv(C) B inv(A), inv(C)]:
+  // (1) each 16 x 16 diagonal block by one warp (lane = column, forward
+  //     substitution in registers, 1 / L_ii from the table), the blocks above
+  //     the diagonal zeroed by the other warps;
+  // (2) the two 32 x 32 diagonal blocks: off-diagonal 16 x 16 blocks (1, 0), (3, 2);
+  // (3) the 64 x 64 tile: off-diagonal 32 x 32 block.
+  __shared__ T tmp[32][33];
+  if (warp < 4) {
+    const int o = warp * 16, c = lane;
+    if (c < 16) {
+      T x[16];
 #pragma unroll
-    for (int i = 0; i < CT; ++i) {
-      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+      for (int i = 0; i < 16; ++i) {
+        T s = (i == c) ? (T)1 : (T)0;
 #pragma unroll
-      for (int k = 0; k + 3 < i; k += 4) {
-        s0 = fma(a[i][k], x[k], s0);
-        s1 = fma(a[i][k + 1], x[k + 1], s1);
-        s2 = fma(a[i][k + 2], x[k + 2], s2);
-        s3 = fma(a[i][k + 3], x[k + 3], s3);
+        for (int k = 0; k < i; ++k) s = fma(-a[o + i][o + k], x[k], s);
+        x[i] = s * rdg[o + i];  // x_i = 0 above the diagonal (i < c) by the same formula
       }
 #pragma unroll
-      for (int k = i & ~3; k < i; ++k) s0 = fma(a[i][k], x[k], s0);
-      const T rhs = ((i == c) ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
-      x[i] = rhs * rdg[i];
+      for (int i = 0; i < 16; ++i) inv[o + i][o + c] = x[i];
     }
+  } else {
+    for (int e = tid - 128; e < CT * CT; e += CTHREADS - 128) {
+      const int i = e >> 6, j = e & 63;
+      if ((j >> 4) > (i >> 4)) inv[i][j] = (T)0;
+    }
+  }
+  __syncthreads();
+  {
+    // (2) T = L[b+1][b] inv(D_b) for b = 0, 2 (one element per thread), then
+    //     inv[b+1][b] = -inv(D_{b+1}) T
+    const int q = tid >> 8, e = tid & 255, i = e >> 4, j = e & 15, b = 32 * q;
+    T acc = (T)0;
 #pragma unroll
-    for (int i = 0; i < CT; ++i) inv[i][c] = x[i];
+    for (int k = 0; k < 16; ++k) acc = fma(a[b + 16 + i][b + k], inv[b + k][b + j], acc);
+    tmp[16 * q + i][j] = acc;
+    __syncthreads();
+    acc = (T)0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(inv[b + 16 + i][b + 16 + k], tmp[16 * q + k][j], acc);
+    inv[b + 16 + i][b + j] = -acc;
+    __syncthreads();
+  }
+  {
+    // (3) T = L[32:64][0:32] inv[0:32][0:32] (two elements per thread), then
+    //     inv[32:64][0:32] = -inv[32:64][32:64] T
+    const int i = tid >> 4, j0 = tid & 15;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + 16 * h;
+      T acc = (T)0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fma(a[32 + i][k], inv[k][j], acc);
+      tmp[i][j] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + 16 * h;
+      T acc = (T)0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fma(inv[32 + i][32 + k], tmp[k][j], acc);
+      inv[32 + i][j] = -acc;
+    }
   }
   __syncthreads();
 }
 
 // CTA-wide: factor diagonal tile p of G into G (L) and Li (L^{-1}).
 template <typename T>
-__device__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi, T thr, int* defl,
+__device__ __forceinline__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi, T thr, int* defl,
                             T (*s0)[CLD], T (*s1)[CLD], int* bad) {
   const int o = p * CT, b = min(CT, r - o);
   for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
@@ -259,11 +312,43 @@ __device__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi,
   __syncthreads();
 }
 
+// Point-to-point publication of a finished tile: the CTA's writes, then the
+// flag (epochs only grow, so the flags need no reset between panels).
+__device__ __forceinline__ void post_flag(int* flag, int epoch) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicMax(flag, epoch);
+  }
+}
+// Bounded wait (thread 0) until *flag >= epoch; false, with the status set,
+// if it never came.
+__device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* status) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile const int* vf = flag;
+    if (*vf < epoch) {
+      const long long t0 = clock64();
+      while (*vf < epoch) {
+        if (clock64() - t0 > (1ll << 32)) {
+          set_status(status, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(CTHREADS, 1)
     k_chol_coop(int r, T* __restrict__ G, int64_t ldg, T* __restrict__ Li, int64_t ldi,
                 T* __restrict__ Tm, int64_t ldt, T tol, int* __restrict__ defl,
-                int* __restrict__ status, GridBar gb) {
+                int* __restrict__ flags, int* __restrict__ status, GridBar gb) {
   extern __shared__ __align__(16) unsigned char cc_smem[];
   T(*s0)[CLD] = reinterpret_cast<T(*)[CLD]>(cc_smem);
   T(*s1)[CLD] = s0 + CT;
@@ -302,8 +387,13 @@ __global__ void __launch_bounds__(CTHREADS, 1)
 
   for (int p = 0; p + 1 < nt; ++p) {
     const int o = p * CT;
-    // panel: L[ib][p] = G[ib][p] inv(L_pp)^T, deflated columns zeroed
-    for (int ib = p + 1 + cta; ib < nt; ib += nb) {
+    // panel: L[ib][p] = G[ib][p] inv(L_pp)^T, deflated columns zeroed.  CTA 0
+    // takes tile p + 1 (then updates and factors the next diagonal tile at
+    // once), CTAs 1.. the tiles below it; each tile is published by its flag
+    // (epoch p + 1), which the trailing updates wait for.
+    const int ib0 = (nb == 1) ? p + 1 : ((cta == 0) ? p + 1 : p + 1 + cta);
+    const int ibs = (nb == 1) ? 1 : ((cta == 0) ? nt : (int)nb - 1);
+    for (int ib = ib0; ib < nt; ib += ibs) {
       ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
       ld_tile<T>(s1, Li, ldi, o, o, r, r, true);
       __syncthreads();
@@ -317,10 +407,10 @@ __global__ void __launch_bounds__(CTHREADS, 1)
           const int i = ib * CT + ty + 32 * v, j = o + tx + 16 * u;
           if (i < r && j < r) G[(int64_t)i * ldg + j] = __ldcg(defl + j) ? (T)0 : acc[v][u];
         }
-      __syncthreads();
+      post_flag(flags + ib, p + 1);
     }
-    if (!grid_sync(gb, nb, status)) return;
-    // trailing update; tile index t = 0 is the next diagonal tile (CTA 0)
+    // trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T, p + 1 <= jb <= ib; tile
+    // index t = 0 is the next diagonal tile (CTA 0, which then factors it)
     const int rest = nt - p - 1;
     const int ntr = rest * (rest + 1) / 2;
     int t0, step;
@@ -341,6 +431,7 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       while (ii * (ii + 1) / 2 > t) --ii;
       const int jj = t - ii * (ii + 1) / 2;
       const int ib = p + 1 + ii, jb = p + 1 + jj;
+      if (!wait_flag(flags + ib, p + 1, status) || !wait_flag(flags + jb, p + 1, status)) return;
       ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
       ld_tile<T>(s1, G, ldg, jb * CT, o, r, r, true);
       __syncthreads();
@@ -358,7 +449,6 @@ __global__ void __launch_bounds__(CTHREADS, 1)
           }
         }
       __syncthreads();
-      if (nb > 1 && cta == 0) break;
     }
     if (cta == 0) factor_tile<T>(p + 1, r, G, ldg, Li, ldi, thr_s, defl, s0, s1, &bad);
     if (!grid_sync(gb, nb, status)) return;
@@ -435,17 +525,20 @@ static int cholesky_inv_coop_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi,
   Arena ar(st);
   SPM_ALLOC(ar, T, Tm, (int64_t)nt * CT * nt * CT);
   SPM_ALLOC(ar, unsigned, bar, 2);
+  SPM_ALLOC(ar, int, flags, nt);
   if (!defl) {
     defl = ar.alloc<int>(r);
     if (!defl) return SPM_ENOMEM;
   }
   SPM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  SPM_CUDA_TRY(cudaMemsetAsync(flags, 0, nt * sizeof(int), st));
   GridBar gb{bar, bar + 1};
   int rr = (int)r;
   int64_t ldt = (int64_t)nt * CT;
   T tolv = tol;
   void* args[] = {(void*)&rr, (void*)&G, (void*)&ldg, (void*)&Li, (void*)&ldi, (void*)&Tm,
-                  (void*)&ldt, (void*)&tolv, (void*)&defl, (void*)&status, (void*)&gb};
+                  (void*)&ldt, (void*)&tolv, (void*)&defl, (void*)&flags, (void*)&status,
+                  (void*)&gb};
   SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(CTHREADS), args, smem, st));
   count_launch();
   return SPM_OK;

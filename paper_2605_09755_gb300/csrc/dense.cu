@@ -615,7 +615,8 @@ __device__ __forceinline__ void rot_params<float>(float app, float aqq, float ap
   if (fabsf(apq) <= 1e-37f) return;
   const float tau = (aqq - app) * __fdividef(0.5f, apq);
   const float at = fabsf(tau);
-  const float t = copysignf(at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + sqrtf(fmaf(at, at, 1.f))), tau);
+  const float y = fmaf(at, at, 1.f);  // sqrt(y) as y rsqrt(y): only the angle sees its error
+  const float t = copysignf(at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + y * rsqrtf(y)), tau);
   const float x = fmaf(t, t, 1.f);
   const float r = rsqrtf(x);
   c = fmaf(0.5f * r, fmaf(-(x * r), r, 1.f), r);

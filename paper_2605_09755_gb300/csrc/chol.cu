@@ -286,10 +286,28 @@ __device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T
   __syncthreads();
 }
 
+// CTA-wide: factor diagonal tile p, held (lower part, identity padding beyond
+// the matrix) in shared memory a, and store L into G and L^{-1} into Li.
+template <typename T>
+__device__ __forceinline__ void factor_tile_smem(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi,
+                                                 T thr, int* defl, T (*a)[CLD], T (*inv)[CLD],
+                                                 int* bad) {
+  const int o = p * CT, b = min(CT, r - o);
+  diag_factor<T>(a, inv, b, thr, defl ? defl + o : nullptr, bad);
+  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
+    const int i = e >> 6, j = e & 63;
+    if (i < b && j < b) {
+      G[(int64_t)(o + i) * ldg + o + j] = a[i][j];
+      Li[(int64_t)(o + i) * ldi + o + j] = inv[i][j];
+    }
+  }
+  __syncthreads();
+}
+
 // CTA-wide: factor diagonal tile p of G into G (L) and Li (L^{-1}).
 template <typename T>
-__device__ __forceinline__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi, T thr, int* defl,
-                            T (*s0)[CLD], T (*s1)[CLD], int* bad) {
+__device__ __forceinline__ void factor_tile(int p, int r, T* G, int64_t ldg, T* Li, int64_t ldi, T thr,
+                                            int* defl, T (*s0)[CLD], T (*s1)[CLD], int* bad) {
   const int o = p * CT, b = min(CT, r - o);
   for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
     const int i = e >> 6, j = e & 63;
@@ -301,15 +319,7 @@ __device__ __forceinline__ void factor_tile(int p, int r, T* G, int64_t ldg, T* 
     s0[i][j] = v;
   }
   __syncthreads();
-  diag_factor<T>(s0, s1, b, thr, defl ? defl + o : nullptr, bad);
-  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
-    const int i = e >> 6, j = e & 63;
-    if (i < b && j < b) {
-      G[(int64_t)(o + i) * ldg + o + j] = s0[i][j];
-      Li[(int64_t)(o + i) * ldi + o + j] = s1[i][j];
-    }
-  }
-  __syncthreads();
+  factor_tile_smem<T>(p, r, G, ldg, Li, ldi, thr, defl, s0, s1, bad);
 }
 
 // Point-to-point publication of a finished tile: the CTA's writes, then the
@@ -387,70 +397,105 @@ __global__ void __launch_bounds__(CTHREADS, 1)
 
   for (int p = 0; p + 1 < nt; ++p) {
     const int o = p * CT;
-    // panel: L[ib][p] = G[ib][p] inv(L_pp)^T, deflated columns zeroed.  CTA 0
-    // takes tile p + 1 (then updates and factors the next diagonal tile at
-    // once), CTAs 1.. the tiles below it; each tile is published by its flag
-    // (epoch p + 1), which the trailing updates wait for.
-    const int ib0 = (nb == 1) ? p + 1 : ((cta == 0) ? p + 1 : p + 1 + cta);
-    const int ibs = (nb == 1) ? 1 : ((cta == 0) ? nt : (int)nb - 1);
-    for (int ib = ib0; ib < nt; ib += ibs) {
-      ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
+    // panel: L[ib][p] = G[ib][p] inv(L_pp)^T, deflated columns zeroed, each
+    // tile published by its flag (epoch p + 1), which the trailing updates
+    // wait for.  CTA 0 takes tile p + 1 and, without a round trip through
+    // global memory, updates the next diagonal tile with it and factors it
+    // (the chain every later panel waits for); CTAs 1.. take the tiles below.
+    if (nb > 1 && cta == 0) {
+      const int ib = p + 1, od = ib * CT, b = min(CT, r - od);
+      ld_tile<T>(s0, G, ldg, od, o, r, r, true);
       ld_tile<T>(s1, Li, ldi, o, o, r, r, true);
       __syncthreads();
       T acc[2][4];
       acc_zero(acc);
       tile_mma<T>(acc, s0, s1);
+      TileRegs<T> gd;  // the diagonal tile before this panel's update
+      ld_regs(gd, (const T*)G, ldg, od, od, r, r);
+      __syncthreads();
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = ib * CT + ty + 32 * v, j = o + tx + 16 * u;
-          if (i < r && j < r) G[(int64_t)i * ldg + j] = __ldcg(defl + j) ? (T)0 : acc[v][u];
+          const int i = od + ty + 32 * v, j = o + tx + 16 * u;
+          const bool in = i < r && j < r;
+          const T val = (in && !__ldcg(defl + j)) ? acc[v][u] : (T)0;
+          if (in) G[(int64_t)i * ldg + j] = val;
+          s0[tx + 16 * u][ty + 32 * v] = val;  // transposed: s0[k][i] = L[i][k]
         }
       post_flag(flags + ib, p + 1);
-    }
-    // trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T, p + 1 <= jb <= ib; tile
-    // index t = 0 is the next diagonal tile (CTA 0, which then factors it)
-    const int rest = nt - p - 1;
-    const int ntr = rest * (rest + 1) / 2;
-    int t0, step;
-    if (nb == 1) {
-      t0 = 0;
-      step = 1;
-    } else if (cta == 0) {
-      t0 = 0;
-      step = ntr;  // only tile 0
-    } else {
-      t0 = cta;    // tiles 1.. over CTAs 1..nb-1
-      step = nb - 1;
-    }
-    for (int t = t0; t < ntr; t += step) {
-      // t -> (ib, jb) with p + 1 <= jb <= ib, row-major over the lower triangle
-      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      const int jj = t - ii * (ii + 1) / 2;
-      const int ib = p + 1 + ii, jb = p + 1 + jj;
-      if (!wait_flag(flags + ib, p + 1, status) || !wait_flag(flags + jb, p + 1, status)) return;
-      ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
-      ld_tile<T>(s1, G, ldg, jb * CT, o, r, r, true);
-      __syncthreads();
-      T acc[2][4];
       acc_zero(acc);
-      tile_mma<T>(acc, s0, s1);
+      tile_mma<T>(acc, s0, s0);  // L L^T of the diagonal tile
+      st_regs(s1, gd, false);
+      __syncthreads();
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
-          if (i < r && j < r && j <= i) {
-            T* g = G + (int64_t)i * ldg + j;
-            *g = __ldcg(g) - acc[v][u];
-          }
-        }
+        for (int u = 0; u < 4; ++u) s1[ty + 32 * v][tx + 16 * u] -= acc[v][u];
       __syncthreads();
+      // lower part only, identity beyond the matrix
+      for (int e = tid; e < CT * CT; e += CTHREADS) {
+        const int i = e >> 6, j = e & 63;
+        if (i >= b || j >= b)
+          s1[i][j] = (i == j) ? (T)1 : (T)0;
+        else if (j > i)
+          s1[i][j] = (T)0;
+      }
+      __syncthreads();
+      factor_tile_smem<T>(ib, r, G, ldg, Li, ldi, thr_s, defl, s1, s0, &bad);
+    } else {
+      const int ib0 = (nb == 1) ? p + 1 : p + 1 + cta;
+      const int ibs = (nb == 1) ? 1 : (int)nb - 1;
+      for (int ib = ib0; ib < nt; ib += ibs) {
+        ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
+        ld_tile<T>(s1, Li, ldi, o, o, r, r, true);
+        __syncthreads();
+        T acc[2][4];
+        acc_zero(acc);
+        tile_mma<T>(acc, s0, s1);
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = ib * CT + ty + 32 * v, j = o + tx + 16 * u;
+            if (i < r && j < r) G[(int64_t)i * ldg + j] = __ldcg(defl + j) ? (T)0 : acc[v][u];
+          }
+        post_flag(flags + ib, p + 1);
+      }
+      // trailing update G[ib][jb] -= L[ib][p] L[jb][p]^T, p + 1 <= jb <= ib,
+      // row-major over the lower triangle; tile t = 0, the next diagonal tile,
+      // is CTA 0's (above) unless one CTA does all
+      const int rest = nt - p - 1;
+      const int ntr = rest * (rest + 1) / 2;
+      const int t0 = (nb == 1) ? 0 : cta;
+      const int step = (nb == 1) ? 1 : (int)nb - 1;
+      for (int t = t0; t < ntr; t += step) {
+        int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+        while (ii * (ii + 1) / 2 > t) --ii;
+        const int jj = t - ii * (ii + 1) / 2;
+        const int ib = p + 1 + ii, jb = p + 1 + jj;
+        if (!wait_flag(flags + ib, p + 1, status) || !wait_flag(flags + jb, p + 1, status)) return;
+        ld_tile<T>(s0, G, ldg, ib * CT, o, r, r, true);
+        ld_tile<T>(s1, G, ldg, jb * CT, o, r, r, true);
+        __syncthreads();
+        T acc[2][4];
+        acc_zero(acc);
+        tile_mma<T>(acc, s0, s1);
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
+            if (i < r && j < r && j <= i) {
+              T* g = G + (int64_t)i * ldg + j;
+              *g = __ldcg(g) - acc[v][u];
+            }
+          }
+        __syncthreads();
+      }
+      if (nb == 1) factor_tile<T>(p + 1, r, G, ldg, Li, ldi, thr_s, defl, s0, s1, &bad);
     }
-    if (cta == 0) factor_tile<T>(p + 1, r, G, ldg, Li, ldi, thr_s, defl, s0, s1, &bad);
     if (!grid_sync(gb, nb, status)) return;
   }
 

@@ -15,6 +15,8 @@
 // the final basis is orth(Y).  In exact arithmetic this equals Algorithm 1.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace spm {
@@ -41,8 +43,28 @@ struct Call {
 
 static int64_t pad8(int64_t x) { return round_up(x, 8); }
 
-// sym: only the tiles a symmetric product computes (clusters of two M tiles
-// that reach the upper triangle) count.
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      return 152;
+  }
+  return sms;
+}
+
+// Split-K factor of a tensor-core product from a small cost model:
+//   waves(sk) x (t0 + ceil(kt / sk) x tk) + [sk > 1] (t0 + sk M N 8 B / HBM)
+// (waves of the tiles x splits work units over the SMs; a CTA's set-up t0,
+// one 64-deep k-tile of a 128 x 256 tile in three passes tk; the split-K
+// partials written and read back once).  Whole waves matter for the few
+// large products (1000 x 16384 output tiles: 3.4 waves unsplit, 6.7 at two
+// splits); the partials' traffic for the short-K ones.  sym: only the tiles a
+// symmetric product computes (clusters of two M tiles that reach the upper
+// triangle) count.
 static int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false) {
   const int BN = (N >= 192) ? 256 : 128;
   int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
@@ -54,9 +76,21 @@ static int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false) {
         if (c * cl * 128 < (j + 1) * BN) tiles += cl;
   }
   const int64_t kt = cdiv(K, 64);
-  int64_t sk = cdiv(2 * 152, tiles);
-  sk = min64(sk, max64(kt / 4, 1));
-  return (int)max64(sk, 1);
+  const int64_t sms = sm_count();
+  const double t0 = 3e-6, tk = 1.3e-6, hbm = 6.5e12;
+  const int64_t skmax = max64(1, min64(kt / 4, 32));
+  auto cost = [&](int64_t sk) {
+    const double waves = (double)cdiv(tiles * sk, sms);
+    double c = waves * (t0 + (double)cdiv(kt, sk) * tk);
+    if (sk > 1) c += t0 + (double)sk * (double)M * (double)N * 8.0 / hbm;
+    return c;
+  };
+  double cmin = cost(1);
+  for (int64_t sk = 2; sk <= skmax; ++sk) cmin = std::min(cmin, cost(sk));
+  // the fewest splits within 2% of the best (the model is coarse)
+  for (int64_t sk = 1; sk <= skmax; ++sk)
+    if (cost(sk) <= 1.02 * cmin) return (int)sk;
+  return 1;
 }
 
 // Split-precision tensor-core product: D = sum of npass terms over (hi, lo) pairs.

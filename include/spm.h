@@ -117,6 +117,13 @@ int spm_version(void);
 const char* spm_status_string(int status);
 /* 1 if the current CUDA device is sm_103 and the kernels loaded, else 0. */
 int spm_device_ok(void);
+
+/* Device workspace comes from a memory pool of the library's own, one per
+ * device, which keeps freed blocks for the next call (so repeated calls do not
+ * map and unmap gigabytes of workspace at every synchronisation).  This call
+ * waits for the current device and hands the pool's unused memory back to it.
+ * Returns SPM_OK, or SPM_ECUDA if the pool or the device is unusable. */
+int spm_trim_memory(void);
 /* Number of kernels this library has launched in the process so far (host-side
  * counter, all threads).  Used to report launches per step. */
 uint64_t spm_launch_count(void);
@@ -179,6 +186,22 @@ int spm_rsvd(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64
              int64_t r2, int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts,
              void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, spm_info* info,
              void* stream);
+
+/* ---- a6 with host buffers: RandSVD of a matrix in host memory ---------------
+ * What spm_rsvd computes, with A (m x n, ld lda), U, sigma and Vt in HOST memory
+ * (page-locked for the copies to run asynchronously; pageable memory works but
+ * its copies block the calling thread).  A is staged into device memory in row
+ * chunks on a separate copy stream, and in MIXED precision the sketch product
+ * A S of each chunk starts as soon as that chunk has arrived, so the transfer
+ * and the sketch pass overlap; the results are copied back on `stream`.
+ * Device memory: the staged A (m x n) and the outputs on top of spm_rsvd's
+ * workspace, all released in stream order.  Returns like spm_rsvd; the host
+ * outputs are complete once `stream` has been synchronised (spm_rsvd_host does
+ * that itself when info != NULL). */
+int spm_rsvd_host(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                  int64_t r2, int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts,
+                  void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, spm_info* info,
+                  void* stream);
 
 /* ---- a7: Algorithm 2, Sketch-Powered Low-Rank Factorization ------------------
  * Y (m x r2, ld ldy) and X (r2 x n, ld ldx) with A ~ Y X, X = (S2^T Y)^+ (S2^T A).

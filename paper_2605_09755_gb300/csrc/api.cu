@@ -16,6 +16,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -38,10 +40,57 @@ struct Call {
   double* acc = nullptr;  // [0] = |A|_F^2, [1] = |B|_F^2
   StageTimer timer;
   int cholqr_passes = 0;
+  // A fed from the host (spm_rsvd_host): row chunks of feed_rows rows arrive
+  // on another stream, chunk c usable on st after feed_ev[c]
+  int feed_n = 0;
+  int64_t feed_rows = 0;
+  const cudaEvent_t* feed_ev = nullptr;
   explicit Call(cudaStream_t s) : st(s), ar(s) { timer.stream = s; }
 };
 
+// Make st wait for every chunk of a host-fed A (a no-op otherwise).
+static int await_feed(const Call& C) {
+  for (int c = 0; c < C.feed_n; ++c) SPM_CUDA_TRY(cudaStreamWaitEvent(C.st, C.feed_ev[c], 0));
+  return SPM_OK;
+}
+
 static int64_t pad8(int64_t x) { return round_up(x, 8); }
+
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[16] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;  // keep freed memory for the next call
+    if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return nullptr;
+    }
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+// One non-blocking stream per device for host staging copies (kept for the
+// life of the process).
+static cudaStream_t copy_stream() {
+  static std::mutex mu;
+  static cudaStream_t cs[16] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cs[dev] && cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking) != cudaSuccess)
+    cs[dev] = nullptr;
+  return cs[dev];
+}
 
 static int sm_count() {
   static int sms = 0;
@@ -344,6 +393,7 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
   const int64_t n = S->n, r1 = S->r1;
   out.m = m;
   out.r2 = r2;
+  if (C.prec != SPM_PREC_MIXED) SPM_TRY(await_feed(C));
   if (C.prec == SPM_PREC_FP64) return range_finder_simt<double>(C, S, A, m, lda, r2, q, seed, out);
   if (C.prec == SPM_PREC_FP32) return range_finder_simt<float>(C, S, A, m, lda, r2, q, seed, out);
   // ---------------- mixed precision
@@ -373,7 +423,19 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
   }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st, Atlo));
+    if (C.feed_n > 0) {
+      // host-fed A: each row chunk's sketch product as soon as the chunk is here
+      const size_t es = dt_size(C.adt);
+      for (int c = 0; c < C.feed_n; ++c) {
+        const int64_t r0 = (int64_t)c * C.feed_rows, rows = min64(C.feed_rows, m - r0);
+        SPM_CUDA_TRY(cudaStreamWaitEvent(C.st, C.feed_ev[c], 0));
+        SPM_TRY(sketch_apply_dev(S, (const unsigned char*)A + (size_t)r0 * lda * es, C.adt, rows,
+                                 lda, At + r0 * r1p, DT_BF16, r1p, C.acc, C.st,
+                                 Atlo ? Atlo + r0 * r1p : nullptr));
+      }
+    } else {
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st, Atlo));
+    }
   }
   const __nv_bfloat16* Alo = Atlo ? Atlo : At;
   {
@@ -641,6 +703,13 @@ const char* spm_status_string(int s) {
 
 int spm_device_ok(void) { return tc_available() ? 1 : 0; }
 
+int spm_trim_memory(void) {
+  cudaMemPool_t p = lib_pool();
+  if (!p) return SPM_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SPM_ECUDA;
+  return cudaMemPoolTrimTo(p, 0) == cudaSuccess ? SPM_OK : SPM_ECUDA;
+}
+
 uint64_t spm_launch_count(void) { return (uint64_t)g_launches.load(); }
 
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
@@ -689,6 +758,66 @@ int spm_rsvd(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64
   RF rf;
   int rc = range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf);
   if (rc == SPM_OK) rc = rsvd_finish(C, A, m, S->n, lda, rf, k, U, ldu, sigma, Vt, ldvt);
+  return finish(C, info, rc, true);
+}
+
+int spm_rsvd_host(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                  int64_t r2, int32_t q, uint64_t omega_seed, int64_t k, const spm_opts* opts,
+                  void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, spm_info* info,
+                  void* stream) {
+  SPM_TRY(check_common(S, A, dtype, m, lda, r2, q, opts));
+  if (!U || !sigma || !Vt || k < 1 || k > r2 || ldu < k || ldvt < S->n) return SPM_EINVAL;
+  const int64_t n = S->n;
+  const size_t es = dtype == SPM_F64 ? 8 : 4;
+  cudaStream_t cs = copy_stream();
+  if (!cs) return SPM_ECUDA;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  void* Ad = C.ar.alloc<unsigned char>((size_t)m * n * es);
+  void* Ud = C.ar.alloc<unsigned char>((size_t)m * k * es);
+  void* sd = C.ar.alloc<unsigned char>((size_t)k * es);
+  void* Vd = C.ar.alloc<unsigned char>((size_t)k * n * es);
+  if (!Ad || !Ud || !sd || !Vd) return SPM_ENOMEM;
+  // row chunks (whole 32-row blocks of the sketch kernel), copied on cs once
+  // the device buffer exists in C.st's order
+  const int64_t rows = round_up(cdiv(m, min64(16, max64(1, cdiv(m, 1024)))), 32);
+  const int nch = (int)cdiv(m, rows);
+  std::vector<cudaEvent_t> ev(nch + 1, nullptr);
+  int rc = SPM_OK;
+  for (int c = 0; c <= nch && rc == SPM_OK; ++c)
+    if (cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming) != cudaSuccess) rc = SPM_ECUDA;
+  if (rc == SPM_OK && (cudaEventRecord(ev[nch], C.st) != cudaSuccess ||
+                       cudaStreamWaitEvent(cs, ev[nch], 0) != cudaSuccess))
+    rc = SPM_ECUDA;
+  for (int c = 0; c < nch && rc == SPM_OK; ++c) {
+    const int64_t r0 = (int64_t)c * rows, rc_rows = min64(rows, m - r0);
+    if (cudaMemcpy2DAsync((unsigned char*)Ad + (size_t)r0 * n * es, n * es,
+                          (const unsigned char*)A + (size_t)r0 * lda * es, lda * es, n * es,
+                          rc_rows, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(ev[c], cs) != cudaSuccess)
+      rc = SPM_ECUDA;
+  }
+  if (rc == SPM_OK) {
+    C.feed_n = nch;
+    C.feed_rows = rows;
+    C.feed_ev = ev.data();
+    RF rf;
+    rc = range_finder_core(C, S, Ad, m, n, r2, q, omega_seed, rf);
+    if (rc == SPM_OK) rc = rsvd_finish(C, Ad, m, n, n, rf, k, Ud, k, sd, Vd, n);
+  }
+  // the staged A and the events are released only after every copy is done
+  const int wrc = await_feed(C);
+  if (rc == SPM_OK) rc = wrc;
+  if (rc == SPM_OK &&
+      (cudaMemcpy2DAsync(U, ldu * es, Ud, k * es, k * es, m, cudaMemcpyDeviceToHost, C.st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(sigma, sd, k * es, cudaMemcpyDeviceToHost, C.st) != cudaSuccess ||
+       cudaMemcpy2DAsync(Vt, ldvt * es, Vd, n * es, n * es, k, cudaMemcpyDeviceToHost, C.st) !=
+           cudaSuccess))
+    rc = SPM_ECUDA;
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
   return finish(C, info, rc, true);
 }
 

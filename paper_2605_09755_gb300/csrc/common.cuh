@@ -60,6 +60,12 @@ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 // Stream-ordered scratch arena: every buffer is cudaMallocAsync'ed on the
 // call's stream and released by cudaFreeAsync when the arena dies.
+// The library's stream-ordered memory pool on the current device: freed
+// blocks stay reserved for the next call instead of being handed back to the
+// device at every synchronisation (the default pool's behaviour), until
+// spm_trim_memory.  Null if it cannot be created (allocations then fail).
+cudaMemPool_t lib_pool();
+
 struct Arena {
   cudaStream_t stream;
   void* ptrs[128];
@@ -76,7 +82,8 @@ struct Arena {
     void* p = nullptr;
     // round to 256 B so that every TMA base is aligned
     size_t bytes = (size_t)round_up(elems * (int64_t)sizeof(T), 256);
-    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaMemPool_t pool = lib_pool();
+    if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
       failed = true;
       return nullptr;
     }

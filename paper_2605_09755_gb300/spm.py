@@ -68,6 +68,9 @@ _SIGS = {
                           ctypes.POINTER(Info), VP], I32),
     "spm_rsvd": ([VP, VP, I32, I64, I64, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64, VP,
                   VP, I64, ctypes.POINTER(Info), VP], I32),
+    "spm_trim_memory": ([], I32),
+    "spm_rsvd_host": ([VP, VP, I32, I64, I64, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64,
+                       VP, VP, I64, ctypes.POINTER(Info), VP], I32),
     "spm_lowrank": ([VP, VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64, VP,
                      I64, ctypes.POINTER(Info), VP], I32),
     "spm_gemm_bf16": ([I64, I64, I64, I32, ctypes.POINTER(VP), I64, I32, ctypes.POINTER(VP), I64,
@@ -227,6 +230,42 @@ def rsvd(S, A, r2, q, k, omega_seed=43, precision=PREC_FP64, timing=False, out=N
                         ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sig), _ptr(Vt), Vt.stride(0),
                         ctypes.byref(inf) if inf is not None else None, _stream())
     _check(rc, "spm_rsvd")
+    return U, sig, Vt, (inf.as_dict() if inf is not None else None)
+
+
+def trim_memory():
+    """Hand the library pool's unused device memory back to the device."""
+    _check(lib().spm_trim_memory(), "spm_trim_memory")
+
+
+def rsvd_host(S, A, r2, q, k, omega_seed=43, precision=PREC_FP64, timing=False, out=None,
+              info=True, **kw):
+    """spm_rsvd_host: RandSVD of a host (CPU) matrix, results in host tensors.
+
+    A and ``out`` should be page-locked (``tensor.pin_memory()``) for the copies
+    to overlap; the library stages A into device memory in row chunks and
+    starts the sketch product of each chunk on arrival.  Returns (U, sigma, Vt,
+    info) once the current stream has been synchronised."""
+    if A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("a row-major host (CPU) matrix is required")
+    o = make_opts(precision, **kw)
+    m, n = A.shape
+    if out is None:
+        U = torch.empty(m, k, dtype=A.dtype).pin_memory()
+        sig = torch.empty(k, dtype=A.dtype).pin_memory()
+        Vt = torch.empty(k, n, dtype=A.dtype).pin_memory()
+    else:
+        U, sig, Vt = out
+        if U.is_cuda or sig.is_cuda or Vt.is_cuda:
+            raise ValueError("host (CPU) output tensors are required")
+    inf = _info(timing) if info else None
+    rc = lib().spm_rsvd_host(S.handle, _ptr(A), _dt(A), m, A.stride(0), r2, q, int(omega_seed), k,
+                             ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sig), _ptr(Vt),
+                             Vt.stride(0), ctypes.byref(inf) if inf is not None else None,
+                             _stream())
+    _check(rc, "spm_rsvd_host")
+    if inf is None:
+        torch.cuda.current_stream().synchronize()
     return U, sig, Vt, (inf.as_dict() if inf is not None else None)
 
 

@@ -244,19 +244,25 @@ def batched_main(a):
     roof = {"kernel": "whole batch (two passes over every A: A S and Q^T A)", "bound": "hbm",
             "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
             "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
-    # end to end: host copies of every A in, every U, sigma, V^T out, eager call
+    # end to end: host copies of every A into the captured call's input buffers,
+    # one replay of the captured batched call, every U, sigma, V^T copied out
     hostA = [p["A"].cpu().pin_memory() for p in probs]
     hostO = [tuple(t.cpu().pin_memory() for t in o) for o in batch.outputs]
-    e0.record()
-    for hA, p in zip(hostA, probs):
-        p["A"].copy_(hA, non_blocking=True)
-    batch.run()
-    for ho, o in zip(hostO, batch.outputs):
-        for h, d in zip(ho, o):
-            h.copy_(d, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e = {"value": e0.elapsed_time(e1), "unit": "ms", "h2d_bytes_per_step": int(a_bytes),
+    e2e_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0.record()
+        for hA, p in zip(hostA, probs):
+            p["A"].copy_(hA, non_blocking=True)
+        graph.replay()
+        for ho, o in zip(hostO, batch.outputs):
+            for h, d in zip(ho, o):
+                h.copy_(d, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    batch.check_status()
+    e2e = {"value": e2e_ms[-1], "unit": "ms", "h2d_bytes_per_step": int(a_bytes),
            "d2h_bytes_per_step": int(sum(sum(t.numel() * 4 for t in o) for o in batch.outputs))}
     cpu = None
     if not a.no_cpu:

@@ -45,6 +45,8 @@ struct TcParams {
   int64_t d_rs, d_cs, split_stride;
   int* status;
   int sym_upper;  // skip clusters whose tiles lie entirely below the diagonal
+  int fused3;     // split product A0 B0 + A0 B1 + A2 B0 (A1 = A0, B2 = B0): each k-tile
+                  // takes two ring stages, (A0, B0) and (A2, B1), and all three MMAs
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -200,7 +202,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (p.sym_upper && (int)(blockIdx.x / CL) * CL * TC_BM >= n0 + BN) return;
   const int kt0 = blockIdx.z * p.kt_per_split;
   const int kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
-  const int iters = (kt1 - kt0) * p.npass;
+  const int per_kt = p.fused3 ? 2 : p.npass;  // ring stages per k-tile
+  const int iters = (kt1 - kt0) * per_kt;
+  static_assert(STAGES % 2 == 0, "a fused k-tile's two stages must not wrap");
 
   uint32_t crank = 0;
   if (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
@@ -240,34 +244,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = false;
           break;
         }
-        const int kt = kt0 + it / p.npass;
-        const int q = it % p.npass;
+        const int kt = kt0 + it / per_kt;
+        const int q = it % per_kt;
+        // fused: the k-tile's first stage holds (A0, B0), its second (A2, B1)
+        const int qa = p.fused3 ? (q == 0 ? 0 : 2) : q;
+        const int qb = p.fused3 ? (q == 0 ? 0 : 1) : q;
         const int k0 = kt * TC_BK;
         const uint32_t fb = full0 + 8 * s;
         mbar_expect_tx(fb, Cfg::STAGE_BYTES);
         const uint32_t sa = smem_u32(tiles + s * Cfg::STAGE_BYTES);
         const uint32_t sb = sa + Cfg::A_BYTES;
         if (!A_MN) {
-          tma_load_2d(sa, ta[q], k0, m0, fb);
+          tma_load_2d(sa, ta[qa], k0, m0, fb);
         } else {
 #pragma unroll
-          for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[q], m0 + 64 * b, k0, fb);
+          for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[qa], m0 + 64 * b, k0, fb);
         }
         if (CL == 1) {
           if (!B_MN) {
-            tma_load_2d(sb, tb[q], k0, n0, fb);
+            tma_load_2d(sb, tb[qb], k0, n0, fb);
           } else {
 #pragma unroll
-            for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[q], n0 + 64 * b, k0, fb);
+            for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb);
           }
         } else {
           if (!B_MN) {
             constexpr int HB = BN / CL;  // rows of the B tile this CTA fetches
-            tma_load_2d_mc(sb + crank * HB * 128, tb[q], k0, n0 + (int)crank * HB, fb, cmask);
+            tma_load_2d_mc(sb + crank * HB * 128, tb[qb], k0, n0 + (int)crank * HB, fb, cmask);
           } else {
 #pragma unroll
             for (int b = 0; b < BN / 64; ++b)
-              if (b % CL == (int)crank) tma_load_2d_mc(sb + b * 8192, tb[q], n0 + 64 * b, k0, fb, cmask);
+              if (b % CL == (int)crank) tma_load_2d_mc(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb, cmask);
           }
         }
         issued = it + 1;
@@ -283,7 +290,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<BN, A_MN, B_MN>();
       bool ok = true;
-      for (int it = 0; it < iters; ++it) {
+      auto desc_a = [&](uint32_t sa, int kk) {
+        return A_MN ? smem_desc(sa + kk * 2048, 8192, 1024) : smem_desc(sa + kk * 32, 16, 1024);
+      };
+      auto desc_b = [&](uint32_t sb, int kk) {
+        return B_MN ? smem_desc(sb + kk * 2048, 8192, 1024) : smem_desc(sb + kk * 32, 16, 1024);
+      };
+      // fused split product: per k-tile wait for both stages, issue A0 B0, A0 B1,
+      // A2 B0 (the order of the unfused passes), release both stages
+      for (int j = 0; p.fused3 && j < iters / 2; ++j) {
+        const int s0 = (2 * j) % STAGES, s1 = (2 * j + 1) % STAGES;
+        if (!mbar_wait(full0 + 8 * s0, (uint32_t)((2 * j) / STAGES) & 1u, p.status) ||
+            !mbar_wait(full0 + 8 * s1, (uint32_t)((2 * j + 1) / STAGES) & 1u, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(tiles + s0 * Cfg::STAGE_BYTES), b_hi = a_hi + Cfg::A_BYTES;
+        const uint32_t a_lo = smem_u32(tiles + s1 * Cfg::STAGE_BYTES), b_lo = a_lo + Cfg::A_BYTES;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const uint32_t sa = (t == 2) ? a_lo : a_hi;
+          const uint32_t sb = (t == 1) ? b_lo : b_hi;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            tc_mma(tmem, desc_a(sa, kk), desc_b(sb, kk), idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
+        }
+        if (CL == 1) {
+          tc_commit(empty0 + 8 * s0);
+          tc_commit(empty0 + 8 * s1);
+        } else {
+          tc_commit_mc(empty0 + 8 * s0, cmask);
+          tc_commit_mc(empty0 + 8 * s1, cmask);
+        }
+      }
+      for (int it = 0; !p.fused3 && it < iters; ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!mbar_wait(full0 + 8 * s, ph, p.status)) {
@@ -476,6 +517,15 @@ static int launch_bn(bool amn, bool bmn, const CUtensorMap* ta, const CUtensorMa
   return launch_tc<BN, true, true, CL>(ta, tb, p, grid, st);
 }
 
+// The split pattern A0 B0 + A0 B1 + A2 B0 (A1 = A0, B2 = B0): four distinct
+// operand tiles per k-tile instead of six.
+static int fused_split(int npass, const TcOp* A, const TcOp* B) {
+  auto same = [](const TcOp& x, const TcOp& y) {
+    return x.p == y.p && x.ld == y.ld && x.mn_major == y.mn_major;
+  };
+  return (npass == 3 && same(A[0], A[1]) && same(B[0], B[2])) ? 1 : 0;
+}
+
 // strictly lower triangle of D (n x n) from the upper one
 __global__ void k_mirror_upper(int n, float* __restrict__ D, int64_t d_rs, int64_t d_cs) {
   for (int i = blockIdx.y; i < n; i += gridDim.y)
@@ -522,6 +572,7 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   p.alpha = alpha;
   p.status = nullptr;
   p.sym_upper = sym_upper ? 1 : 0;
+  p.fused3 = fused_split(npass, A, B);
   dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
   Arena ar(st);
   if (splitk == 1) {
@@ -623,6 +674,7 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   p.npass = npass;
   p.alpha = 1.0f;
   p.status = nullptr;
+  p.fused3 = fused_split(npass, A, B);
   if (splitk == 1) {
     p.D = D;
     p.d_rs = ldd;

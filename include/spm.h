@@ -203,6 +203,41 @@ int spm_rsvd_host(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, 
                   void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, spm_info* info,
                   void* stream);
 
+/* ---- sparse input: A = A_csr + U diag(sig) V^T --------------------------------
+ * A CSR matrix (row pointers, column indices ascending or not inside a row,
+ * values) with an optional low-rank term kept as factors, never formed densely
+ * (Section 2: the sketch pass costs O(nnz(A)); the workload's CSR matrix with a
+ * planted rank-200 term).  All arrays are device memory, values and factors of
+ * the call's dtype.  p = 0: no low-rank term (U, sig, V ignored). */
+typedef struct spm_csr {
+  const int64_t* rowptr; /* m + 1 */
+  const int32_t* colind; /* nnz, each in [0, n) */
+  const void* vals;      /* nnz */
+  int64_t m, n, nnz;
+  const void* U;         /* m x p, row-major, ld ldu */
+  int64_t ldu;
+  const void* sig;       /* p */
+  const void* V;         /* n x p, row-major, ld ldv */
+  int64_t ldv;
+  int64_t p;
+} spm_csr;
+
+/* A~ = A S (Algorithm 1 line 1) for a sparse A: out (m x r1, ld ldo, dtype).
+ * S.n == A->n.  A column index outside [0, n) is skipped (spm_rsvd_csr reports
+ * it as device status SPM_EINVAL). */
+int spm_sketch_apply_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, void* out, int64_t ldo,
+                         void* stream);
+
+/* RandSVD (as spm_rsvd) of a sparse A: the range finder on A~ = A S, then
+ * B = Q^T A = (A_csr^T Q)^T + (Q^T U) diag(sig) V^T through a column index of
+ * A built on the device.  SPM_PREC_FP64 takes FP64 values; MIXED and FP32 take
+ * FP32 values (else SPM_EUNSUPPORTED).  info->fro_a and resid_est are -1 (the
+ * norm of A is not formed).  Workspace: A~, the column index (nnz x (4 + size
+ * of a value) + 8 (n + 1) bytes) and the dense path's. */
+int spm_rsvd_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, int64_t r2, int32_t q,
+                 uint64_t omega_seed, int64_t k, const spm_opts* opts, void* U, int64_t ldu,
+                 void* sigma, void* Vt, int64_t ldvt, spm_info* info, void* stream);
+
 /* ---- a7: Algorithm 2, Sketch-Powered Low-Rank Factorization ------------------
  * Y (m x r2, ld ldy) and X (r2 x n, ld ldx) with A ~ Y X, X = (S2^T Y)^+ (S2^T A).
  * Y is returned orthonormal (the product Y X does not depend on the basis).

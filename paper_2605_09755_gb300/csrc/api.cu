@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -45,6 +46,13 @@ struct Call {
   int feed_n = 0;
   int64_t feed_rows = 0;
   const cudaEvent_t* feed_ev = nullptr;
+  // sparse input: A~ made beforehand (at_pre, dtype adt, ld at_pre_ld), and
+  // B = Q^T A made by make_b(rf, B, ldb) in B's precision (FP32 in MIXED);
+  // |A|_F is not formed (no_fro)
+  const void* at_pre = nullptr;
+  int64_t at_pre_ld = 0;
+  std::function<int(const struct RF&, void*, int64_t)> make_b;
+  bool no_fro = false;
   explicit Call(cudaStream_t s) : st(s), ar(s) { timer.stream = s; }
 };
 
@@ -352,7 +360,10 @@ static int range_finder_simt(Call& C, const spm_sketch* S, const void* A, int64_
   }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, dt, r1, C.acc, C.st));
+    if (C.at_pre)
+      SPM_TRY(convert2d(m, r1, rowmajor(C.at_pre, C.adt, C.at_pre_ld), mrowmajor(At, dt, r1), C.st));
+    else
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, dt, r1, C.acc, C.st));
   }
   {
     StageScope sc(C.timer, SPM_STAGE_POWER);
@@ -423,7 +434,13 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
   }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    if (C.feed_n > 0) {
+    if (C.at_pre) {
+      const View src = rowmajor(C.at_pre, C.adt, C.at_pre_ld);
+      if (Atlo)
+        SPM_TRY(split_bf16(m, r1, src, mrowmajor(At, DT_BF16, r1p), mrowmajor(Atlo, DT_BF16, r1p), C.st));
+      else
+        SPM_TRY(convert2d(m, r1, src, mrowmajor(At, DT_BF16, r1p), C.st));
+    } else if (C.feed_n > 0) {
       // host-fed A: each row chunk's sketch product as soon as the chunk is here
       const size_t es = dt_size(C.adt);
       for (int c = 0; c < C.feed_n; ++c) {
@@ -540,8 +557,8 @@ static int finish(Call& C, spm_info* info, int rc, bool has_b) {
   info->device_status = dst;
   info->eig_sweeps = stw[1];
   info->cholqr_passes = C.cholqr_passes;
-  info->fro_a = sqrt(acc[0]);
-  info->resid_est = has_b ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
+  info->fro_a = C.no_fro ? -1.0 : sqrt(acc[0]);
+  info->resid_est = (has_b && !C.no_fro) ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
   return dst == 0 ? SPM_OK : dst;
 }
 
@@ -569,8 +586,11 @@ static int rsvd_finish_simt(Call& C, const void* A, int64_t m, int64_t n, int64_
   SPM_ALLOC(C.ar, T, Uo, m * k);
   {
     StageScope sc(C.timer, SPM_STAGE_PROJECT);
-    SPM_TRY(gemm_simt(r2, n, m, 1.0, transpose(rowmajor(Q, dt, r2)),
-                      rowmajor(A, edt, lda), 0.0, mrowmajor(B, dt, n), C.st));
+    if (C.make_b)
+      SPM_TRY(C.make_b(rf, B, n));
+    else
+      SPM_TRY(gemm_simt(r2, n, m, 1.0, transpose(rowmajor(Q, dt, r2)),
+                        rowmajor(A, edt, lda), 0.0, mrowmajor(B, dt, n), C.st));
   }
   {
     StageScope sc(C.timer, SPM_STAGE_SMALL);
@@ -608,8 +628,12 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
   const int64_t np_ = pad8(n), r2p = pad8(r2);
   const int sdt = C.small64 ? DT_F64 : DT_F32;
   const size_t es = dt_size(sdt);
-  SPM_ALLOC(C.ar, __nv_bfloat16, Ahi, m * np_);
-  SPM_ALLOC(C.ar, __nv_bfloat16, Alo, m * np_);
+  __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
+  if (!C.make_b) {
+    Ahi = C.ar.alloc<__nv_bfloat16>(m * np_);
+    Alo = C.ar.alloc<__nv_bfloat16>(m * np_);
+    if (!Ahi || !Alo) return SPM_ENOMEM;
+  }
   SPM_ALLOC(C.ar, float, B, r2 * n);
   SPM_ALLOC(C.ar, __nv_bfloat16, Bhi, r2 * np_);
   SPM_ALLOC(C.ar, __nv_bfloat16, Blo, r2 * np_);
@@ -625,11 +649,15 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
   SPM_ALLOC(C.ar, float, Uo, m * k);
   {
     StageScope sc(C.timer, SPM_STAGE_PROJECT);
-    SPM_TRY(split_bf16(m, n, rowmajor(A, edt, lda), mrowmajor(Ahi, DT_BF16, np_),
-                       mrowmajor(Alo, DT_BF16, np_), C.st));
-    // B = Q^T A: A-op Q^T (M = r2, K = m) MN-major; B-op A (N = n, K = m) MN-major
-    SPM_TRY(tc_split(r2, n, m, rf.Qhi, rf.Qlo, r2p, true, Ahi, Alo, np_, true, C.final_passes, B,
-                     n, 1, C.st));
+    if (C.make_b) {
+      SPM_TRY(C.make_b(rf, B, n));
+    } else {
+      SPM_TRY(split_bf16(m, n, rowmajor(A, edt, lda), mrowmajor(Ahi, DT_BF16, np_),
+                         mrowmajor(Alo, DT_BF16, np_), C.st));
+      // B = Q^T A: A-op Q^T (M = r2, K = m) MN-major; B-op A (N = n, K = m) MN-major
+      SPM_TRY(tc_split(r2, n, m, rf.Qhi, rf.Qlo, r2p, true, Ahi, Alo, np_, true, C.final_passes,
+                       B, n, 1, C.st));
+    }
   }
   {
     StageScope sc(C.timer, SPM_STAGE_SMALL);
@@ -818,6 +846,51 @@ int spm_rsvd_host(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, 
     rc = SPM_ECUDA;
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
+  return finish(C, info, rc, true);
+}
+
+int spm_sketch_apply_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, void* out, int64_t ldo,
+                         void* stream) {
+  if (!S || !out || (dtype != SPM_F32 && dtype != SPM_F64)) return SPM_EINVAL;
+  SPM_TRY(csr_check(A, S->n));
+  if (ldo < S->r1) return SPM_EINVAL;
+  return csr_sketch_dev(S, A, dtype == SPM_F64 ? DT_F64 : DT_F32, out, ldo, nullptr,
+                        as_stream(stream));
+}
+
+int spm_rsvd_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, int64_t r2, int32_t q,
+                 uint64_t omega_seed, int64_t k, const spm_opts* opts, void* U, int64_t ldu,
+                 void* sigma, void* Vt, int64_t ldvt, spm_info* info, void* stream) {
+  if (!S || !A) return SPM_EINVAL;
+  SPM_TRY(csr_check(A, S->n));
+  // the dense checks on a stand-in pointer (A itself is never read as dense)
+  SPM_TRY(check_common(S, A, dtype, A->m, S->n, r2, q, opts));
+  if (!U || !sigma || !Vt || k < 1 || k > r2 || ldu < k || ldvt < S->n) return SPM_EINVAL;
+  const int64_t m = A->m, n = S->n, r1 = S->r1;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  const int qdt = C.prec == SPM_PREC_FP64 ? DT_F64 : DT_F32;
+  if (qdt != C.adt) return SPM_EUNSUPPORTED;  // FP64 mode wants FP64 values, the others FP32
+  SPM_TRY(prepare(C));
+  // A~ in the call's type (FP32 in MIXED: split into BF16 by the range finder)
+  void* At = C.ar.alloc<unsigned char>((size_t)m * r1 * dt_size(C.adt));
+  if (!At) return SPM_ENOMEM;
+  {
+    StageScope sc(C.timer, SPM_STAGE_APPLY);
+    SPM_TRY(csr_sketch_dev(S, A, C.adt, At, r1, C.status, C.st));
+  }
+  CscIndex csc{};
+  SPM_TRY(csc_build(A, C.adt, C.ar, csc, C.st));
+  C.at_pre = At;
+  C.at_pre_ld = r1;
+  C.no_fro = true;
+  C.make_b = [&](const RF& rf, void* B, int64_t ldb) {
+    const void* Q = qdt == DT_F64 ? (const void*)rf.Q64 : (const void*)rf.Q32;
+    return csr_project_dev(A, csc, qdt, Q, rf.r2, rf.r2, B, ldb, C.st);
+  };
+  RF rf;
+  int rc = range_finder_core(C, S, At, m, r1, r2, q, omega_seed, rf);
+  if (rc == SPM_OK) rc = rsvd_finish(C, nullptr, m, n, n, rf, k, U, ldu, sigma, Vt, ldvt);
   return finish(C, info, rc, true);
 }
 

@@ -45,6 +45,23 @@ int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint
 int gemm_simt(int64_t M, int64_t N, int64_t K, double alpha, View A, View B, double beta, MView C,
               cudaStream_t st, int batch = 1, int64_t sA = 0, int64_t sB = 0, int64_t sC = 0);
 
+// ---------------------------------------------------------------- sparse.cu
+// Column index of a CSR matrix (rows ascending inside each column).
+struct CscIndex {
+  int64_t* colptr;  // n + 1
+  int32_t* rowind;  // nnz
+  void* vals;       // nnz, the matrix's type
+};
+int csr_check(const spm_csr* A, int64_t n);
+// out (m x r1, ld ldo, type dt) = A S for A = A_csr + U diag(sig) V^T; an
+// out-of-range column index sets SPM_EINVAL in *status and is skipped
+int csr_sketch_dev(const spm_sketch* S, const spm_csr* A, int dt, void* out, int64_t ldo, int* status,
+                   cudaStream_t st);
+int csc_build(const spm_csr* A, int dt, Arena& ar, CscIndex& out, cudaStream_t st);
+// B (r2 x n, ld ldb) = Q^T A, Q (m x r2, ld ldq), all of type dt
+int csr_project_dev(const spm_csr* A, const CscIndex& csc, int dt, const void* Q, int64_t ldq,
+                    int64_t r2, void* B, int64_t ldb, cudaStream_t st);
+
 // ---------------------------------------------------------------- gemm_tc.cu
 // One BF16 operand of a tcgen05 product.  `p` points at a row-major array with
 // leading dimension `ld` (elements, multiple of 8).  For the A operand (M x K):

@@ -15,6 +15,7 @@ from . import _build
 F32, F64 = 0, 1
 SPARSE_SIGN, IDENTITY = 0, 1
 PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
+EINVAL = 1  # SPM_EINVAL
 STAGES = ("sketch", "apply", "power", "orth", "project", "small", "finish", "other")
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
@@ -69,6 +70,9 @@ _SIGS = {
     "spm_rsvd": ([VP, VP, I32, I64, I64, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64, VP,
                   VP, I64, ctypes.POINTER(Info), VP], I32),
     "spm_trim_memory": ([], I32),
+    "spm_sketch_apply_csr": ([VP, VP, I32, VP, I64, VP], I32),
+    "spm_rsvd_csr": ([VP, VP, I32, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64, VP, VP, I64,
+                      ctypes.POINTER(Info), VP], I32),
     "spm_rsvd_host": ([VP, VP, I32, I64, I64, I64, I32, U64, I64, ctypes.POINTER(Opts), VP, I64,
                        VP, VP, I64, ctypes.POINTER(Info), VP], I32),
     "spm_lowrank": ([VP, VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64, VP,
@@ -231,6 +235,58 @@ def rsvd(S, A, r2, q, k, omega_seed=43, precision=PREC_FP64, timing=False, out=N
                         ctypes.byref(inf) if inf is not None else None, _stream())
     _check(rc, "spm_rsvd")
     return U, sig, Vt, (inf.as_dict() if inf is not None else None)
+
+
+class CsrStruct(ctypes.Structure):
+    _fields_ = [("rowptr", VP), ("colind", VP), ("vals", VP), ("m", I64), ("n", I64), ("nnz", I64),
+                ("U", VP), ("ldu", I64), ("sig", VP), ("V", VP), ("ldv", I64), ("p", I64)]
+
+
+class CsrMatrix:
+    """A = A_csr + U diag(sig) V^T on the device (spm_csr); the tensors stay
+    referenced while the object lives.  rowptr int64 (m + 1), colind int32
+    (nnz), vals / U / sig / V float32 or float64 on one CUDA device."""
+
+    def __init__(self, rowptr, colind, vals, n, U=None, sig=None, V=None):
+        _require_cuda(rowptr, colind, vals)
+        if rowptr.dtype != torch.int64 or colind.dtype != torch.int32:
+            raise TypeError("rowptr int64, colind int32")
+        self.rowptr, self.colind, self.vals = rowptr, colind, vals
+        self.m, self.n, self.nnz = rowptr.numel() - 1, int(n), colind.numel()
+        self.U, self.sig, self.V = U, sig, V
+        self.dtype = vals.dtype
+        s = CsrStruct(_ptr(rowptr), _ptr(colind), _ptr(vals), self.m, self.n, self.nnz, None, 0,
+                      None, None, 0, 0)
+        if U is not None:
+            _require_cuda(U, sig, V)
+            s.U, s.ldu, s.sig, s.V, s.ldv, s.p = (_ptr(U), U.stride(0), _ptr(sig), _ptr(V),
+                                                   V.stride(0), U.shape[1])
+        self.struct = s
+
+
+def sketch_apply_csr(S, A, out=None):
+    """A~ = A S for a CsrMatrix A (m x r1, A's dtype)."""
+    if out is None:
+        out = torch.empty(A.m, S.r1, dtype=A.dtype, device=A.vals.device)
+    dt = F64 if A.dtype == torch.float64 else F32
+    _check(lib().spm_sketch_apply_csr(S.handle, ctypes.byref(A.struct), dt, _ptr(out), out.stride(0),
+                                      _stream()), "spm_sketch_apply_csr")
+    return out
+
+
+def rsvd_csr(S, A, r2, q, k, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    """RandSVD of a CsrMatrix A: (U, sigma, Vt, info)."""
+    o = make_opts(precision, **kw)
+    dev = A.vals.device
+    U = torch.empty(A.m, k, dtype=A.dtype, device=dev)
+    sig = torch.empty(k, dtype=A.dtype, device=dev)
+    Vt = torch.empty(k, A.n, dtype=A.dtype, device=dev)
+    inf = _info(timing)
+    dt = F64 if A.dtype == torch.float64 else F32
+    _check(lib().spm_rsvd_csr(S.handle, ctypes.byref(A.struct), dt, r2, q, int(omega_seed), k,
+                              ctypes.byref(o), _ptr(U), U.stride(0), _ptr(sig), _ptr(Vt),
+                              Vt.stride(0), ctypes.byref(inf), _stream()), "spm_rsvd_csr")
+    return U, sig, Vt, inf.as_dict()
 
 
 def trim_memory():

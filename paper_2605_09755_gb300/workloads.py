@@ -146,14 +146,22 @@ def gmm_kernel(npts, dim=16, comps=8, seed=1004):
     return 0.5 * (K + K.T), h, X
 
 
-def sparse_planted(m, n, nnz_row, p, seed=1003, amp=100.0):
-    """CSR (indptr, indices, values) + planted factors U (m x p), sig (p), V (n x p)."""
+def sparse_planted(m, n, nnz_row, p, seed=1003, amp=100.0, factors=True):
+    """CSR (indptr, indices, values) + planted factors U (m x p), sig (p), V (n x p).
+
+    Each row holds `nnz_row` distinct uniform columns (ascending) with N(0, 1)
+    values; the planted term is U diag(amp i^-1/2) V^T with Haar U, V (None for
+    the factors when factors=False)."""
     rng = _rng(seed)
-    indices = np.empty(m * nnz_row, dtype=np.int64)
-    for i in range(m):
-        indices[i * nnz_row:(i + 1) * nnz_row] = np.sort(rng.choice(n, nnz_row, replace=False))
+    cols = np.sort(rng.integers(0, n, size=(m, nnz_row)), axis=1)
+    dup = np.nonzero((cols[:, 1:] == cols[:, :-1]).any(axis=1))[0]
+    for i in dup:  # rare: redraw the row without replacement
+        cols[i] = np.sort(rng.choice(n, nnz_row, replace=False))
+    indices = cols.reshape(-1)
     indptr = np.arange(0, m * nnz_row + 1, nnz_row, dtype=np.int64)
     values = rng.standard_normal(m * nnz_row)
+    if not factors:
+        return indptr, indices, values, None, None, None
     U = haar(m, p, rng)
     V = haar(n, p, rng)
     sig = amp * np.arange(1, p + 1, dtype=np.float64) ** -0.5

@@ -51,9 +51,10 @@ def parse():
     p.add_argument("--final-passes", type=int, default=3)
     p.add_argument("--power-passes", type=int, default=3)
     p.add_argument("--cpu-rows", type=int, default=2048)
-    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched"],
+    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr"],
                    help="rsvd: the 65536 x 16384 RandSVD (default); batched: 512 uneven "
-                        "problems in one graph-captured spm_rsvd_batched call")
+                        "problems in one graph-captured spm_rsvd_batched call; csr: the "
+                        "10^6 x 2*10^5 sparse matrix with a planted rank-200 term")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--nstreams", type=int, default=16)
     p.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"])
@@ -302,6 +303,88 @@ def batched_main(a):
     print(json.dumps(line), flush=True)
 
 
+def csr_main(a):
+    """The sparse workload: A = A_csr + U diag(100 i^-1/2) V^T, 10^6 x 2*10^5 with 20
+    N(0, 1) non-zeros per row, planted rank 200 kept as factors; r1 = 400, k = 200,
+    s = 8, q = 2, mixed precision through spm_rsvd_csr.  One step = one call."""
+    import numpy as np
+    import torch
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import workloads as wl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    lib = spm.lib()
+    m, n, nnz_row, p, r1, k = 1_000_000, 200_000, 20, 200, 400, 200
+    indptr, indices, values, U, sig, V = wl.sparse_planted(m, n, nnz_row, p, seed=1003)
+    f32 = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    A = spm.CsrMatrix(torch.tensor(indptr, device="cuda"),
+                      torch.tensor(indices, dtype=torch.int32, device="cuda"), f32(values), n,
+                      U=f32(U), sig=f32(sig), V=f32(V))
+    del indices, values, U, V
+    S = spm.Sketch(n, r1, a.s, 42)
+    step = lambda timing=False: spm.rsvd_csr(S, A, k, a.q, k, precision=spm.PREC_MIXED,
+                                            timing=timing)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    c0 = lib.spm_launch_count()
+    _, _, _, inf = step(timing=True)
+    torch.cuda.synchronize()
+    launches = int(lib.spm_launch_count() - c0)
+    # the CSR sketch pass alone, for its roofline: rowptr, colind, values and U read,
+    # A~ written (the sketch tables sit in L2)
+    At = torch.empty(m, r1, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        spm.sketch_apply_csr(S, A, out=At)
+    e0.record()
+    for _ in range(a.steps):
+        spm.sketch_apply_csr(S, A, out=At)
+    e1.record()
+    torch.cuda.synchronize()
+    sk_ms = e0.elapsed_time(e1) / a.steps
+    sk_bytes = (m + 1) * 8 + m * nnz_row * 8 + m * p * 4 + m * r1 * 4
+    del At
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach = sk_bytes / (sk_ms * 1e-3) / 1e9
+    line = {
+        "metric": "time to rank-k approx of a sparse CSR matrix with a planted low-rank term",
+        "value": ms, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"CSR {m}x{n}, {nnz_row} N(0,1) non-zeros per row, planted "
+                               f"U diag(100 i^-1/2) V^T of rank {p} as factors, r1 = {r1}, "
+                               f"k = {k}, s = {a.s}, q = {a.q}, RandSVD",
+                   "precision": "mixed", "l2": "A~ (1.6 GB) larger than L2; no flush"},
+        "stage_ms": inf["stage_ms"],
+        "roofline": {"kernel": "k_csr_sketch (A S, CSR part) + the factor term", "bound": "hbm",
+                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
+        "e2e": None,
+        "cpu_baseline": {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "not run: the oracle's RandSVD needs the dense 10^6 x 2*10^5 "
+                                   "matrix (1.6 TB in FP64)"},
+        "gpu_launches": launches * a.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -309,6 +392,9 @@ def main():
         return
     if a.workload == "batched":
         batched_main(a)
+        return
+    if a.workload == "csr":
+        csr_main(a)
         return
     import numpy as np
     import torch

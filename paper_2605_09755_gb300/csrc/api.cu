@@ -122,7 +122,7 @@ static int sm_count() {
 // splits); the partials' traffic for the short-K ones.  sym: only the tiles a
 // symmetric product computes (clusters of two M tiles that reach the upper
 // triangle) count.
-static int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false) {
+int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym) {
   const int BN = (N >= 192) ? 256 : 128;
   int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
   if (sym) {
@@ -877,7 +877,7 @@ int spm_rsvd_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, int64_t r
   if (!At) return SPM_ENOMEM;
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    SPM_TRY(csr_sketch_dev(S, A, C.adt, At, r1, C.status, C.st));
+    SPM_TRY(csr_sketch_dev(S, A, C.adt, At, r1, C.status, C.st, C.prec == SPM_PREC_MIXED));
   }
   CscIndex csc{};
   SPM_TRY(csc_build(A, C.adt, C.ar, csc, C.st));
@@ -886,6 +886,9 @@ int spm_rsvd_csr(const spm_sketch* S, const spm_csr* A, int32_t dtype, int64_t r
   C.no_fro = true;
   C.make_b = [&](const RF& rf, void* B, int64_t ldb) {
     const void* Q = qdt == DT_F64 ? (const void*)rf.Q64 : (const void*)rf.Q32;
+    if (C.prec == SPM_PREC_MIXED)
+      return csr_project_dev(A, csc, qdt, Q, rf.r2, rf.r2, B, ldb, C.st, rf.Qhi, rf.Qlo,
+                             round_up(rf.r2, 8));
     return csr_project_dev(A, csc, qdt, Q, rf.r2, rf.r2, B, ldb, C.st);
   };
   RF rf;

@@ -1229,6 +1229,48 @@ __global__ void k_sign_flags(int64_t m, int64_t k, const T* __restrict__ U, int6
   }
 }
 
+// The same argmax in two passes for a row-major U (cs == 1): a CTA scans a
+// block of rows with its threads on columns (coalesced rows) and keeps, per
+// column, the largest |U| and its first row; then each column's block results
+// are combined in block order.  Ties go to the smallest row, as above.
+template <typename T>
+__global__ void k_sign_part(int64_t m, int64_t k, const T* __restrict__ U, int64_t rs, int64_t rows_per,
+                            T* __restrict__ pv, int64_t* __restrict__ pi) {
+  const int64_t r0 = blockIdx.x * rows_per, r1 = min64(m, r0 + rows_per);
+  for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
+    T best = (T)-1;
+    int64_t idx = r0;
+    for (int64_t i = r0; i < r1; ++i) {
+      const T v = fabs(U[i * rs + j]);
+      if (v > best) {
+        best = v;
+        idx = i;
+      }
+    }
+    pv[blockIdx.x * k + j] = best;
+    pi[blockIdx.x * k + j] = idx;
+  }
+}
+
+template <typename T>
+__global__ void k_sign_combine(int nblk, int64_t k, const T* __restrict__ U, int64_t rs,
+                               const T* __restrict__ pv, const int64_t* __restrict__ pi,
+                               int* __restrict__ flip) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    T best = (T)-1;
+    int64_t idx = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const T v = pv[b * k + j];
+      if (v > best) {
+        best = v;
+        idx = pi[b * k + j];
+      }
+    }
+    flip[j] = (U[idx * rs + j] < (T)0) ? 1 : 0;
+  }
+}
+
 template <typename T>
 __global__ void k_apply_flags(int64_t rows, int64_t cols, T* __restrict__ X, int64_t rs, int64_t cs,
                               bool by_col, const int* __restrict__ flip) {
@@ -1240,16 +1282,36 @@ __global__ void k_apply_flags(int64_t rows, int64_t cols, T* __restrict__ X, int
   }
 }
 
+template <typename T>
+static void sign_flags_rows(int64_t m, int64_t k, const T* U, int64_t rs, int* flip, Arena& ar,
+                            cudaStream_t st, bool& done) {
+  done = false;
+  const int64_t nblk = min64(cdiv(m, 64), 152 * 4);
+  const int64_t rows_per = cdiv(m, nblk);
+  T* pv = ar.alloc<T>(nblk * k);
+  int64_t* pi = ar.alloc<int64_t>(nblk * k);
+  if (!pv || !pi) return;
+  k_sign_part<T><<<(unsigned)cdiv(m, rows_per), 256, 0, st>>>(m, k, U, rs, rows_per, pv, pi);
+  k_sign_combine<T><<<(unsigned)min64(cdiv(k, 256), 152), 256, 0, st>>>((int)cdiv(m, rows_per), k, U,
+                                                                         rs, pv, pi, flip);
+  done = true;
+}
+
 int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st) {
   Arena ar(st);
   SPM_ALLOC(ar, int, flip, k);
   const int g = (int)min64(k, 152 * 8);
+  bool rows_done = false;
+  if (U.cs == 1 && U.dt == DT_F32)
+    sign_flags_rows<float>(m, k, (const float*)U.p, U.rs, flip, ar, st, rows_done);
+  else if (U.cs == 1 && U.dt == DT_F64)
+    sign_flags_rows<double>(m, k, (const double*)U.p, U.rs, flip, ar, st, rows_done);
   if (U.dt == DT_F32) {
-    k_sign_flags<float><<<g, 256, 0, st>>>(m, k, (const float*)U.p, U.rs, U.cs, flip);
+    if (!rows_done) k_sign_flags<float><<<g, 256, 0, st>>>(m, k, (const float*)U.p, U.rs, U.cs, flip);
     k_apply_flags<float><<<grid_for(m * k), 256, 0, st>>>(m, k, (float*)U.p, U.rs, U.cs, true, flip);
     k_apply_flags<float><<<grid_for(k * n), 256, 0, st>>>(k, n, (float*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else if (U.dt == DT_F64) {
-    k_sign_flags<double><<<g, 256, 0, st>>>(m, k, (const double*)U.p, U.rs, U.cs, flip);
+    if (!rows_done) k_sign_flags<double><<<g, 256, 0, st>>>(m, k, (const double*)U.p, U.rs, U.cs, flip);
     k_apply_flags<double><<<grid_for(m * k), 256, 0, st>>>(m, k, (double*)U.p, U.rs, U.cs, true, flip);
     k_apply_flags<double><<<grid_for(k * n), 256, 0, st>>>(k, n, (double*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else {

@@ -56,11 +56,15 @@ int csr_check(const spm_csr* A, int64_t n);
 // out (m x r1, ld ldo, type dt) = A S for A = A_csr + U diag(sig) V^T; an
 // out-of-range column index sets SPM_EINVAL in *status and is skipped
 int csr_sketch_dev(const spm_sketch* S, const spm_csr* A, int dt, void* out, int64_t ldo, int* status,
-                   cudaStream_t st);
+                   cudaStream_t st, bool tc = false);
 int csc_build(const spm_csr* A, int dt, Arena& ar, CscIndex& out, cudaStream_t st);
 // B (r2 x n, ld ldb) = Q^T A, Q (m x r2, ld ldq), all of type dt
+// tc (FP32 only): the low-rank terms as split-BF16 tensor-core products, with
+// Q's split (Qhi, Qlo, ld ldqh) for Q^T U
 int csr_project_dev(const spm_csr* A, const CscIndex& csc, int dt, const void* Q, int64_t ldq,
-                    int64_t r2, void* B, int64_t ldb, cudaStream_t st);
+                    int64_t r2, void* B, int64_t ldb, cudaStream_t st,
+                    const __nv_bfloat16* Qhi = nullptr, const __nv_bfloat16* Qlo = nullptr,
+                    int64_t ldqh = 0);
 
 // ---------------------------------------------------------------- gemm_tc.cu
 // One BF16 operand of a tcgen05 product.  `p` points at a row-major array with
@@ -82,6 +86,8 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
             float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st,
             bool sym_upper = false);
 bool tc_available();
+// split-K factor of a tensor-core product (a wave and traffic cost model; api.cu)
+int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false);
 
 // ---------------------------------------------------------------- dense.cu
 // y = convert(x) elementwise on a strided 2-D view (rows x cols).

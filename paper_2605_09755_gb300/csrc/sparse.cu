@@ -20,7 +20,7 @@ __global__ void k_csr_sketch(int64_t m, int64_t n, int64_t nnz, int r1, int s,
                              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                              const T* __restrict__ vals, const int32_t* __restrict__ scols,
                              const int8_t* __restrict__ ssigns, TACC scale, TACC* __restrict__ out,
-                             int64_t ldo, int* __restrict__ status) {
+                             int64_t ldo, int* __restrict__ status, bool add) {
   extern __shared__ __align__(16) unsigned char csr_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   TACC* acc = reinterpret_cast<TACC*>(csr_smem) + (size_t)wib * r1;
@@ -44,7 +44,8 @@ __global__ void k_csr_sketch(int64_t m, int64_t n, int64_t nnz, int r1, int s,
       }
       __syncwarp();
     }
-    for (int c = lane; c < r1; c += 32) out[i * ldo + c] = acc[c] * scale;
+    for (int c = lane; c < r1; c += 32)
+      out[i * ldo + c] = add ? out[i * ldo + c] + acc[c] * scale : acc[c] * scale;
     __syncwarp();
   }
   if (bad && lane == 0) set_status(status, SPM_EINVAL);
@@ -176,6 +177,28 @@ static int blocks_for(int64_t work, int per_block) {
   return (int)max64(1, min64(cdiv(work, per_block), 152 * 32));
 }
 
+// D (M x N, FP32, ld ldd) = X Y^T from the BF16 splits of X (M x K) and Y
+// (N x K), both row-major FP32 with ld ldx / ldy; x_mn / y_mn: the operand is
+// stored transposed (K x M, K x N) instead.  Three passes (hi hi + hi lo + lo hi).
+static int tc_split_f32(int64_t M, int64_t N, int64_t K, const float* X, int64_t ldx, bool x_mn,
+                        const float* Y, int64_t ldy, bool y_mn, float* D, int64_t ldd, Arena& ar,
+                        cudaStream_t st) {
+  const int64_t xr = x_mn ? K : M, xc = x_mn ? M : K, yr = y_mn ? K : N, yc = y_mn ? N : K;
+  const int64_t xp = round_up(xc, 8), yp = round_up(yc, 8);
+  __nv_bfloat16* xh = ar.alloc<__nv_bfloat16>(xr * xp);
+  __nv_bfloat16* xl = ar.alloc<__nv_bfloat16>(xr * xp);
+  __nv_bfloat16* yh = ar.alloc<__nv_bfloat16>(yr * yp);
+  __nv_bfloat16* yl = ar.alloc<__nv_bfloat16>(yr * yp);
+  if (!xh || !xl || !yh || !yl) return SPM_ENOMEM;
+  SPM_TRY(split_bf16(xr, xc, rowmajor(X, DT_F32, ldx), mrowmajor(xh, DT_BF16, xp),
+                     mrowmajor(xl, DT_BF16, xp), st));
+  SPM_TRY(split_bf16(yr, yc, rowmajor(Y, DT_F32, ldy), mrowmajor(yh, DT_BF16, yp),
+                     mrowmajor(yl, DT_BF16, yp), st));
+  TcOp a[3] = {{xh, xp, x_mn}, {xh, xp, x_mn}, {xl, xp, x_mn}};
+  TcOp b[3] = {{yh, yp, y_mn}, {yl, yp, y_mn}, {yh, yp, y_mn}};
+  return gemm_tc(M, N, K, 3, a, b, 1.0f, D, ldd, 1, auto_splitk(M, N, K), st);
+}
+
 // out[e] = sum_c parts[c * len + e], c ascending
 template <typename T>
 __global__ void k_sum_parts(int count, int64_t len, const T* __restrict__ parts, T* __restrict__ out) {
@@ -226,7 +249,7 @@ int csr_check(const spm_csr* A, int64_t n) {
 }
 
 int csr_sketch_dev(const spm_sketch* S, const spm_csr* A, int dt, void* out, int64_t ldo, int* status,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool tc) {
   if (S->kind != SPM_SKETCH_SPARSE_SIGN && S->kind != SPM_SKETCH_IDENTITY) return SPM_EINVAL;
   const int64_t m = A->m, n = A->n, r1 = S->r1;
   const int s = S->s;
@@ -236,21 +259,34 @@ int csr_sketch_dev(const spm_sketch* S, const spm_csr* A, int dt, void* out, int
   if (smem > 200 * 1024) return SPM_EUNSUPPORTED;
   const int grid = blocks_for(m, wpb);
   const double scale = (S->kind == SPM_SKETCH_IDENTITY) ? 1.0 : 1.0 / sqrt((double)s);
+  const bool tc_factor = tc && dt == DT_F32 && A->p > 0 && tc_available();
+  if (tc_factor) {
+    // out = U (diag(sig) (S^T V)^T) on tensor cores first; the sparse part is added below
+    Arena ar(st);
+    float* SV = ar.alloc<float>(r1 * A->p);
+    if (!SV) return SPM_ENOMEM;
+    SPM_TRY(sketch_apply_t_dev(S, A->V, dt, A->p, A->ldv, SV, dt, A->p, st));
+    k_scale_cols<float><<<blocks_for(r1 * A->p, 256), 256, 0, st>>>(r1, A->p, SV, A->p,
+                                                                     (const float*)A->sig);
+    SPM_LAUNCH_CHECK();
+    SPM_TRY(tc_split_f32(m, r1, A->p, (const float*)A->U, A->ldu, false, SV, A->p, false,
+                         (float*)out, ldo, ar, st));
+  }
   if (dt == DT_F64) {
     auto kern = k_csr_sketch<double, double>;
     SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, threads, smem, st>>>(m, n, A->nnz, (int)r1, s, A->rowptr, A->colind,
                                       (const double*)A->vals, S->cols, S->signs, scale, (double*)out,
-                                      ldo, status);
+                                      ldo, status, false);
   } else {
     auto kern = k_csr_sketch<float, float>;
     SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, threads, smem, st>>>(m, n, A->nnz, (int)r1, s, A->rowptr, A->colind,
                                       (const float*)A->vals, S->cols, S->signs, (float)scale,
-                                      (float*)out, ldo, status);
+                                      (float*)out, ldo, status, tc_factor);
   }
   SPM_LAUNCH_CHECK();
-  if (A->p > 0) {
+  if (A->p > 0 && !tc_factor) {
     // A~ += U diag(sig) (S^T V)^T
     Arena ar(st);
     void* SV = ar.alloc<unsigned char>((size_t)r1 * A->p * es);
@@ -306,7 +342,8 @@ int csc_build(const spm_csr* A, int dt, Arena& ar, CscIndex& out, cudaStream_t s
 }
 
 int csr_project_dev(const spm_csr* A, const CscIndex& csc, int dt, const void* Q, int64_t ldq,
-                    int64_t r2, void* B, int64_t ldb, cudaStream_t st) {
+                    int64_t r2, void* B, int64_t ldb, cudaStream_t st, const __nv_bfloat16* Qhi,
+                    const __nv_bfloat16* Qlo, int64_t ldqh) {
   const int64_t m = A->m, n = A->n;
   const size_t es = dt == DT_F64 ? 8 : 4;
   Arena ar(st);
@@ -323,7 +360,26 @@ int csr_project_dev(const spm_csr* A, const CscIndex& csc, int dt, const void* Q
                                               r2);
   SPM_LAUNCH_CHECK();
   SPM_TRY(convert2d(r2, n, transpose(rowmajor(Bt, dt, r2)), mrowmajor(B, dt, ldb), st));
-  if (A->p > 0) {
+  if (A->p > 0 && dt == DT_F32 && Qhi && Qlo && tc_available()) {
+    // B += (Q^T U) diag(sig) V^T on tensor cores: Q^T U from Q's split and U's,
+    // then (Q^T U diag(sig)) V^T into a scratch added to B
+    const int64_t p = A->p, pp = round_up(p, 8);
+    float* QU = ar.alloc<float>(r2 * p);
+    float* Bf = ar.alloc<float>(r2 * n);
+    __nv_bfloat16* uh = ar.alloc<__nv_bfloat16>(m * pp);
+    __nv_bfloat16* ul = ar.alloc<__nv_bfloat16>(m * pp);
+    if (!QU || !Bf || !uh || !ul) return SPM_ENOMEM;
+    SPM_TRY(split_bf16(m, p, rowmajor(A->U, DT_F32, A->ldu), mrowmajor(uh, DT_BF16, pp),
+                       mrowmajor(ul, DT_BF16, pp), st));
+    // A-op Q^T (M = r2, K = m) and B-op U (N = p, K = m), both MN-major
+    TcOp a[3] = {{Qhi, ldqh, true}, {Qhi, ldqh, true}, {Qlo, ldqh, true}};
+    TcOp b[3] = {{uh, pp, true}, {ul, pp, true}, {uh, pp, true}};
+    SPM_TRY(gemm_tc(r2, p, m, 3, a, b, 1.0f, QU, p, 1, auto_splitk(r2, p, m), st));
+    k_scale_cols<float><<<blocks_for(r2 * p, 256), 256, 0, st>>>(r2, p, QU, p, (const float*)A->sig);
+    SPM_LAUNCH_CHECK();
+    SPM_TRY(tc_split_f32(r2, n, p, QU, p, false, (const float*)A->V, A->ldv, false, Bf, n, ar, st));
+    SPM_TRY(add2d_f32(r2, n, (float*)B, ldb, Bf, n, st));
+  } else if (A->p > 0) {
     // B += (Q^T U) diag(sig) V^T
     void* QU = ar.alloc<unsigned char>((size_t)r2 * A->p * es);
     if (!QU) return SPM_ENOMEM;

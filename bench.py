@@ -51,10 +51,11 @@ def parse():
     p.add_argument("--final-passes", type=int, default=3)
     p.add_argument("--power-passes", type=int, default=3)
     p.add_argument("--cpu-rows", type=int, default=2048)
-    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr"],
+    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr", "nystrom"],
                    help="rsvd: the 65536 x 16384 RandSVD (default); batched: 512 uneven "
                         "problems in one graph-captured spm_rsvd_batched call; csr: the "
-                        "10^6 x 2*10^5 sparse matrix with a planted rank-200 term")
+                        "10^6 x 2*10^5 sparse matrix with a planted rank-200 term; nystrom: the "
+                        "40000-point Gaussian kernel")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--nstreams", type=int, default=16)
     p.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"])
@@ -386,6 +387,115 @@ def csr_main(a):
     print(json.dumps(line), flush=True)
 
 
+def nystrom_main(a):
+    """Nystrom (Algorithm 3) of the Gaussian kernel over 40000 points of an 8-component
+    mixture in R^16 (means N(0, 3^2 I), unit covariance), h = the lower median of the
+    pairwise distances, K materialised in FP32; r1 = 1000, k = 500, s = 8, q = 1,
+    mixed precision.  One step = one spm_nystrom call."""
+    import numpy as np
+    import torch
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import workloads as wl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    lib = spm.lib()
+    n, r1, k, q = 40000, 1000, 500, 1
+    X = wl.gmm_points(n, 16, 8, seed=1004)
+    Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+    sq = (Xd * Xd).sum(1)
+    D2 = (sq[:, None] + sq[None, :] - 2.0 * (Xd @ Xd.T)).clamp_min_(0.0)
+    # lower median over the pairs i < j: every pair appears twice off the diagonal
+    npairs = n * (n - 1) // 2
+    D2.fill_diagonal_(float("inf"))
+    kth = 2 * ((npairs - 1) // 2) + 1
+    h2 = float(torch.kthvalue(D2.reshape(-1), kth).values)
+    D2.fill_diagonal_(0.0)
+    K64 = torch.exp(D2 / (-2.0 * h2))
+    del D2
+    K64 = 0.5 * (K64 + K64.T)
+    K = K64.float()
+    S = spm.Sketch(n, r1, a.s, 42)
+    step = lambda timing=False: spm.nystrom(S, K, k, q, precision=spm.PREC_MIXED, timing=timing)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    c0 = lib.spm_launch_count()
+    Cm, W, inf = step(timing=True)
+    torch.cuda.synchronize()
+    launches = int(lib.spm_launch_count() - c0)
+    clocks = ClockSampler()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+
+    def rel_err(Cm, W, Kref):
+        Wp = torch.linalg.pinv(W.double(), hermitian=True)
+        C = Cm.double()
+        err2, ref2 = 0.0, 0.0
+        for i0 in range(0, n, 4096):       # ||K - C W^+ C^T||_F in row blocks
+            blk = Kref[i0:i0 + 4096] - (C[i0:i0 + 4096] @ Wp) @ C.T
+            err2 += float((blk * blk).sum())
+            ref2 += float((Kref[i0:i0 + 4096] ** 2).sum())
+        return (err2 / ref2) ** 0.5
+
+    e_mixed = rel_err(Cm, W, K64)
+    C64, W64, _ = spm.nystrom(S, K64, k, q, precision=spm.PREC_FP64)
+    e_fp64 = rel_err(C64, W64, K64)
+    del C64, W64, K64
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    apply_ms = inf["stage_ms"]["apply"]
+    ap_bytes = n * n * 4 + n * r1 * 4
+    ach = ap_bytes / (apply_ms * 1e-3) / 1e9 if apply_ms else None
+    cpu = None
+    if not a.no_cpu:
+        from oracle import algorithms as alg
+        from oracle import sketch as osk
+        ns = 4000
+        Xs = X[:ns]
+        sqs = np.sum(Xs * Xs, axis=1)
+        Ks = np.exp(-np.maximum(sqs[:, None] + sqs[None, :] - 2.0 * (Xs @ Xs.T), 0.0) / (2.0 * h2))
+        Ks = 0.5 * (Ks + Ks.T)
+        t0 = time.perf_counter()
+        alg.nystrom(Ks, osk.Sketch(ns, r1, a.s, 42), osk.gaussian(r1, k, 43), q)
+        t = (time.perf_counter() - t0) * 1e3
+        scale = (n / ns) ** 2
+        cpu = {"value": t * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle Nystrom on the kernel of the first {ns} of the {n} points "
+                         f"(same r1, k, q, h), time scaled by (n / {ns})^2 = {scale:.0f}x"}
+    line = {
+        "metric": "time to a rank-k Nystrom approximation of a PSD kernel matrix", "value": ms,
+        "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"Nystrom of the Gaussian kernel over {n} points of an 8-component "
+                               f"mixture in R^16, h = lower median distance, K FP32 "
+                               f"({n * n * 4 / 1e9:.1f} GB), r1 = {r1}, k = {k}, s = {a.s}, q = {q}",
+                   "precision": "mixed", "l2": "K larger than L2; no flush"},
+        "stage_ms": inf["stage_ms"],
+        "accuracy": {"rel_fro_err_mixed": e_mixed, "rel_fro_err_fp64": e_fp64,
+                     "ratio": e_mixed / e_fp64 if e_fp64 > 0 else None, "h": h2 ** 0.5},
+        "roofline": {"kernel": "sketch apply of K (the apply stage)", "bound": "hbm",
+                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ach / hbm_peak if ach else None, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
+        "e2e": None, "cpu_baseline": cpu, "gpu_launches": launches * a.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -396,6 +506,9 @@ def main():
         return
     if a.workload == "csr":
         csr_main(a)
+        return
+    if a.workload == "nystrom":
+        nystrom_main(a)
         return
     import numpy as np
     import torch

@@ -1252,22 +1252,34 @@ __global__ void k_sign_part(int64_t m, int64_t k, const T* __restrict__ U, int64
   }
 }
 
+// a warp per column: lane l takes blocks l, l + 32, ... in order, then the warp
+// keeps the largest value and, among equal ones, the smallest row (the result
+// of a scan over the blocks in order)
 template <typename T>
 __global__ void k_sign_combine(int nblk, int64_t k, const T* __restrict__ U, int64_t rs,
                                const T* __restrict__ pv, const int64_t* __restrict__ pi,
                                int* __restrict__ flip) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
-       j += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < k; j += nw) {
     T best = (T)-1;
     int64_t idx = 0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
       const T v = pv[b * k + j];
       if (v > best) {
         best = v;
         idx = pi[b * k + j];
       }
     }
-    flip[j] = (U[idx * rs + j] < (T)0) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T v2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+      const int64_t i2 = __shfl_xor_sync(0xFFFFFFFFu, idx, o);
+      if (v2 > best || (v2 == best && i2 < idx)) {
+        best = v2;
+        idx = i2;
+      }
+    }
+    if (lane == 0) flip[j] = (U[idx * rs + j] < (T)0) ? 1 : 0;
   }
 }
 
@@ -1292,8 +1304,8 @@ static void sign_flags_rows(int64_t m, int64_t k, const T* U, int64_t rs, int* f
   int64_t* pi = ar.alloc<int64_t>(nblk * k);
   if (!pv || !pi) return;
   k_sign_part<T><<<(unsigned)cdiv(m, rows_per), 256, 0, st>>>(m, k, U, rs, rows_per, pv, pi);
-  k_sign_combine<T><<<(unsigned)min64(cdiv(k, 256), 152), 256, 0, st>>>((int)cdiv(m, rows_per), k, U,
-                                                                         rs, pv, pi, flip);
+  k_sign_combine<T><<<(unsigned)min64(cdiv(k, 8), 152 * 8), 256, 0, st>>>((int)cdiv(m, rows_per), k, U,
+                                                                          rs, pv, pi, flip);
   done = true;
 }
 

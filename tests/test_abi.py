@@ -50,6 +50,23 @@ def test_host_only_calls(libspm):
     assert f(None, 100, 10, 1, 1, 0, None) == 1
 
 
+def test_host_only_argument_checks_of_the_newer_entries(libspm):
+    """Host-buffer, sparse and pool entries reject bad arguments before any device work."""
+    vp = ctypes.c_void_p
+    i64, i32, u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    f = libspm.spm_rsvd_host
+    f.argtypes = [vp, vp, i32, i64, i64, i64, i32, u64, i64, vp, vp, i64, vp, vp, i64, vp, vp]
+    assert f(None, None, 0, 10, 10, 5, 1, 1, 5, None, None, 5, None, None, 10, None, None) == 1
+    f = libspm.spm_rsvd_csr
+    f.argtypes = [vp, vp, i32, i64, i32, u64, i64, vp, vp, i64, vp, vp, i64, vp, vp]
+    assert f(None, None, 0, 5, 1, 1, 5, None, None, 5, None, None, 10, None, None) == 1
+    f = libspm.spm_sketch_apply_csr
+    f.argtypes = [vp, vp, i32, vp, i64, vp]
+    assert f(None, None, 0, None, 10, None) == 1
+    libspm.spm_trim_memory.restype = ctypes.c_int
+    assert libspm.spm_trim_memory() in (0, 3)   # SPM_ECUDA where no device is usable
+
+
 def test_binding_has_no_cpu_path():
     src = open(os.path.join(ROOT, "paper_2605_09755_gb300", "spm.py")).read()
     assert "oracle" not in src

@@ -109,6 +109,105 @@ def test_identity_sketch():
     assert np.array_equal(S.dense(), np.eye(12))
 
 
+# ---------------------------------------------------------------- dense sketches (Lemma 3.2 items 1, 3)
+@pytest.mark.parametrize("n", [1, 2, 16, 256])
+def test_hadamard_entries_match_library(n):
+    import scipy.linalg
+    j = np.arange(n)
+    assert np.array_equal(sk.hadamard_entries(j, j), scipy.linalg.hadamard(n))
+
+
+@pytest.mark.parametrize("n,r1", [(64, 10), (64, 64), (1024, 100), (1024, 1024), (1, 1)])
+def test_srht_columns_orthogonal_when_n_is_a_power_of_two(n, r1):
+    """S = D H I_{:,T} / sqrt(r1) with H^T H = n I and D^2 = I: S^T S = (n / r1) I exactly
+    when T has r1 distinct columns (a repeated or mis-signed column breaks it)."""
+    S = sk.Sketch(n, r1, 1, 17, kind=sk.SRHT)
+    assert S.npad == n and len(set(S.T.tolist())) == r1
+    assert S.T.min() >= 0 and S.T.max() < n
+    D = S.dense()
+    assert np.allclose(np.abs(D), 1.0 / np.sqrt(r1), rtol=1e-15, atol=0)
+    assert np.allclose(D.T @ D, (n / r1) * np.eye(r1), rtol=0, atol=1e-12)
+
+
+def test_srht_apply_matches_fast_walsh_hadamard_transform():
+    """A S against the butterfly recursion of the Walsh-Hadamard transform on the
+    D-signed, zero-padded rows of A, then the columns of T (n = 300 -> n' = 512)."""
+    rng = np.random.default_rng(4)
+    m, n, r1 = 7, 300, 40
+    A = rng.standard_normal((m, n))
+    S = sk.Sketch(n, r1, 1, 29, kind=sk.SRHT)
+    assert S.npad == 512
+    X = np.zeros((m, 512))
+    X[:, :n] = A * S.d[:n]
+    h = 1
+    while h < 512:                       # in-place butterflies (x + y, x - y)
+        X = X.reshape(m, -1, 2, h)
+        X = np.stack([X[:, :, 0] + X[:, :, 1], X[:, :, 0] - X[:, :, 1]], axis=2).reshape(m, 512)
+        h *= 2
+    ref = X[:, S.T] / np.sqrt(r1)
+    assert np.allclose(sk.apply_right(A, S), ref, rtol=0, atol=1e-12)
+    # zero columns appended up to n' change nothing (the padding reading)
+    Ap = np.zeros((m, 512))
+    Ap[:, :n] = A
+    S512 = sk.Sketch(512, r1, 1, 29, kind=sk.SRHT)
+    assert np.allclose(sk.apply_right(Ap, S512), sk.apply_right(A, S), rtol=0, atol=1e-12)
+
+
+def test_srht_column_draws_uniform():
+    """Each of the n' = 16 columns lands in T (r1 = 4) with probability 1/4, and the
+    first drawn column is uniform over the 16."""
+    counts = np.zeros(16)
+    first = np.zeros(16)
+    trials = 3000
+    for seed in range(trials):
+        T = sk.srht_columns(4, 4, seed)
+        assert len(set(T.tolist())) == 4
+        counts[T] += 1
+        first[T[0]] += 1
+    assert scipy.stats.chisquare(counts).pvalue > 1e-4
+    assert scipy.stats.chisquare(first).pvalue > 1e-4
+    d = sk.srht_signs(1 << 16, 5)
+    assert abs(d.mean()) < 5 / np.sqrt(d.size)
+
+
+def test_dense_sign_entries():
+    n, r1 = 2000, 300
+    S = sk.Sketch(n, r1, 1, 42, kind=sk.DENSE_SIGN)
+    D = S.dense()
+    assert np.array_equal(np.abs(D), np.full((n, r1), 1.0 / np.sqrt(r1)))
+    G = D.T @ D
+    assert np.allclose(np.diag(G), n / r1, rtol=1e-14)
+    off = (G - np.diag(np.diag(G))) * r1 / np.sqrt(n)      # ~ N(0, 1) per entry
+    assert abs(off.std() - 1.0) < 0.03 and np.abs(off).max() < 6.0
+    sg = S.signs.astype(np.float64)
+    assert abs(sg.mean()) < 5 / np.sqrt(sg.size)
+    # neighbouring entries come from neighbouring bits of one draw: uncorrelated
+    assert abs(np.mean(sg[:, :-1] * sg[:, 1:])) < 5 / np.sqrt(sg.size)
+    assert abs(np.mean(sg[:-1] * sg[1:])) < 5 / np.sqrt(sg.size)
+    assert np.array_equal(sk.dense_signs(5, 7, 42), S.signs[:5, :7])
+
+
+@pytest.mark.parametrize("kind", [sk.DENSE_SIGN, sk.SRHT, sk.SPARSE_SIGN])
+def test_sketch_families_are_subspace_embeddings(kind):
+    """Lemma 3.2: for U (n x k) with orthonormal columns, U^T S S^T U is close to
+    I once r1 >> k; each family's scale makes E[S S^T] = I (a wrong scale fails)."""
+    rng = np.random.default_rng(8)
+    n, k, r1 = 1024, 8, 512
+    U, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    S = sk.Sketch(n, r1, 8, 77, kind=kind)
+    SU = sk.apply_left_t(S, U)
+    assert np.linalg.norm(SU.T @ SU - np.eye(k), 2) < 0.5
+
+
+@pytest.mark.parametrize("kind", [sk.DENSE_SIGN, sk.SRHT])
+def test_exact_low_rank_is_recovered_with_dense_sketches(kind):
+    sigma = np.array([5.0, 3.0, 2.0, 1.0, 0.5])
+    A, _ = wl.dense_lowrank(90, 60, sigma, seed=12)
+    S = sk.Sketch(60, 20, 1, 3, kind=kind)
+    Q = alg.range_finder(A, S, sk.gaussian(20, 8, 4), q=1)
+    assert alg.residual_fro(A, Q) < 1e-13 * np.linalg.norm(A)
+
+
 def test_gaussian_omega_is_standard_normal():
     z = sk.gaussian(300, 400, seed=43).reshape(-1)
     assert abs(z.mean()) < 5 / np.sqrt(z.size)

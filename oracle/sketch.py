@@ -103,10 +103,13 @@ def dense_signs(n, r1, seed):
     """Signs (n, r1) of the dense sign sketch (Lemma 3.2 item 1), as +-1 int8."""
     k0, k1 = seed_key(seed)
     j = np.arange(n, dtype=np.uint64)[:, None]
-    c = np.arange(r1, dtype=np.uint64)[None, :]
-    j, c = np.broadcast_arrays(j, c)
-    bit = _bits(philox4x32_10(j & _MASK32, j >> _S32, c >> np.uint64(7), 4, k0, k1), c)
-    return (1 - 2 * bit.astype(np.int64)).astype(np.int8)
+    blk = np.arange((r1 + 127) // 128, dtype=np.uint64)[None, :]
+    W = np.stack(philox4x32_10(j & _MASK32, j >> _S32, blk, 4, k0, k1))   # (4, n, blocks)
+    c = np.arange(r1, dtype=np.uint64)
+    words = W[((c >> np.uint64(5)) & np.uint64(3)).astype(np.int64), :,
+              (c >> np.uint64(7)).astype(np.int64)]                          # (r1, n)
+    bit = (words >> (c & np.uint64(31))[:, None]) & np.uint64(1)
+    return np.ascontiguousarray((1 - 2 * bit.astype(np.int64)).T).astype(np.int8)
 
 
 def hadamard_order(n):

@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--final-passes", type=int, default=3)
     p.add_argument("--power-passes", type=int, default=3)
     p.add_argument("--cpu-rows", type=int, default=2048)
+    p.add_argument("--sketch", default="sparse", choices=["sparse", "dense", "srht"],
+                   help="sketch family of Lemma 3.2 (item 2, 1 or 3) for the rsvd workload")
     p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr", "nystrom"],
                    help="rsvd: the 65536 x 16384 RandSVD (default); batched: 512 uneven "
                         "problems in one graph-captured spm_rsvd_batched call; csr: the "
@@ -63,8 +65,10 @@ def parse():
 
 
 def workload_name(a):
+    sk = {"sparse": f"sparse sign sketch r1={a.r1} s={a.s}", "dense": f"dense sign sketch r1={a.r1}",
+          "srht": f"SRHT sketch r1={a.r1}"}[getattr(a, "sketch", "sparse")]
     return (f"dense {a.m}x{a.n} f32, sigma_i=exp(-i/200) + {a.noise:g}*N(0,1) noise, "
-            f"k={a.k}, sketch r1={a.r1} s={a.s}, q={a.q}, RandSVD")
+            f"k={a.k}, {sk}, q={a.q}, RandSVD")
 
 
 # ------------------------------------------------------------------ clocks
@@ -529,7 +533,12 @@ def main():
     m, n, r1, k = a.m, a.n, a.r1, a.k
     A, sigma = wl.noisy_exp_torch(m, n, seed=1002 + rank * 0, noise=a.noise)
     torch.cuda.synchronize()
-    S = spm.Sketch(n, r1, a.s, seed=42)
+    kind = {"sparse": spm.SPARSE_SIGN, "dense": spm.DENSE_SIGN, "srht": spm.SRHT}[a.sketch]
+    if a.sketch != "sparse":
+        # the other families are compared on the timed step and its residual only
+        # (their plain FP64 form would multiply by a dense n x r1 S on CUDA cores)
+        a.no_fp64 = a.no_e2e = a.no_cpu = True
+    S = spm.Sketch(n, r1, a.s, seed=42, kind=kind)
     U = torch.empty(m, k, device="cuda")
     sg = torch.empty(k, device="cuda")
     Vt = torch.empty(k, n, device="cuda")
@@ -607,19 +616,31 @@ def main():
     proj_ms = stages.get("project", 0.0)
     apply_ms = stages.get("apply", 0.0)
     proj_flops = a.final_passes * 2.0 * m * n * k
-    apply_bytes = 4.0 * m * n + 2.0 * m * r1
+    # A read once; A~ written as BF16 (hi, and lo when the power products use
+    # the split)
+    apply_bytes = 4.0 * m * n + (4.0 if a.power_passes > 1 else 2.0) * m * r1
+    apply_kernel = {"sparse": "k_sketch_apply_sacc", "srht": "k_srht_apply",
+                    "dense": "k_gemm_tc (A S, dense sign)"}[a.sketch]
     if proj_ms >= apply_ms:
         ach = proj_flops / (proj_ms * 1e-3) / 1e12
         roof = {"kernel": "k_gemm_tc (B = Q^T A, %d BF16 passes)" % a.final_passes,
                 "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": ach / bf16_peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    elif a.sketch == "dense":
+        # the stage also holds the BF16 split of A and of the product; the
+        # contraction's flops over the stage time bound its rate from below
+        flops = (2 if a.power_passes > 1 else 1) * 2.0 * m * n * r1
+        ach = flops / (apply_ms * 1e-3) / 1e12
+        roof = {"kernel": apply_kernel + ", apply stage", "bound": "tensor", "achieved": ach,
+                "peak": bf16_peak, "unit": "TFLOP/s", "frac": ach / bf16_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
     else:
         ach = apply_bytes / (apply_ms * 1e-3) / 1e9
         default_size = (m, n, r1, a.s) == (65536, 16384, 2000, 8)
-        roof = {"kernel": "k_sketch_apply_sacc", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+        roof = {"kernel": apply_kernel, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
                 "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": NCU_TRAFFIC["k_sketch_apply"] if default_size else None,
+                "traffic": NCU_TRAFFIC["k_sketch_apply"] if default_size and a.sketch == "sparse" else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
     sketch_roof = {"achieved_gbs": apply_bytes / (apply_ms * 1e-3) / 1e9 if apply_ms else None,
                    "frac": (apply_bytes / (apply_ms * 1e-3) / 1e9) / hbm_peak if apply_ms else None}
@@ -667,7 +688,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32",
             "data": "synthetic (seeded, generated on device)",
-            "config": {"workload": workload_name(a), "precision": "mixed",
+            "config": {"workload": workload_name(a), "sketch": a.sketch, "precision": "mixed",
                        "final_passes": a.final_passes, "power_passes": a.power_passes, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs (4.3 GB) larger than L2; no flush"},
             "accuracy": {"residual_mixed": res_mixed, "residual_fp64": fp64.get("residual"),

@@ -57,6 +57,9 @@ extern "C" {
 
 #define SPM_SKETCH_SPARSE_SIGN 0 /* s non-zeros +-1/sqrt(s) per row (Lemma 3.2 item 2) */
 #define SPM_SKETCH_IDENTITY 1    /* S = I (r1 = n): the classical power method (Section 2) */
+#define SPM_SKETCH_DENSE_SIGN 2  /* independent +-1/sqrt(r1) entries (Lemma 3.2 item 1)       */
+#define SPM_SKETCH_SRHT 3        /* (1/sqrt(r1)) D H I_{:,T}: subsampled randomized Hadamard
+                                    transform (Lemma 3.2 item 3)                            */
 
 #define SPM_PREC_FP64 0   /* every product and factorisation in FP64 (CUDA cores)        */
 #define SPM_PREC_MIXED 1  /* BF16 tensor-core products (FP32 accumulate), split-precision
@@ -135,8 +138,24 @@ uint64_t spm_launch_count(void);
  * `seed`; column = floor(u * r1 / 2^32).  The tables are built on the device in
  * stream order and are bit-identical to the CPU oracle's for the same seed.
  * kind = SPM_SKETCH_IDENTITY needs r1 == n and s == 1 (S = I).
- * Errors: SPM_EINVAL if n < 1, r1 < 1, s < 1, s > r1, s > 64, n > 2^31 - 1,
- * r1 > 2^31 - 1, or out == NULL.
+ * kind = SPM_SKETCH_DENSE_SIGN (Lemma 3.2 item 1): entry (j, c) = +-1/sqrt(r1), the
+ *   sign bit c & 31 of word (c >> 5) & 3 of the Philox block at counter
+ *   (j lo, j hi, c >> 7, 4) (1 = minus); s is not used.  Held as an n x r1 BF16
+ *   +-1 matrix; A S runs on the tensor cores when it is kept in BF16 (mixed
+ *   precision), on CUDA cores in FP32/FP64 otherwise.
+ * kind = SPM_SKETCH_SRHT (Lemma 3.2 item 3): S = (1/sqrt(r1)) D H I_{:,T} with H
+ *   Sylvester's Hadamard matrix of order n' = 2^L, the smallest power of two >= n
+ *   (A is read as padded with zero columns; S is the first n rows), D_j the bit
+ *   j & 31 of word (j >> 5) & 3 of the block at counter (j >> 7, 0, 0, 5), and T
+ *   the first r1 distinct columns word >> (32 - L) drawn from the words u of the
+ *   blocks at counters (u >> 2, 0, 0, 6), in draw order; s is not used.  Needs
+ *   r1 <= n; n <= 32768 (SPM_EUNSUPPORTED beyond: a row of the transform is held
+ *   in one CTA's shared memory; FP64 inputs need n <= 16384 at apply time).
+ *   The dense kinds have no sparse tables: spm_sketch_tables and the CSR entry
+ *   points return SPM_EUNSUPPORTED for them.
+ * Errors: SPM_EINVAL if n < 1, r1 < 1, s < 1, n > 2^31 - 1, r1 > 2^31 - 1,
+ * out == NULL, an unknown kind, or (sparse sign) s > r1 or s > 64, or (SRHT)
+ * r1 > n.
  * Ownership: *out is owned by the caller and released with spm_sketch_destroy. */
 int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64_t seed,
                       int32_t kind, void* stream);
@@ -161,7 +180,9 @@ int spm_gaussian(void* out, int32_t dtype, int64_t rows, int64_t cols, int64_t l
 
 /* ---- a3: sketch products ----------------------------------------------------
  * out (m x r1, ld ldo) = A (m x n, ld lda) * S  (Algorithm 1 line 1, A~ = A S;
- * Algorithm 3 line 1, C~ = A S).  Sums run over the column buckets of S. */
+ * Algorithm 3 line 1, C~ = A S).  Sparse kinds: sums run over the column buckets
+ * of S.  Dense sign: a dense product.  SRHT: a fast Walsh-Hadamard transform of
+ * each row of A, then the columns of T. */
 int spm_sketch_apply(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,
                      void* out, int64_t ldo, void* stream);
 /* out (r1 x p, ld ldo) = S^T X with X (n x p, ld ldx)  (Algorithm 2 line 2: S2^T Y,

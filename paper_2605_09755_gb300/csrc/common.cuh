@@ -205,4 +205,10 @@ struct spm_sketch {
                           // bits 0..14, accumulator offset (c mod cg) * 33 in bits 15..30,
                           // sign in bit 31 (the shared-accumulator apply kernel); or null
   int32_t acc_cg;         // column-group size of entacc (at most SACC_MAX_CG)
+  // dense families (Lemma 3.2 items 1 and 3); null for the sparse kinds
+  __nv_bfloat16* dsign;   // dense sign: n x ld_dsign, +-1 (exact in BF16)
+  int64_t ld_dsign;
+  uint32_t* dbits;        // SRHT: D as bits (1 = minus), max(1, n'/32) words
+  int32_t* hcols;         // SRHT: the r1 sampled Hadamard columns, in draw order
+  int32_t hl;             // SRHT: log2 n'
 };

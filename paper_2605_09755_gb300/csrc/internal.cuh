@@ -39,6 +39,20 @@ int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, 
 int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
                  cudaStream_t st);
 
+// ---------------------------------------------------------------- sketch_dense.cu
+// Dense sign (Lemma 3.2 item 1) and SRHT (item 3) sketches: tables, A S and
+// S^T X with the contracts of sketch_apply_dev / sketch_apply_t_dev.
+int dense_sketch_create(spm_sketch* S, cudaStream_t st);
+void dense_sketch_free(spm_sketch* S);
+int dense_sketch_apply(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
+                       void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
+                       void* out_lo);
+int dense_sketch_apply_t(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
+                         void* out, int out_dt, int64_t ldo, cudaStream_t st);
+inline bool dense_kind(const spm_sketch* S) {
+  return S->kind == SPM_SKETCH_DENSE_SIGN || S->kind == SPM_SKETCH_SRHT;
+}
+
 // ---------------------------------------------------------------- gemm_simt.cu
 // C = alpha * A(MxK) * B(KxN) + beta * C  on CUDA cores.  Accumulates in FP64 if
 // any operand is FP64, else FP32.  batch > 1: pointers advance by the strides.

@@ -715,6 +715,7 @@ int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, in
                      void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
                      void* out_lo) {
   if (m <= 0) return SPM_OK;
+  if (dense_kind(S)) return dense_sketch_apply(S, A, a_dt, m, lda, out, out_dt, ldo, fro2, st, out_lo);
   if (a_dt == DT_F32) {
     const float* a = (const float*)A;
     if (out_dt == DT_F32) return launch_apply<float, float, float, 32, 2>(S, a, m, lda, (float*)out, ldo, fro2, st);
@@ -736,6 +737,7 @@ int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, in
 int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
                        void* out, int out_dt, int64_t ldo, cudaStream_t st) {
   if (p <= 0) return SPM_OK;
+  if (dense_kind(S)) return dense_sketch_apply_t(S, X, x_dt, p, ldx, out, out_dt, ldo, st);
   const int64_t strips = cdiv(p, 256);
   const int64_t grid = strips * S->r1;
   if (grid > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
@@ -774,8 +776,29 @@ int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64
     if (r1 > 48 * 1024) return SPM_EUNSUPPORTED;  // per-chunk histogram lives in shared memory
   } else if (kind == SPM_SKETCH_IDENTITY) {
     if (r1 != n || s != 1) return SPM_EINVAL;
+  } else if (kind == SPM_SKETCH_DENSE_SIGN) {
+    if (n * round_up(r1, 8) > ((int64_t)1 << 36)) return SPM_EUNSUPPORTED;
+  } else if (kind == SPM_SKETCH_SRHT) {
+    if (r1 > n) return SPM_EINVAL;
+    if (n > 32768) return SPM_EUNSUPPORTED;  // one row of the transform per CTA in shared memory
   } else {
     return SPM_EINVAL;
+  }
+  if (kind == SPM_SKETCH_DENSE_SIGN || kind == SPM_SKETCH_SRHT) {
+    spm_sketch* S = new spm_sketch();
+    S->n = n;
+    S->r1 = r1;
+    S->s = s;
+    S->kind = kind;
+    S->seed = seed;
+    S->stream = as_stream(stream);
+    const int rc = dense_sketch_create(S, S->stream);
+    if (rc != SPM_OK) {
+      spm_sketch_destroy(S);
+      return rc;
+    }
+    *out = S;
+    return SPM_OK;
   }
   if (n * (int64_t)s > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
   cudaStream_t st = as_stream(stream);
@@ -847,6 +870,7 @@ int spm_sketch_destroy(spm_sketch* S) {
   if (S->seg) cudaFreeAsync(S->seg, S->stream);
   if (S->entoff) cudaFreeAsync(S->entoff, S->stream);
   if (S->entacc) cudaFreeAsync(S->entacc, S->stream);
+  dense_sketch_free(S);
   delete S;
   return SPM_OK;
 }
@@ -863,6 +887,7 @@ int spm_sketch_shape(const spm_sketch* S, int64_t* n, int64_t* r1, int32_t* s, i
 int spm_sketch_tables(const spm_sketch* S, int32_t* cols, int8_t* signs, int64_t* bucket_ptr,
                       int32_t* bucket_rows, int8_t* bucket_signs, void* stream) {
   if (!S) return SPM_EINVAL;
+  if (dense_kind(S)) return SPM_EUNSUPPORTED;  // no sparse tables
   cudaStream_t st = as_stream(stream);
   const int64_t nnz = S->n * S->s;
   if (cols) SPM_CUDA_TRY(cudaMemcpyAsync(cols, S->cols, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));

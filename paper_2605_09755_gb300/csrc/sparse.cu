@@ -250,7 +250,7 @@ int csr_check(const spm_csr* A, int64_t n) {
 
 int csr_sketch_dev(const spm_sketch* S, const spm_csr* A, int dt, void* out, int64_t ldo, int* status,
                    cudaStream_t st, bool tc) {
-  if (S->kind != SPM_SKETCH_SPARSE_SIGN && S->kind != SPM_SKETCH_IDENTITY) return SPM_EINVAL;
+  if (S->kind != SPM_SKETCH_SPARSE_SIGN && S->kind != SPM_SKETCH_IDENTITY) return SPM_EUNSUPPORTED;
   const int64_t m = A->m, n = A->n, r1 = S->r1;
   const int s = S->s;
   const size_t es = dt == DT_F64 ? 8 : 4;

@@ -13,7 +13,8 @@ import torch
 from . import _build
 
 F32, F64 = 0, 1
-SPARSE_SIGN, IDENTITY = 0, 1
+SPARSE_SIGN, IDENTITY, DENSE_SIGN, SRHT = 0, 1, 2, 3
+EUNSUPPORTED = 7  # SPM_EUNSUPPORTED
 PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
 EINVAL = 1  # SPM_EINVAL
 STAGES = ("sketch", "apply", "power", "orth", "project", "small", "finish", "other")
@@ -134,7 +135,8 @@ def _require_cuda(*ts):
 
 
 class Sketch:
-    """Device tables of one sparse sign sketch S in R^{n x r1} (or the identity)."""
+    """Device tables of one sketch S in R^{n x r1}: sparse sign (default), identity,
+    dense sign or SRHT (``kind``; s is not used by the two dense kinds)."""
 
     def __init__(self, n, r1, s=8, seed=42, kind=SPARSE_SIGN):
         h = ctypes.c_void_p()

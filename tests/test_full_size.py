@@ -1,0 +1,94 @@
+"""The 65536 x 16384 workload at full size, in the launch configuration the
+benchmark times (FP32 A, mixed precision, r1 = 2000, k = r2 = 1000, q = 2), for
+the sparse sign sketch (s = 8) and the two dense families of Lemma 3.2.
+
+A is the seeded device generator's sigma_i = exp(-i/200) matrix plus 1e-3 N(0,1)
+noise.  The oracle cannot run the whole problem in seconds, so:
+  * 64 sampled rows of A S against the oracle's row-by-row products (FP32
+    output; bound 3e-5 relative to the row's largest entry: an index, sign or
+    scale error is of order 1, the FP32 sums' rounding about u32 sqrt(n) / 5 ~ 2e-6);
+  * properties of the mixed RandSVD that hold at any size: sigma positive and
+    descending; U and V orthonormal (||U^T U - I||_F <= k u32 sqrt(m) = 2e-2, the
+    single-precision inner products over m rows); U_i^T A V_i = sigma_i on
+    the leading directions (within 1e-4 sigma_1); the Pythagorean identity of
+    a projection, ||A - U S V^T||_F^2 = ||A||_F^2 - sum sigma_i^2 (within 1e-3);
+  * the three sketch families at the same r1 reach residuals within 1% of each
+    other (Lemma 3.2: each is a regularized spectral approximation; here the
+    noise dominates and every family lands near the rank-k optimum).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sketch as osk
+from paper_2605_09755_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+M, N, R1, K, Q = 65536, 16384, 2000, 1000, 2
+
+
+@pytest.fixture(scope="module")
+def spm():
+    from paper_2605_09755_gb300 import _build, spm as _spm
+    _build.build()
+    _spm.lib()
+    return _spm
+
+
+@pytest.fixture(scope="module")
+def big():
+    A, _ = wl.noisy_exp_torch(M, N, seed=1002, noise=1e-3)
+    torch.cuda.synchronize()
+    yield A
+    del A
+    torch.cuda.empty_cache()
+
+
+def _sketches(spm):
+    return {"sparse": (spm.Sketch(N, R1, 8, 42), osk.Sketch(N, R1, 8, 42)),
+            "dense": (spm.Sketch(N, R1, 1, 42, kind=spm.DENSE_SIGN),
+                      osk.Sketch(N, R1, 1, 42, kind=osk.DENSE_SIGN)),
+            "srht": (spm.Sketch(N, R1, 1, 42, kind=spm.SRHT), osk.Sketch(N, R1, 1, 42, kind=osk.SRHT))}
+
+
+def _residual2(A, U, sg, Vt, chunk=4096):
+    tot = 0.0
+    Us = U * sg
+    for i in range(0, A.shape[0], chunk):
+        R = A[i:i + chunk] - Us[i:i + chunk] @ Vt
+        tot += float((R.double() ** 2).sum())
+    return tot
+
+
+def test_full_size_sketch_rows_and_factors(spm, big):
+    A = big
+    rows = np.random.default_rng(17).choice(M, 64, replace=False)
+    Arows = A[torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+    fro2 = float((A.double() ** 2).sum())
+    res2 = {}
+    for name, (S, So) in _sketches(spm).items():
+        At = spm.sketch_apply(S, A)
+        got = At[torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+        del At
+        ref = osk.apply_right(Arows, So)
+        err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+        assert np.all(err <= 3e-5), (name, err.max())
+
+        U, sg, Vt, info = spm.rsvd(S, A, K, Q, K, omega_seed=43, precision=spm.PREC_MIXED)
+        torch.cuda.synchronize()
+        assert info["device_status"] == 0, name
+        s = sg.double()
+        assert bool(torch.all(s[:-1] >= s[1:])) and float(s[-1]) > 0, name
+        eye = torch.eye(K, device="cuda", dtype=torch.float64)
+        assert float(torch.linalg.norm(U.double().T @ U.double() - eye)) <= 2e-2, name
+        assert float(torch.linalg.norm(Vt.double() @ Vt.double().T - eye)) <= 2e-2, name
+        lead = (U[:, :8].double().T @ (A @ Vt[:8].T).double())
+        assert float(torch.max(torch.abs(lead - torch.diag(s[:8])))) <= 1e-4 * float(s[0]), name
+        r2 = _residual2(A, U, sg, Vt)
+        assert abs(r2 - (fro2 - float((s ** 2).sum()))) <= 1e-3 * fro2, name
+        res2[name] = r2
+        del U, sg, Vt
+        torch.cuda.empty_cache()
+    for name in ("dense", "srht"):
+        assert abs(np.sqrt(res2[name] / res2["sparse"]) - 1) <= 1e-2, (name, res2)

@@ -584,6 +584,10 @@ static int rsvd_finish_simt(Call& C, const void* A, int64_t m, int64_t n, int64_
   SPM_ALLOC(C.ar, T, W, r2 * n);
   SPM_ALLOC(C.ar, double, sig, r2);
   SPM_ALLOC(C.ar, T, Uo, m * k);
+  SPM_ALLOC(C.ar, int, perm, r2);
+  SPM_ALLOC(C.ar, double, sigs, r2);
+  SPM_ALLOC(C.ar, T, Wk, k * n);
+  SPM_ALLOC(C.ar, T, Utk, r2 * k);
   {
     StageScope sc(C.timer, SPM_STAGE_PROJECT);
     if (C.make_b)
@@ -605,13 +609,18 @@ static int rsvd_finish_simt(Call& C, const void* A, int64_t m, int64_t n, int64_
     SPM_TRY(gemm_simt(r2, n, r2, 1.0, transpose(rowmajor(Ut, dt, r2)),
                       rowmajor(B, dt, n), 0.0, mrowmajor(W, dt, n), C.st));
     SPM_TRY(norms(r2, n, rowmajor(W, dt, n), false, sig, C.st));
-    SPM_TRY(scale_lines(k, n, mrowmajor(W, dt, n), true, sig, true, C.st));
-    SPM_TRY(gemm_simt(m, k, r2, 1.0, rowmajor(Q, dt, r2), rowmajor(Ut, dt, r2), 0.0,
+    // sigma_i = |row i of W|, ordered by the eigenvalues; order them by their
+    // own values (the two can swap neighbours that agree to rounding)
+    SPM_TRY(desc_order(r2, sig, perm, sigs, C.st));
+    SPM_TRY(gather_lines(k, n, rowmajor(W, dt, n), mrowmajor(Wk, dt, n), perm, true, C.st));
+    SPM_TRY(gather_lines(k, r2, rowmajor(Ut, dt, r2), mrowmajor(Utk, dt, k), perm, false, C.st));
+    SPM_TRY(scale_lines(k, n, mrowmajor(Wk, dt, n), true, sigs, true, C.st));
+    SPM_TRY(gemm_simt(m, k, r2, 1.0, rowmajor(Q, dt, r2), rowmajor(Utk, dt, k), 0.0,
                       mrowmajor(Uo, dt, k), C.st));
-    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, dt, k), mrowmajor(W, dt, n), C.st));
+    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, dt, k), mrowmajor(Wk, dt, n), C.st));
     SPM_TRY(store_out(m, k, rowmajor(Uo, dt, k), U, edt, ldu, C.st));
-    SPM_TRY(store_out(k, n, rowmajor(W, dt, n), Vt, edt, ldvt, C.st));
-    SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
+    SPM_TRY(store_out(k, n, rowmajor(Wk, dt, n), Vt, edt, ldvt, C.st));
+    SPM_TRY(copy_vec(k, sigs, sigma, edt, C.st));
   }
   return SPM_OK;
 }
@@ -647,6 +656,12 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
   SPM_ALLOC(C.ar, float, W, r2 * n);
   SPM_ALLOC(C.ar, double, sig, r2);
   SPM_ALLOC(C.ar, float, Uo, m * k);
+  const int64_t kp = pad8(k);
+  SPM_ALLOC(C.ar, int, perm, r2);
+  SPM_ALLOC(C.ar, double, sigs, r2);
+  SPM_ALLOC(C.ar, float, Wk, k * n);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Ukhi, r2 * kp);
+  SPM_ALLOC(C.ar, __nv_bfloat16, Uklo, r2 * kp);
   {
     StageScope sc(C.timer, SPM_STAGE_PROJECT);
     if (C.make_b) {
@@ -677,13 +692,21 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     // W = U~^T B: A-op U~^T (M = r2, K = r2) MN-major; B-op B (N = n, K = r2) MN-major
     SPM_TRY(tc_split(r2, n, r2, Uhi, Ulo, r2p, true, Bhi, Blo, np_, true, 3, W, n, 1, C.st));
     SPM_TRY(norms(r2, n, rowmajor(W, DT_F32, n), false, sig, C.st));
-    SPM_TRY(scale_lines(k, n, mrowmajor(W, DT_F32, n), true, sig, true, C.st));
+    // sigma_i = |row i of W|, ordered by the eigenvalues; order them by their
+    // own values (the two can swap neighbours that agree to rounding)
+    SPM_TRY(desc_order(r2, sig, perm, sigs, C.st));
+    SPM_TRY(gather_lines(k, n, rowmajor(W, DT_F32, n), mrowmajor(Wk, DT_F32, n), perm, true, C.st));
+    SPM_TRY(gather_lines(k, r2, rowmajor(Uhi, DT_BF16, r2p), mrowmajor(Ukhi, DT_BF16, kp), perm,
+                         false, C.st));
+    SPM_TRY(gather_lines(k, r2, rowmajor(Ulo, DT_BF16, r2p), mrowmajor(Uklo, DT_BF16, kp), perm,
+                         false, C.st));
+    SPM_TRY(scale_lines(k, n, mrowmajor(Wk, DT_F32, n), true, sigs, true, C.st));
     // U = Q U~[:, :k]: A-op Q (M = m, K = r2) K-major; B-op U~ (N = k, K = r2) MN-major
-    SPM_TRY(tc_split(m, k, r2, rf.Qhi, rf.Qlo, r2p, false, Uhi, Ulo, r2p, true, 3, Uo, k, 1, C.st));
-    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F32, k), mrowmajor(W, DT_F32, n), C.st));
+    SPM_TRY(tc_split(m, k, r2, rf.Qhi, rf.Qlo, r2p, false, Ukhi, Uklo, kp, true, 3, Uo, k, 1, C.st));
+    SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F32, k), mrowmajor(Wk, DT_F32, n), C.st));
     SPM_TRY(store_out(m, k, rowmajor(Uo, DT_F32, k), U, edt, ldu, C.st));
-    SPM_TRY(store_out(k, n, rowmajor(W, DT_F32, n), Vt, edt, ldvt, C.st));
-    SPM_TRY(copy_vec(k, sig, sigma, edt, C.st));
+    SPM_TRY(store_out(k, n, rowmajor(Wk, DT_F32, n), Vt, edt, ldvt, C.st));
+    SPM_TRY(copy_vec(k, sigs, sigma, edt, C.st));
   }
   return SPM_OK;
 }

@@ -1164,6 +1164,76 @@ int scale_lines(int64_t rows, int64_t cols, MView X, bool rows_not_cols, const d
   return SPM_OK;
 }
 
+// Descending order of x[0..r): pos(i) = #{j : x_j > x_i, or x_j = x_i and j < i}
+// (NaN ranks last, as -inf), so every position is taken exactly once;
+// perm[pos(i)] = i, xs[pos(i)] = x_i.  x is staged through shared memory.
+__device__ __forceinline__ double order_key(double v) { return v == v ? v : -INFINITY; }
+
+__global__ void k_desc_order(int r, const double* __restrict__ x, int* __restrict__ perm,
+                             double* __restrict__ xs) {
+  __shared__ double tile[1024];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double ki = i < r ? order_key(x[i]) : 0.0;
+  int pos = 0;
+  for (int j0 = 0; j0 < r; j0 += 1024) {
+    const int nt = min(1024, r - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) tile[t] = order_key(x[j0 + t]);
+    __syncthreads();
+    if (i < r)
+      for (int t = 0; t < nt; ++t) {
+        const double kj = tile[t];
+        pos += (kj > ki) || (kj == ki && j0 + t < i);
+      }
+  }
+  if (i < r) {
+    perm[pos] = i;
+    xs[pos] = x[i];
+  }
+}
+
+int desc_order(int64_t r, const double* x, int* perm, double* xs, cudaStream_t st) {
+  if (r <= 0) return SPM_OK;
+  if (r > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  k_desc_order<<<(unsigned)cdiv(r, 256), 256, 0, st>>>((int)r, x, perm, xs);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+// dst line l = src line perm[l] (rows when by_row, else columns), l < lines.
+template <typename T>
+__global__ void k_gather_lines(int64_t lines, int64_t len, const T* __restrict__ src, int64_t srs,
+                               int64_t scs, T* __restrict__ dst, int64_t drs, int64_t dcs,
+                               const int* __restrict__ perm, bool by_row) {
+  for (int64_t l = blockIdx.y; l < lines; l += gridDim.y) {
+    const int64_t from = perm[l];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      if (by_row)
+        dst[l * drs + e * dcs] = src[from * srs + e * scs];
+      else
+        dst[e * drs + l * dcs] = src[e * srs + from * scs];
+    }
+  }
+}
+
+int gather_lines(int64_t lines, int64_t len, View src, MView dst, const int* perm, bool by_row,
+                 cudaStream_t st) {
+  if (lines <= 0 || len <= 0) return SPM_OK;
+  if (src.dt != dst.dt) return SPM_EINVAL;
+  const dim3 g((unsigned)min64(cdiv(len, 256), 64), (unsigned)min64(lines, 65535));
+#define SPM_GL(T)                                                                              \
+  k_gather_lines<T><<<g, 256, 0, st>>>(lines, len, (const T*)src.p, src.rs, src.cs, (T*)dst.p, \
+                                       dst.rs, dst.cs, perm, by_row)
+  if (src.dt == DT_F32) SPM_GL(float);
+  else if (src.dt == DT_F64) SPM_GL(double);
+  else if (src.dt == DT_BF16) SPM_GL(__nv_bfloat16);
+  else return SPM_EINVAL;
+#undef SPM_GL
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
 template <typename T>
 __global__ void k_sumsq(int64_t rows, int64_t cols, const T* __restrict__ X, int64_t rs, int64_t cs,
                         double* acc) {

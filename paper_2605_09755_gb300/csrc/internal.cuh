@@ -137,6 +137,13 @@ int sym_eig(int64_t r, void* A, int64_t lda, void* V, int64_t ldv, void* lam, in
             cudaStream_t st, int* sweeps = nullptr);
 // out[j] = sqrt(sum_i X[i,j]^2) for columns (col = true) or rows (col = false), in FP64.
 int norms(int64_t rows, int64_t cols, View X, bool by_col, double* out, cudaStream_t st);
+// Descending order of x (r values; NaN last; ties by index): perm[pos] = i and
+// xs[pos] = x[i] (device arrays).
+int desc_order(int64_t r, const double* x, int* perm, double* xs, cudaStream_t st);
+// dst line l = src line perm[l] for l < lines (rows when by_row, else columns;
+// each line has len elements).  src and dst of the same type.
+int gather_lines(int64_t lines, int64_t len, View src, MView dst, const int* perm, bool by_row,
+                 cudaStream_t st);
 // Scale rows (or columns) of X by s[i] (or 1/s[i] when inv).
 int scale_lines(int64_t rows, int64_t cols, MView X, bool rows_not_cols, const double* s, bool inv,
                 cudaStream_t st);

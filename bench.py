@@ -32,6 +32,20 @@ METRIC = "time to rank-k approx at fixed rel. residual vs plain FP64 GPU; HBM GB
 NCU_TRAFFIC = {"k_sketch_apply": 8 * (537.8e6 + 12.0e6)}
 
 
+def max_over_ranks(x, dist, device):
+    """x on this rank -> the largest x over the ranks of the default process group."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_approximation_ms(ms_total, steps, world):
+    """Whole-job time per rank-k approximation: each of `world` ranks runs `steps`
+    of them within ms_total (the slowest rank's time)."""
+    return ms_total / (steps * world)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -584,11 +598,9 @@ def main():
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
     if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, dist, "cuda")
     ms_step = ms_total / a.steps
-    value = ms_total / (a.steps * world)   # ms per rank-k approximation, whole job
+    value = per_approximation_ms(ms_total, a.steps, world)
 
     # stage breakdown (events recorded by the library on the launching stream)
     _, _, _, inf = step(info=True, timing=True)

@@ -48,6 +48,12 @@ def test_host_only_calls(libspm):
     assert f(ctypes.byref(h), 0, 10, 1, 1, 0, None) == 1         # n < 1
     assert f(ctypes.byref(h), 100, 50, 1, 1, 1, None) == 1       # identity needs r1 == n
     assert f(None, 100, 10, 1, 1, 0, None) == 1
+    # the dense families (Lemma 3.2 items 1 and 3)
+    assert f(ctypes.byref(h), 100, 101, 1, 1, 3, None) == 1     # SRHT needs r1 <= n
+    assert f(ctypes.byref(h), 40000, 100, 1, 1, 3, None) == 7   # n' = 2^16 > 2^15: unsupported
+    assert f(ctypes.byref(h), 1 << 30, 1 << 10, 1, 1, 2, None) == 7   # n x r1 dense signs > 2^36
+    assert f(ctypes.byref(h), 100, 10, 1, 1, 4, None) == 1      # unknown kind
+    assert f(ctypes.byref(h), 100, 10, 0, 1, 2, None) == 1      # s < 1
 
 
 def test_host_only_argument_checks_of_the_newer_entries(libspm):

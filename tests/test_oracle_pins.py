@@ -188,11 +188,14 @@ def test_dense_sign_entries():
 
 
 @pytest.mark.parametrize("kind", [sk.DENSE_SIGN, sk.SRHT, sk.SPARSE_SIGN])
-def test_sketch_families_are_subspace_embeddings(kind):
+@pytest.mark.parametrize("n", [1024, 600])
+def test_sketch_families_are_subspace_embeddings(kind, n):
     """Lemma 3.2: for U (n x k) with orthonormal columns, U^T S S^T U is close to
-    I once r1 >> k; each family's scale makes E[S S^T] = I (a wrong scale fails)."""
+    I once r1 >> k; each family's scale makes E[S S^T] = I (a wrong scale fails).
+    For the SRHT with n < n' (zero padding) E[S S^T] = (1/r1)(r1/n') D H H^T D = I
+    still holds on the first n rows."""
     rng = np.random.default_rng(8)
-    n, k, r1 = 1024, 8, 512
+    k, r1 = 8, 512
     U, _ = np.linalg.qr(rng.standard_normal((n, k)))
     S = sk.Sketch(n, r1, 8, 77, kind=kind)
     SU = sk.apply_left_t(S, U)

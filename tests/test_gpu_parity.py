@@ -165,6 +165,36 @@ def test_rsvd_fp64_parity(spm, m, n, r1, r2, q, s):
     assert info["device_status"] == 0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rsvd_truncated_rank_below_r2(spm, prec):
+    """k < r2: the finish keeps the k largest of the r2 computed directions (the
+    rows of V^T and columns of U~ gathered in the order of sigma)."""
+    m, n, r1, r2, k, q = 1500, 700, 120, 60, 25, 2
+    A, sigma = wl.plain_fp64(m, n, seed=1001)
+    if prec == "mixed":
+        A = A.astype(np.float32).astype(np.float64)
+    U_o, s_o, Vt_o, _ = _oracle_rsvd(A, n, r1, 8, r2, q, k)
+    res_o = np.linalg.norm(A - (U_o * s_o) @ Vt_o)
+    S = spm.Sketch(n, r1, 8, 42)
+    if prec == "fp64":
+        U, sg, Vt, info = spm.rsvd(S, dev(A), r2, q, k, omega_seed=43, precision=spm.PREC_FP64)
+    else:
+        U, sg, Vt, info = spm.rsvd(S, dev(A, torch.float32), r2, q, k, precision=spm.PREC_MIXED)
+    U, sg, Vt = host(U), host(sg), host(Vt)
+    assert U.shape == (m, k) and sg.shape == (k,) and Vt.shape == (k, n)
+    res = np.linalg.norm(A - (U * sg) @ Vt)
+    if prec == "fp64":
+        assert abs(res - res_o) <= 1e-10 * res_o
+        assert np.max(np.abs(sg - s_o) / s_o) <= 1e-10
+        assert np.linalg.norm(U.T @ U - np.eye(k)) <= 1e-12
+    else:
+        assert res <= 1.01 * res_o, (res, res_o)
+        assert np.max(np.abs(sg - s_o) / s_o) <= 1e-4
+        assert np.linalg.norm(U.T @ U - np.eye(k)) <= 1e-3
+    assert np.all(sg[:-1] >= sg[1:])
+    assert info["device_status"] == 0
+
+
 def test_range_finder_fp64_identity_sketch_is_classical(spm):
     """S = I: the CUDA path reproduces the classical range finder of the oracle."""
     A, sigma = wl.plain_fp64(400, 200, seed=3)

@@ -67,7 +67,14 @@ def parse():
     p.add_argument("--cpu-rows", type=int, default=2048)
     p.add_argument("--sketch", default="sparse", choices=["sparse", "dense", "srht"],
                    help="sketch family of Lemma 3.2 (item 2, 1 or 3) for the rsvd workload")
-    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr", "nystrom"],
+    p.add_argument("--trials", type=int, default=5, help="polydecay: trials (the paper: 25)")
+    p.add_argument("--poly-l", default="800,1200,1600", help="polydecay: sketch sizes l")
+    p.add_argument("--q-sketched", type=int, default=15)
+    p.add_argument("--q-classical", type=int, default=5)
+    p.add_argument("--poly-target", type=float, default=0.1,
+                   help="polydecay: relative spectral error the time is measured to")
+    p.add_argument("--workload", default="rsvd", choices=["rsvd", "batched", "csr", "nystrom",
+                                                          "polydecay"],
                    help="rsvd: the 65536 x 16384 RandSVD (default); batched: 512 uneven "
                         "problems in one graph-captured spm_rsvd_batched call; csr: the "
                         "10^6 x 2*10^5 sparse matrix with a planted rank-200 term; nystrom: the "
@@ -514,6 +521,116 @@ def nystrom_main(a):
     print(json.dumps(line), flush=True)
 
 
+def protocol_summary(records, target):
+    """Section 4's curves from individual runs.
+
+    records: dicts with method ("sketched" or "classical"), l (sketch size; n for
+    the classical form), q, ms and err (relative spectral error).  Returns
+    (curves, best): curves[method:l] = [(q, mean ms, mean err, runs)] by q, and
+    best[method] = the smallest mean time whose mean error is <= target, with its
+    (l, q), or None when no iterate reaches the target."""
+    groups = {}
+    for r in records:
+        groups.setdefault((r["method"], r["l"], r["q"]), []).append(r)
+    curves = {}
+    for (method, l, q), rs in sorted(groups.items()):
+        curves.setdefault(f"{method}:{l}", []).append(
+            (q, statistics.mean(x["ms"] for x in rs), statistics.mean(x["err"] for x in rs), len(rs)))
+    best = {}
+    for key, pts in curves.items():
+        method, l = key.split(":")
+        for q, ms, err, _ in pts:
+            if err <= target and (best.get(method) is None or ms < best[method]["ms"]):
+                best[method] = {"ms": ms, "err": err, "l": int(l), "q": q}
+        best.setdefault(method, None)
+    return curves, best
+
+
+def polydecay_main(a):
+    """Section 4's protocol on its synthetic polydecay matrix (30000 x 15000,
+    sigma_i = 30000 / i between Haar factors), FP32 A, mixed precision, k = 40:
+    the Sketch-Powered RandSVD with a CountSketch S (s = 1) of l columns,
+    l in {800, 1200, 1600}, q = 0..15, against the classical RandSVD (S = I),
+    q = 0..5, each iterate computed from scratch and timed alone (CUDA events),
+    error = ||A - U S V^T||_2 / sigma_{k+1} - 1 (the spectral norm by block power
+    iteration on the residual), averaged over the trials (sketch seed 42 + t,
+    Omega seed 43 + t)."""
+    import torch
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import workloads as wl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    _build.build()
+    lib = spm.lib()
+    m, n, k = 30000, 15000, 40
+    ls = [int(x) for x in a.poly_l.split(",")]
+    A, sigma = wl.polydecay_torch(m, n, seed=1006)
+    torch.cuda.synchronize()
+    sig_k1 = float(sigma[k])
+    U = torch.empty(m, k, device="cuda")
+    sg = torch.empty(k, device="cuda")
+    Vt = torch.empty(k, n, device="cuda")
+    g = torch.Generator(device="cuda")
+
+    def spectral_err():
+        # block power iteration on R = A - U diag(sg) Vt (block 8, 40 steps)
+        g.manual_seed(0)
+        X, _ = torch.linalg.qr(torch.randn(n, 8, device="cuda", generator=g))
+        Us = U * sg
+        for _ in range(40):
+            Y = A @ X - Us @ (Vt @ X)
+            X, _ = torch.linalg.qr(A.T @ Y - Vt.T @ (Us.T @ Y))
+        Y = A @ X - Us @ (Vt @ X)
+        return float(torch.linalg.svdvals(Y)[0]) / sig_k1 - 1.0
+
+    def run(S, q, oseed):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        spm.rsvd(S, A, k, q, k, omega_seed=oseed, out=(U, sg, Vt), info=False,
+                 precision=spm.PREC_MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    records = []
+    ident = spm.Sketch(n, n, 1, 0, kind=spm.IDENTITY)
+    run(ident, 1, 43)                                   # warm-up (kernel attributes, pool)
+    Sw = spm.Sketch(n, ls[0], 1, 41)
+    run(Sw, 1, 43)
+    Sw.close()
+    c0 = lib.spm_launch_count()
+    for t in range(a.trials):
+        for l in ls:
+            S = spm.Sketch(n, l, 1, 42 + t)
+            for q in range(a.q_sketched + 1):
+                ms = run(S, q, 43 + t)
+                records.append({"method": "sketched", "l": l, "q": q, "ms": ms, "err": spectral_err()})
+            S.close()
+        for q in range(a.q_classical + 1):
+            ms = run(ident, q, 43 + t)
+            records.append({"method": "classical", "l": n, "q": q, "ms": ms, "err": spectral_err()})
+    launches = int(lib.spm_launch_count() - c0)
+    curves, best = protocol_summary(records, a.poly_target)
+    sk, cl = best.get("sketched"), best.get("classical")
+    line = {
+        "metric": f"time to relative spectral error <= {a.poly_target:g} (Section 4 protocol)",
+        "value": sk["ms"] if sk else None, "unit": "ms", "n_gpus": 1, "steps": len(records),
+        "warmup": 1, "ms_per_step": sk["ms"] if sk else None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"polydecay {m}x{n} f32, sigma_i = {m}/i, Haar factors, k = {k}; "
+                               f"CountSketch l in {ls}, q = 0..{a.q_sketched}; classical q = "
+                               f"0..{a.q_classical}; {a.trials} trials", "precision": "mixed",
+                   "l2": "A (1.8 GB) larger than L2; no flush"},
+        "best": best, "classical_ms_to_target": cl["ms"] if cl else None,
+        "speedup_vs_classical": (cl["ms"] / sk["ms"]) if (sk and cl) else None,
+        "curves": curves, "roofline": None, "e2e": None, "cpu_baseline": None,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -527,6 +644,9 @@ def main():
         return
     if a.workload == "nystrom":
         nystrom_main(a)
+        return
+    if a.workload == "polydecay":
+        polydecay_main(a)
         return
     import numpy as np
     import torch

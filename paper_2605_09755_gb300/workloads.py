@@ -21,6 +21,8 @@ orthogonal factors -- is the model for all dense cases):
     equal weights), h = lower median of the pairwise distances.
   * ``batch_specs``: uneven batch, m in [512, 8192], n in [256, 4096]
     log-uniform, k in [16, 256], decay i^-alpha or exp(-i/tau).
+  * ``polydecay_torch``: Section 4's synthetic matrix, 30000 x 15000 with
+    sigma_i = 30000 / i between Haar factors, generated on the device.
 """
 import math
 
@@ -107,6 +109,30 @@ def noisy_exp_torch(m, n, seed=1002, noise=1e-3, tau=200.0, device="cuda", chunk
         A[i0:i1] = U[i0:i1] @ Vs
         if noise:
             A[i0:i1] += noise * torch.randn(i1 - i0, n, generator=g, device=device, dtype=torch.float32)
+    del U, V, Vs
+    return A, sigma.cpu().numpy().astype(np.float64)
+
+
+def polydecay_torch(m=30000, n=15000, seed=1006, device="cuda", chunk=8192):
+    """Section 4's polydecay matrix on the device (float32): sigma_i = m / i for
+    i = 1..min(m, n) between Haar factors (float32 QR of seeded Gaussians, sign of
+    diag(R) folded in).  Returns (A, sigma as float64 numpy)."""
+    import torch
+    load_torch_linalg()
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    r = min(m, n)
+    sigma = torch.tensor(float(m) / np.arange(1, r + 1), dtype=torch.float32, device=device)
+    U, Ru = torch.linalg.qr(torch.randn(m, r, generator=g, device=device, dtype=torch.float32))
+    U *= torch.sign(torch.diagonal(Ru))
+    V, Rv = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=torch.float32))
+    V *= torch.sign(torch.diagonal(Rv))
+    del Ru, Rv
+    A = torch.empty(m, n, device=device, dtype=torch.float32)
+    Vs = (V * sigma).t().contiguous()
+    for i0 in range(0, m, chunk):
+        i1 = min(m, i0 + chunk)
+        A[i0:i1] = U[i0:i1] @ Vs
     del U, V, Vs
     return A, sigma.cpu().numpy().astype(np.float64)
 

@@ -73,3 +73,21 @@ def test_max_over_ranks_two_gloo_ranks():
         res = dict(out)
     # both ranks see the slowest rank's time; 2 ranks x 4 steps share it
     assert res[0] == res[1] == (15.0, 15.0 / 8)
+
+
+def test_protocol_summary_curves_and_time_to_target():
+    recs = []
+    for t in range(3):
+        for q, (ms, err) in enumerate([(2.0, 0.5), (3.0, 0.08), (4.0, 0.05)]):
+            recs.append({"method": "sketched", "l": 800, "q": q, "ms": ms + 0.1 * t, "err": err})
+        for q, (ms, err) in enumerate([(2.5, 0.4), (3.5, 0.09)]):
+            recs.append({"method": "sketched", "l": 1600, "q": q, "ms": ms, "err": err})
+        for q, (ms, err) in enumerate([(5.0, 0.9), (9.0, 0.3)]):
+            recs.append({"method": "classical", "l": 15000, "q": q, "ms": ms, "err": err})
+    curves, best = bench.protocol_summary(recs, 0.1)
+    assert [p[0] for p in curves["sketched:800"]] == [0, 1, 2]
+    q1 = curves["sketched:800"][1]
+    assert q1[1] == pytest.approx(3.1) and q1[2] == pytest.approx(0.08) and q1[3] == 3
+    # the fastest iterate under the target, over every sketch size
+    assert best["sketched"] == {"ms": pytest.approx(3.1), "err": pytest.approx(0.08), "l": 800, "q": 1}
+    assert best["classical"] is None           # never reaches 0.1 within its iterates

@@ -118,7 +118,8 @@ def polydecay_torch(m=30000, n=15000, seed=1006, device="cuda", chunk=8192):
     i = 1..min(m, n) between Haar factors (float32 QR of seeded Gaussians, sign of
     diag(R) folded in).  Returns (A, sigma as float64 numpy)."""
     import torch
-    load_torch_linalg()
+    if str(device).startswith("cuda"):
+        load_torch_linalg()
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     r = min(m, n)

@@ -451,3 +451,14 @@ def test_selector_features_closed_form():
     assert np.isclose(f[2], np.log10(s[7]))
     assert np.isclose(f[3], np.log10(r2 * s[7] ** 2 / np.sum(s ** 2)))
     assert np.isclose(f[7], 2.0 / 3)
+
+
+def test_polydecay_generator_spectrum():
+    """Section 4's polydecay matrix: singular values m / i exactly up to FP32 rounding
+    (the benchmark's Section 4 protocol builds it the same way at 30000 x 15000)."""
+    import torch
+    A, sigma = wl.polydecay_torch(300, 150, seed=3, device="cpu")
+    assert A.shape == (300, 150) and A.dtype == torch.float32
+    assert np.allclose(sigma, 300.0 / np.arange(1, 151))
+    s = np.linalg.svd(A.double().numpy(), compute_uv=False)
+    assert np.max(np.abs(s - sigma) / sigma[0]) < 1e-5

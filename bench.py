@@ -27,9 +27,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to rank-k approx at fixed rel. residual vs plain FP64 GPU; HBM GB/s"
 
-# DRAM bytes (read + write) per launch at the 65536 x 16384 size, from one ncu capture of the
-# same kernel on 8192 rows scaled by the rows (profiles/k_sketch_apply_sacc_8192x16384_r2000.md)
-NCU_TRAFFIC = {"k_sketch_apply": 8 * (537.8e6 + 12.0e6)}
+# DRAM bytes (read + write) per launch measured by ncu for the sketch-apply kernel, per
+# element of A and per element of A~ at the capture's shape; scaled to the run's shape
+# (traffic grows with m n and m r1).  None until a capture of the current kernel exists.
+NCU_TRAFFIC = {
+    # profiles/k_sketch_sched_8192x16384_r2000.md: 537.6 MB read + 58.9 MB written at
+    # m = 8192, n = 16384, r1 = 2000 (BF16 hi/lo out)
+    "k_sketch_sched": {"per_a": 537.606656e6 / (8192 * 16384),
+                       "per_out": 58.929664e6 / (8192 * 2000)},
+}
+
+
+def ncu_traffic(kernel, m, n, r1):
+    t = NCU_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    return t["per_a"] * m * n + t["per_out"] * m * r1
 
 
 def max_over_ranks(x, dist, device):
@@ -722,9 +735,11 @@ def main():
     ms_step = ms_total / a.steps
     value = per_approximation_ms(ms_total, a.steps, world)
 
-    # stage breakdown (events recorded by the library on the launching stream)
-    _, _, _, inf = step(info=True, timing=True)
+    # stage breakdown (events recorded by the library on the launching stream), in
+    # the timed steps' configuration (no |A|_F sum); then |A|_F and the estimate
+    _, _, _, inf = step(info=True, timing=2)
     stages = inf["stage_ms"]
+    _, _, _, inf = step(info=True)
     res_mixed = residual(A, U, sg, Vt)
     launches = None
     try:
@@ -751,8 +766,9 @@ def main():
     # A read once; A~ written as BF16 (hi, and lo when the power products use
     # the split)
     apply_bytes = 4.0 * m * n + (4.0 if a.power_passes > 1 else 2.0) * m * r1
-    apply_kernel = {"sparse": "k_sketch_apply_sacc", "srht": "k_srht_apply",
-                    "dense": "k_gemm_tc (A S, dense sign)"}[a.sketch]
+    sched_state = spm.sketch_plan(S)[0] if a.sketch == "sparse" else -1
+    apply_kernel = {"sparse": "k_sketch_sched" if sched_state == 1 else "k_sketch_apply_sacc",
+                    "srht": "k_srht_apply", "dense": "k_gemm_tc (A S, dense sign)"}[a.sketch]
     if proj_ms >= apply_ms:
         ach = proj_flops / (proj_ms * 1e-3) / 1e12
         roof = {"kernel": "k_gemm_tc (B = Q^T A, %d BF16 passes)" % a.final_passes,
@@ -769,10 +785,10 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
     else:
         ach = apply_bytes / (apply_ms * 1e-3) / 1e9
-        default_size = (m, n, r1, a.s) == (65536, 16384, 2000, 8)
         roof = {"kernel": apply_kernel, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
                 "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": NCU_TRAFFIC["k_sketch_apply"] if default_size and a.sketch == "sparse" else None,
+                "traffic": ncu_traffic(apply_kernel, m, n, r1),
+                "algorithmic_bytes": apply_bytes,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
     sketch_roof = {"achieved_gbs": apply_bytes / (apply_ms * 1e-3) / 1e9 if apply_ms else None,
                    "frac": (apply_bytes / (apply_ms * 1e-3) / 1e9) / hbm_peak if apply_ms else None}

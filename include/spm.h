@@ -16,10 +16,12 @@
  *   - Dense matrices are row-major: element (i, j) of a matrix with leading
  *     dimension ld sits at ptr[i * ld + j]; ld >= number of columns.
  *   - Matrix pointers are DEVICE pointers unless a parameter says "host".  The
- *     caller owns every input and output buffer.  The library allocates its
- *     own workspace stream-ordered (cudaMallocAsync on the given stream) and
- *     frees it before the call returns (or in spm_sketch_destroy for sketch
- *     tables).
+ *     caller owns every input and output buffer.  The library takes its
+ *     workspace stream-ordered (cudaMallocFromPoolAsync on the given stream)
+ *     from a memory pool of its own, one per device, and releases it to that
+ *     pool in stream order before the call returns; the pool keeps the freed
+ *     memory for later calls until spm_trim_memory.  Sketch tables live until
+ *     spm_sketch_destroy.
  *   - Every call is stream-ordered on `stream` (a cudaStream_t; NULL = legacy
  *     default stream).  A call returns after its kernels are enqueued; it
  *     synchronises only when an `info` pointer is passed (it then reads the
@@ -102,7 +104,9 @@ typedef struct spm_opts {
 
 typedef struct spm_info {
   /* inputs */
-  int32_t want_timing;  /* 1: record CUDA events around stages (forces a final sync)       */
+  int32_t want_timing;  /* 1: record CUDA events around stages (forces a final sync); 2: the
+                           same, and skip the |A|_F sum (fro_a and resid_est are then -1),
+                           so that the stages run exactly as in a call without info      */
   int32_t eig_sweeps;   /* output: Jacobi sweeps used by the core eigensolver (rsvd)       */
   /* outputs (written when info != NULL; the call synchronises its stream) */
   int32_t device_status;    /* SPM_OK or the first device-side error code                */
@@ -170,6 +174,54 @@ int spm_sketch_shape(const spm_sketch* S, int64_t* n, int64_t* r1, int32_t* s, i
  *   column in ascending order; bucket_signs[n*s] int8. */
 int spm_sketch_tables(const spm_sketch* S, int32_t* cols, int8_t* signs, int64_t* bucket_ptr,
                       int32_t* bucket_rows, int8_t* bucket_signs, void* stream);
+
+/* ---- a3 plan: the scheduled sketch product ------------------------------------
+ * For an FP32 A whose rows fit whole in one SM's shared memory (n <= 18656 with
+ * a three-row ring, n <= 28000 with two; n and lda multiples of 4; A 16-byte
+ * aligned), A S (Algorithm 1 line 1, with S of Lemma 3.2 item 2) runs a kernel
+ * that gives each output column to one lane and reads, at every step, 32 row
+ * elements from 32 distinct shared-memory banks.  Which element each lane
+ * reads at which step is planned once per sketch on the host (about 0.1 s for a
+ * 16384 x 2000 sketch), at the first such product that is not being captured
+ * into a CUDA graph and, unless spm_sketch_set_plan asks otherwise, whose A has
+ * at least 2^24 elements; planning copies the column buckets to the host and
+ * synchronises that call's stream once.  Until then, or when the sketch does not
+ * fit (for example more than about 90 non-zeros per column of S, or n above the
+ * limits), the products use the general kernels.  Either way the results agree
+ * to rounding (the two sum a column's terms in different orders).
+ * spm_sketch_plan reports the plan: *state = 0 (not planned yet), 1 (ready) or
+ * -1 (does not fit, or planning switched off); *steps_per_row = shared-memory
+ * gather steps (one 32-lane wavefront each) per row of A over all *groups CTAs
+ * that share a row; the n * s non-zeros of S need at least n * s / 32.  Any
+ * pointer may be NULL. */
+int spm_sketch_plan(const spm_sketch* S, int32_t* state, int64_t* steps_per_row, int32_t* groups);
+/* mode 0: this sketch never plans and its products always run the general
+ * kernels (no plan synchronisation is ever taken, and the results match, bit for
+ * bit, those of spm_rsvd_batched, whose internal sketches are set this way);
+ * mode 1: plan at the first eligible product, whatever its size; mode 2 (the
+ * default): plan at the first eligible product over at least 2^24 elements of A.
+ * SPM_EINVAL for mode 0 after the plan is built (it stays in use) or for a bad
+ * mode; SPM_EUNSUPPORTED for mode 1 or 2 on a kind without a scheduled product. */
+int spm_sketch_set_plan(spm_sketch* S, int32_t mode);
+/* The same plan computed on the host for a sparse sign matrix given by its
+ * columns (no GPU needed): column c of S (n x r1) lists its non-zeros as
+ * col_ent[col_ptr[c] .. col_ptr[c+1]), each j | 0x80000000 for a -1 entry,
+ * j < n ascending.  search: moves of the local search (the library uses
+ * 300000).  Outputs (host; any may be NULL except as noted): *groups = G;
+ * *steps_per_row; words[G * 32 * 48 * 32] (per group, warp, register step pair
+ * and lane: two row offsets, the even register step's in bits 0-14 and the odd
+ * one's in bits 17-31; offset = 32 + j for an element, below 32 for the zero pad
+ * of that bank); wsteps[G * 32 * 2] (steps of the + and the -
+ * phase of each warp: the + phase occupies register steps [96 - T+, 96), step t
+ * at 96 - T+ + t; the - phase step t at T- - 1 - t); slots[G * 1024] (staging
+ * slot of each lane's column part, | 0x4000000 if the lane gathers it negated,
+ * -1 for an idle lane; slot c < cw is column c of the group, slot >= cw a second
+ * part); partner[G * cw] (cw = ceil(r1 / G): slot of a column's second part, or
+ * -1).  Returns SPM_OK, SPM_EINVAL on bad arguments, or SPM_EUNSUPPORTED if the
+ * matrix does not fit the kernel. */
+int spm_sched_plan_host(int64_t n, int64_t r1, const int64_t* col_ptr, const uint32_t* col_ent,
+                        int64_t search, int32_t* groups, int64_t* steps_per_row, uint32_t* words,
+                        int32_t* wsteps, int32_t* slots, int32_t* partner);
 
 /* ---- a2: Gaussian start block Omega (Algorithm 1 input, Theorem 2.1) --------
  * out[i*ld + j] = N(0,1) draw for row-major element e = i*cols + j: Box-Muller on
@@ -286,7 +338,9 @@ int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, in
  * multiple of 8, base 16-byte aligned): a_mn = 0 -> stored M x K (K contiguous);
  * a_mn = 1 -> stored K x M.  Same for B with N.  splitk >= 1 splits K; partial
  * sums are reduced in a fixed order (deterministic).
- * Errors: SPM_EINVAL on bad sizes/alignment, SPM_ECUDA without an sm_103 device. */
+ * Errors: SPM_EINVAL on bad sizes/alignment, SPM_ECUDA without an sm_103 device.
+ * The call does not synchronise; a bounded device wait that expires is recorded
+ * in a per-device status word that spm_gemm_bf16_status reads. */
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream);
@@ -311,7 +365,9 @@ typedef struct spm_batch_item {
 /* Runs every item of the host array `items` (count >= 0) on `nstreams` side
  * streams (0 = 16, at most 32) forked from and joined back into `stream`, with
  * no host synchronisation: the whole call may be captured into one CUDA graph.
- * Results equal those of separate spm_rsvd calls with the same arguments.
+ * Results equal those of separate spm_rsvd calls with the same arguments whose
+ * sketches are kept on the general kernels (spm_sketch_set_plan(S, 0)); with
+ * planned sketches they agree to rounding.
  * dev_status (device, count int32, may be NULL) receives each problem's device
  * status (0 or an SPM_E* code); the return value covers host-side checks and
  * launch errors only.  SPM_EINVAL on any invalid item (nothing is launched). */
@@ -372,18 +428,22 @@ int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, d
  * The paper has no counterpart: this entry point exists for callers that may not
  * allocate device memory at all -- a plug-in running inside an engine that owns
  * the whole device pool, or a serving process that reserves its memory once at
- * start-up.  It computes exactly what spm_gemm_bf16 computes (same kernels, same
- * fixed split-K reduction order) but keeps the split-K partial sums in a fixed
- * file-scope device array of SPM_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every
- * GPU which loads the library holds until the process exits; it calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * start-up.  It computes what spm_gemm_bf16 computes, bit for bit (the same
+ * kernels with the same tiles, the same fixed split-K reduction order), but keeps
+ * the split-K partial sums in a fixed file-scope device array of
+ * SPM_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every GPU which loads the library
+ * holds until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  An expired bounded wait is reported through
+ * spm_gemm_bf16_status.
  *   - splitk > 1 needs splitk_effective * M * N <= SPM_NOALLOC_SCRATCH_FLOATS, where
  *     splitk_effective = ceil(ceil(K/64) / ceil(ceil(K/64)/splitk)); larger
  *     requests return SPM_EINVAL before anything is launched.  splitk = 1 uses no
  *     scratch.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture on that device.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing), so no address is cached
+ *     past a cudaDeviceReset.  The first call on a device also loads the
+ *     library's device code there; make it before any stream capture on that
+ *     device.
  *   - All calls share the one array per device and it keeps the last call's
  *     contents (every partial sum is written before it is read, so nothing needs
  *     clearing).  Calls that overlap on the GPU (different streams, or concurrent
@@ -392,6 +452,14 @@ int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, d
 int spm_gemm_bf16_noalloc(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
                           int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb,
                           int32_t b_mn, float* D, int64_t ldd, int32_t splitk, void* stream);
+
+/* Device-side status of spm_gemm_bf16 and spm_gemm_bf16_noalloc on the current
+ * device: synchronises `stream` and returns SPM_OK, or SPM_ETIMEOUT if a bounded
+ * wait inside one of their kernels expired (that product's output is then
+ * incomplete) since the word was last cleared; clear != 0 resets it to SPM_OK
+ * (stream-ordered).  The word is one per device, shared by every stream and
+ * thread; it allocates nothing.  Returns SPM_ECUDA if the device is unusable. */
+int spm_gemm_bf16_status(int32_t clear, void* stream);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libspm.so")
-SOURCES = ["sketch.cu", "gemm_simt.cu", "gemm_tc.cu", "dense.cu", "api.cu", "mlp.cu", "selector.cu", "batched.cu", "chol.cu", "sparse.cu", "sketch_dense.cu"]
+SOURCES = ["sketch.cu", "gemm_simt.cu", "gemm_tc.cu", "dense.cu", "api.cu", "mlp.cu", "selector.cu", "batched.cu", "chol.cu", "sparse.cu", "sketch_dense.cu", "sketch_sched.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]
@@ -22,7 +22,7 @@ def _nvcc():
 def _stale(obj, src):
     if not os.path.exists(obj):
         return True
-    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(HERE, "..", "include", "spm.h"))
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))

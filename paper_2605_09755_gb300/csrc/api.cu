@@ -39,6 +39,7 @@ struct Call {
   const void* omega = nullptr;
   int* status = nullptr;
   double* acc = nullptr;  // [0] = |A|_F^2, [1] = |B|_F^2
+  bool want_fro = false;  // |A|_F is reported (info given): the sketch pass sums squares
   StageTimer timer;
   int cholqr_passes = 0;
   // A fed from the host (spm_rsvd_host): row chunks of feed_rows rows arrive
@@ -120,17 +121,17 @@ static int sm_count() {
 // partials written and read back once).  Whole waves matter for the few
 // large products (1000 x 16384 output tiles: 3.4 waves unsplit, 6.7 at two
 // splits); the partials' traffic for the short-K ones.  sym: only the tiles a
-// symmetric product computes (clusters of two M tiles that reach the upper
+// symmetric product computes (the 128-row tiles that reach the upper
 // triangle) count.
 int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym) {
   const int BN = (N >= 192) ? 256 : 128;
   int64_t tiles = cdiv(M, 128) * cdiv(N, BN);
   if (sym) {
-    const int64_t mt = cdiv(M, 128), cl = mt >= 2 ? 2 : 1;
+    const int64_t mt = cdiv(M, 128);
     tiles = 0;
     for (int64_t j = 0; j < cdiv(N, BN); ++j)
-      for (int64_t c = 0; c < cdiv(mt, cl); ++c)
-        if (c * cl * 128 < (j + 1) * BN) tiles += cl;
+      for (int64_t i = 0; i < mt; ++i)
+        if (i * 128 < (j + 1) * BN) tiles += 1;
   }
   const int64_t kt = cdiv(K, 64);
   const int64_t sms = sm_count();
@@ -154,10 +155,11 @@ int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym) {
 static int tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* Ahi,
                     const __nv_bfloat16* Alo, int64_t lda, bool a_mn, const __nv_bfloat16* Bhi,
                     const __nv_bfloat16* Blo, int64_t ldb, bool b_mn, int npass, float* D,
-                    int64_t d_rs, int64_t d_cs, cudaStream_t st, bool sym = false) {
+                    int64_t d_rs, int64_t d_cs, cudaStream_t st, int* status, bool sym = false) {
   TcOp A[3] = {{Ahi, lda, a_mn}, {Ahi, lda, a_mn}, {Alo, lda, a_mn}};
   TcOp B[3] = {{Bhi, ldb, b_mn}, {Blo, ldb, b_mn}, {Bhi, ldb, b_mn}};
-  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K, sym), st, sym);
+  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K, sym), st, sym,
+                 status);
 }
 
 // ------------------------------------------------------------------ CholeskyQR
@@ -238,7 +240,7 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
     SPM_TRY(split_bf16(m, c, rowmajor(Y, DT_F32, ldy), mrowmajor(Qhi, DT_BF16, cp),
                        mrowmajor(Qlo, DT_BF16, cp), C.st));
     // G = Y^T Y: A-op Y^T (M = c, K = m) and B-op (N = c, K = m) both MN-major
-    SPM_TRY(tc_split(c, c, m, Qhi, Qlo, cp, true, Qhi, Qlo, cp, true, 3, G, c, 1, C.st, true));
+    SPM_TRY(tc_split(c, c, m, Qhi, Qlo, cp, true, Qhi, Qlo, cp, true, 3, G, c, 1, C.st, C.status, true));
     if (sdt == DT_F64)
       SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F64, c), C.st));
     else
@@ -249,7 +251,7 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
     // (n, k) = Linv[n][k], i.e. Linv row-major is K-major.
     SPM_TRY(split_bf16(c, c, rowmajor(Li, sdt, c), mrowmajor(Lhi, DT_BF16, cp),
                        mrowmajor(Llo, DT_BF16, cp), C.st));
-    SPM_TRY(tc_split(m, c, c, Qhi, Qlo, cp, false, Lhi, Llo, cp, false, 3, Y, ldy, 1, C.st));
+    SPM_TRY(tc_split(m, c, c, Qhi, Qlo, cp, false, Lhi, Llo, cp, false, 3, Y, ldy, 1, C.st, C.status));
     SPM_TRY(fill_deflated(m, c, Y, ldy, DT_F32, defl, 0x5EED0200u + ps, C.st));
     C.cholqr_passes++;
   }
@@ -263,14 +265,14 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
 // (1,3) (2,2) (3,1) in a second one added on.  T: scratch of M x N floats.
 static int tc_six(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* const* X, int64_t ldx,
                   bool x_mn, const __nv_bfloat16* const* Y, int64_t ldy, bool y_mn, float* D,
-                  int64_t ldd, bool sym, float* T, cudaStream_t st) {
+                  int64_t ldd, bool sym, float* T, cudaStream_t st, int* status) {
   const int sk = auto_splitk(M, N, K, sym);
   TcOp a1[3] = {{X[0], ldx, x_mn}, {X[0], ldx, x_mn}, {X[1], ldx, x_mn}};
   TcOp b1[3] = {{Y[0], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
   TcOp a2[3] = {{X[0], ldx, x_mn}, {X[1], ldx, x_mn}, {X[2], ldx, x_mn}};
   TcOp b2[3] = {{Y[2], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
-  SPM_TRY(gemm_tc(M, N, K, 3, a1, b1, 1.0f, D, ldd, 1, sk, st, sym));
-  SPM_TRY(gemm_tc(M, N, K, 3, a2, b2, 1.0f, T, N, 1, sk, st, sym));
+  SPM_TRY(gemm_tc(M, N, K, 3, a1, b1, 1.0f, D, ldd, 1, sk, st, sym, status));
+  SPM_TRY(gemm_tc(M, N, K, 3, a2, b2, 1.0f, T, N, 1, sk, st, sym, status));
   return add2d_f32(M, N, D, ldd, T, N, st);
 }
 
@@ -301,7 +303,7 @@ static int orth_mixed6(Call& C, float* X, int64_t rows, int64_t c, int64_t ldx,
   for (int ps = 0; ps < passes; ++ps) {
     SPM_TRY(split3_bf16(rows, c, X, DT_F32, ldx, Xhi, Xlo, X3, cp, C.st));
     // G = X^T X: both operands X^T (M = N = c, K = rows), MN-major
-    SPM_TRY(tc_six(c, c, rows, xs, cp, true, xs, cp, true, G, c, true, T, C.st));
+    SPM_TRY(tc_six(c, c, rows, xs, cp, true, xs, cp, true, G, c, true, T, C.st, C.status));
     if (sdt == DT_F64)
       SPM_TRY(convert2d(c, c, rowmajor(G, DT_F32, c), mrowmajor(Gs, DT_F64, c), C.st));
     else
@@ -310,7 +312,7 @@ static int orth_mixed6(Call& C, float* X, int64_t rows, int64_t c, int64_t ldx,
     SPM_TRY(cholesky_inv(c, Gs, c, Li, c, sdt, defl, C.status, C.st));
     // X <- X L^{-T}: A-op X (M = rows, K = c) K-major; B-op L^{-1} row-major (K-major)
     SPM_TRY(split3_bf16(c, c, Li, sdt, c, L1, L2, L3, cp, C.st));
-    SPM_TRY(tc_six(rows, c, c, xs, cp, false, ls, cp, false, X, ldx, false, T, C.st));
+    SPM_TRY(tc_six(rows, c, c, xs, cp, false, ls, cp, false, X, ldx, false, T, C.st, C.status));
     SPM_TRY(fill_deflated(rows, c, X, ldx, DT_F32, defl, 0x5EED0400u + ps, C.st));
     C.cholqr_passes++;
   }
@@ -363,7 +365,8 @@ static int range_finder_simt(Call& C, const spm_sketch* S, const void* A, int64_
     if (C.at_pre)
       SPM_TRY(convert2d(m, r1, rowmajor(C.at_pre, C.adt, C.at_pre_ld), mrowmajor(At, dt, r1), C.st));
     else
-      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, dt, r1, C.acc, C.st));
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, dt, r1, C.want_fro ? C.acc : nullptr, C.st,
+                               nullptr, C.status));
   }
   {
     StageScope sc(C.timer, SPM_STAGE_POWER);
@@ -447,18 +450,19 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
         const int64_t r0 = (int64_t)c * C.feed_rows, rows = min64(C.feed_rows, m - r0);
         SPM_CUDA_TRY(cudaStreamWaitEvent(C.st, C.feed_ev[c], 0));
         SPM_TRY(sketch_apply_dev(S, (const unsigned char*)A + (size_t)r0 * lda * es, C.adt, rows,
-                                 lda, At + r0 * r1p, DT_BF16, r1p, C.acc, C.st,
-                                 Atlo ? Atlo + r0 * r1p : nullptr));
+                                 lda, At + r0 * r1p, DT_BF16, r1p, C.want_fro ? C.acc : nullptr,
+                                 C.st, Atlo ? Atlo + r0 * r1p : nullptr, C.status));
       }
     } else {
-      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.acc, C.st, Atlo));
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.want_fro ? C.acc : nullptr,
+                               C.st, Atlo, C.status));
     }
   }
   const __nv_bfloat16* Alo = Atlo ? Atlo : At;
   {
     // Y = A~ Omega: A-op A~ (M = m, K = r1) K-major; B-op Omega (N = r2, K = r1) MN-major
     StageScope sc(C.timer, SPM_STAGE_POWER);
-    SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
+    SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st, C.status));
   }
   for (int t = 0; t < q; ++t) {
     if (C.reorth_y) {
@@ -474,7 +478,7 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
       if (!C.reorth_y)
         SPM_TRY(split_bf16(m, r2, rowmajor(Y, DT_F32, r2), mrowmajor(Qhi, DT_BF16, r2p),
                            mrowmajor(Qlo, DT_BF16, r2p), C.st));
-      SPM_TRY(tc_split(r1, r2, m, At, Alo, r1p, true, Qhi, Qlo, r2p, true, pp, Z, r2, 1, C.st));
+      SPM_TRY(tc_split(r1, r2, m, At, Alo, r1p, true, Qhi, Qlo, r2p, true, pp, Z, r2, 1, C.st, C.status));
     }
     if (C.reorth) {
       // Z <- orth(Z) on tensor cores with FP32-equivalent products (shifted
@@ -489,7 +493,7 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
       if (!C.reorth)
         SPM_TRY(split_bf16(r1, r2, rowmajor(Z, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
                            mrowmajor(Zlo, DT_BF16, r2p), C.st));
-      SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st));
+      SPM_TRY(tc_split(m, r2, r1, At, Alo, r1p, false, Zhi, Zlo, r2p, true, pp, Y, r2, 1, C.st, C.status));
     }
   }
   {
@@ -531,6 +535,7 @@ static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info
     C.omega = o->omega;
   }
   if (info && info->want_timing) C.timer.on = true;
+  C.want_fro = info != nullptr && info->want_timing != 2;
 }
 
 static int prepare(Call& C) {
@@ -557,8 +562,9 @@ static int finish(Call& C, spm_info* info, int rc, bool has_b) {
   info->device_status = dst;
   info->eig_sweeps = stw[1];
   info->cholqr_passes = C.cholqr_passes;
-  info->fro_a = C.no_fro ? -1.0 : sqrt(acc[0]);
-  info->resid_est = (has_b && !C.no_fro) ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
+  const bool fro = !C.no_fro && C.want_fro;
+  info->fro_a = fro ? sqrt(acc[0]) : -1.0;
+  info->resid_est = (has_b && fro) ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
   return dst == 0 ? SPM_OK : dst;
 }
 
@@ -671,7 +677,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
                          mrowmajor(Alo, DT_BF16, np_), C.st));
       // B = Q^T A: A-op Q^T (M = r2, K = m) MN-major; B-op A (N = n, K = m) MN-major
       SPM_TRY(tc_split(r2, n, m, rf.Qhi, rf.Qlo, r2p, true, Ahi, Alo, np_, true, C.final_passes,
-                       B, n, 1, C.st));
+                       B, n, 1, C.st, C.status));
     }
   }
   {
@@ -680,7 +686,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     SPM_TRY(split_bf16(r2, n, rowmajor(B, DT_F32, n), mrowmajor(Bhi, DT_BF16, np_),
                        mrowmajor(Blo, DT_BF16, np_), C.st));
     // G = B B^T: both operands B (r2 x n), K-major
-    SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st, true));
+    SPM_TRY(tc_split(r2, r2, n, Bhi, Blo, np_, false, Bhi, Blo, np_, false, 3, G, r2, 1, C.st, C.status, true));
     SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Gs, sdt, r2), C.st));
     SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
     SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st, C.status + 1));
@@ -690,7 +696,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
   {
     StageScope sc(C.timer, SPM_STAGE_FINISH);
     // W = U~^T B: A-op U~^T (M = r2, K = r2) MN-major; B-op B (N = n, K = r2) MN-major
-    SPM_TRY(tc_split(r2, n, r2, Uhi, Ulo, r2p, true, Bhi, Blo, np_, true, 3, W, n, 1, C.st));
+    SPM_TRY(tc_split(r2, n, r2, Uhi, Ulo, r2p, true, Bhi, Blo, np_, true, 3, W, n, 1, C.st, C.status));
     SPM_TRY(norms(r2, n, rowmajor(W, DT_F32, n), false, sig, C.st));
     // sigma_i = |row i of W|, ordered by the eigenvalues; order them by their
     // own values (the two can swap neighbours that agree to rounding)
@@ -702,7 +708,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
                          false, C.st));
     SPM_TRY(scale_lines(k, n, mrowmajor(Wk, DT_F32, n), true, sigs, true, C.st));
     // U = Q U~[:, :k]: A-op Q (M = m, K = r2) K-major; B-op U~ (N = k, K = r2) MN-major
-    SPM_TRY(tc_split(m, k, r2, rf.Qhi, rf.Qlo, r2p, false, Ukhi, Uklo, kp, true, 3, Uo, k, 1, C.st));
+    SPM_TRY(tc_split(m, k, r2, rf.Qhi, rf.Qlo, r2p, false, Ukhi, Uklo, kp, true, 3, Uo, k, 1, C.st, C.status));
     SPM_TRY(sign_fix(m, k, n, mrowmajor(Uo, DT_F32, k), mrowmajor(Wk, DT_F32, n), C.st));
     SPM_TRY(store_out(m, k, rowmajor(Uo, DT_F32, k), U, edt, ldu, C.st));
     SPM_TRY(store_out(k, n, rowmajor(Wk, DT_F32, n), Vt, edt, ldvt, C.st));
@@ -776,7 +782,9 @@ int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* co
     b[q] = TcOp{(const __nv_bfloat16*)B[q], ldb, b_mn != 0};
   }
   if (lda < (a_mn ? M : K) || ldb < (b_mn ? N : K)) return SPM_EINVAL;
-  return gemm_tc(M, N, K, npass, a, b, 1.0f, D, ldd, 1, splitk, as_stream(stream));
+  int* status = nullptr;
+  SPM_TRY(gemm_public_status(&status));
+  return gemm_tc(M, N, K, npass, a, b, 1.0f, D, ldd, 1, splitk, as_stream(stream), false, status);
 }
 
 int spm_range_finder(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64_t lda,

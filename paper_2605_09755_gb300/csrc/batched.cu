@@ -105,6 +105,9 @@ extern "C" int spm_rsvd_batched(int32_t count, const spm_batch_item* items, int3
     if (f == sketches.end()) {
       spm_sketch* S = nullptr;
       rc = spm_sketch_create(&S, it.n, it.r1, it.s, it.seed, SPM_SKETCH_SPARSE_SIGN, st);
+      // no plan (it would synchronise a stream): the batch runs the general
+      // sketch kernels, the same whether it is captured or not
+      if (rc == SPM_OK) rc = spm_sketch_set_plan(S, 0);
       if (rc == SPM_OK) sketches[key] = of[i] = S;
     } else {
       of[i] = f->second;

@@ -211,4 +211,16 @@ struct spm_sketch {
   uint32_t* dbits;        // SRHT: D as bits (1 = minus), max(1, n'/32) words
   int32_t* hcols;         // SRHT: the r1 sampled Hadamard columns, in draw order
   int32_t hl;             // SRHT: log2 n'
+  // Scheduled A S for FP32 rows held whole in shared memory (sketch_sched.cu),
+  // planned on the host at the first eligible call: 0 = not planned yet,
+  // 1 = ready, -1 = this sketch does not fit the kernel.
+  int32_t sched_state;
+  int32_t sched_groups;   // column groups G (CTAs per row)
+  int32_t sched_cw;       // columns per group
+  int64_t sched_steps;    // shared-memory gather steps per row, all groups together
+  uint32_t* sched_words;  // G x 32 warps x (SCHED_TT / 2) words x 32 lanes: two 16-bit row offsets each
+  int2* sched_wsteps;     // G x 32: steps of the + and the - phase of each warp
+  int32_t* sched_slot;    // G x 1024: staging slot of each lane's column part (-1: idle)
+  int32_t* sched_partner; // G x cw: staging slot of a column's second part (-1: none)
+  void* sched_mu;         // std::mutex guarding the lazy planning
 };

@@ -44,7 +44,7 @@ struct TcParams {
   float* D;
   int64_t d_rs, d_cs, split_stride;
   int* status;
-  int sym_upper;  // skip clusters whose tiles lie entirely below the diagonal
+  int sym_upper;  // skip output tiles that lie entirely below the diagonal
   int fused3;     // split product A0 B0 + A0 B1 + A2 B0 (A1 = A0, B2 = B0): each k-tile
                   // takes two ring stages, (A0, B0) and (A2, B1), and all three MMAs
 };
@@ -92,22 +92,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// The same load into the same shared-memory offset of every CTA in `mask` of
-// the cluster; each destination's barrier at `bar` receives the bytes.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
 // byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
 // value 1 in bits 46-48, swizzle mode 2 (128-byte) in bits 61-63.
@@ -149,15 +133,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
-// arrive (when the MMAs complete) on the barrier at `bar` of every CTA in mask
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(bar),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -172,10 +147,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// CL = 2: the two CTAs of a cluster take neighbouring M tiles of the same N
-// tile; each loads half of the shared B tile and multicasts it to both, and
-// a stage is refilled only after both CTAs' MMAs have released it.
-template <int BN, bool A_MN, bool B_MN, int CL>
+// One CTA per 128 x BN output tile (and K split); every operand tile is
+// fetched by this CTA's own TMA loads from this GPU's memory.
+template <int BN, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
               const __grid_constant__ CUtensorMap ta2, const __grid_constant__ CUtensorMap tb0,
@@ -197,25 +171,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM;
   const int n0 = blockIdx.y * BN;
-  // symmetric output: a whole cluster below the diagonal leaves before it
-  // touches any barrier (the decision is the same for all its CTAs)
-  if (p.sym_upper && (int)(blockIdx.x / CL) * CL * TC_BM >= n0 + BN) return;
+  // symmetric output: a tile entirely below the diagonal leaves before it
+  // touches any barrier
+  if (p.sym_upper && (int)blockIdx.x * TC_BM >= n0 + BN) return;
   const int kt0 = blockIdx.z * p.kt_per_split;
   const int kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
   const int per_kt = p.fused3 ? 2 : p.npass;  // ring stages per k-tile
   const int iters = (kt1 - kt0) * per_kt;
   static_assert(STAGES % 2 == 0, "a fused k-tile's two stages must not wrap");
 
-  uint32_t crank = 0;
-  if (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
-  constexpr uint16_t cmask = (uint16_t)((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL);
+      mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // barrier inits visible to the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
@@ -228,7 +199,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (CL > 1) cluster_sync_all();  // peers' barriers exist before any multicast reaches them
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0) {
@@ -260,22 +230,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[qa], m0 + 64 * b, k0, fb);
         }
-        if (CL == 1) {
-          if (!B_MN) {
-            tma_load_2d(sb, tb[qb], k0, n0, fb);
-          } else {
-#pragma unroll
-            for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb);
-          }
+        if (!B_MN) {
+          tma_load_2d(sb, tb[qb], k0, n0, fb);
         } else {
-          if (!B_MN) {
-            constexpr int HB = BN / CL;  // rows of the B tile this CTA fetches
-            tma_load_2d_mc(sb + crank * HB * 128, tb[qb], k0, n0 + (int)crank * HB, fb, cmask);
-          } else {
 #pragma unroll
-            for (int b = 0; b < BN / 64; ++b)
-              if (b % CL == (int)crank) tma_load_2d_mc(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb, cmask);
-          }
+          for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb);
         }
         issued = it + 1;
       }
@@ -316,13 +275,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int kk = 0; kk < TC_BK / 16; ++kk)
             tc_mma(tmem, desc_a(sa, kk), desc_b(sb, kk), idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
         }
-        if (CL == 1) {
-          tc_commit(empty0 + 8 * s0);
-          tc_commit(empty0 + 8 * s1);
-        } else {
-          tc_commit_mc(empty0 + 8 * s0, cmask);
-          tc_commit_mc(empty0 + 8 * s1, cmask);
-        }
+        tc_commit(empty0 + 8 * s0);
+        tc_commit(empty0 + 8 * s1);
       }
       for (int it = 0; !p.fused3 && it < iters; ++it) {
         const int s = it % STAGES;
@@ -347,10 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bd = smem_desc(sb + kk * 2048, 8192, 1024);
           tc_mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
         }
-        if (CL == 1)
-          tc_commit(empty0 + 8 * s);
-        else
-          tc_commit_mc(empty0 + 8 * s, cmask);
+        tc_commit(empty0 + 8 * s);
       }
       tc_commit(done);  // fires once every MMA above has completed
       (void)ok;
@@ -400,11 +351,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   // the MMA thread's final commit must have fired before the columns go back
-  // and (in a cluster) before the peer may exit: every arrival this CTA's MMAs
-  // make on the peer's barriers precedes it
   if (warp == 1 && lane == 0) mbar_wait(done, 0, p.status);
   __syncthreads();
-  if (CL > 1) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -481,40 +429,24 @@ static int make_map(CUtensorMap* map, const TcOp& op, int64_t rows_mn, int64_t k
   return r == CUDA_SUCCESS ? SPM_OK : SPM_EINVAL;
 }
 
-template <int BN, bool A_MN, bool B_MN, int CL>
+template <int BN, bool A_MN, bool B_MN>
 static int launch_tc(const CUtensorMap* ta, const CUtensorMap* tb, const TcParams& p, dim3 grid,
                      cudaStream_t st) {
-  auto kern = k_gemm_tc<BN, A_MN, B_MN, CL>;
+  auto kern = k_gemm_tc<BN, A_MN, B_MN>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcCfg<BN>::SMEM));
-  if (CL == 1) {
-    kern<<<grid, TC_THREADS, TcCfg<BN>::SMEM, st>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(TC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = TcCfg<BN>::SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SPM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p));
-  }
+  kern<<<grid, TC_THREADS, TcCfg<BN>::SMEM, st>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], p);
   SPM_LAUNCH_CHECK();
   return SPM_OK;
 }
 
-template <int BN, int CL>
+template <int BN>
 static int launch_bn(bool amn, bool bmn, const CUtensorMap* ta, const CUtensorMap* tb,
                      const TcParams& p, dim3 grid, cudaStream_t st) {
-  if (!amn && !bmn) return launch_tc<BN, false, false, CL>(ta, tb, p, grid, st);
-  if (!amn && bmn) return launch_tc<BN, false, true, CL>(ta, tb, p, grid, st);
-  if (amn && !bmn) return launch_tc<BN, true, false, CL>(ta, tb, p, grid, st);
-  return launch_tc<BN, true, true, CL>(ta, tb, p, grid, st);
+  if (!amn && !bmn) return launch_tc<BN, false, false>(ta, tb, p, grid, st);
+  if (!amn && bmn) return launch_tc<BN, false, true>(ta, tb, p, grid, st);
+  if (amn && !bmn) return launch_tc<BN, true, false>(ta, tb, p, grid, st);
+  return launch_tc<BN, true, true>(ta, tb, p, grid, st);
 }
 
 // The split pattern A0 B0 + A0 B1 + A2 B0 (A1 = A0, B2 = B0): four distinct
@@ -534,7 +466,8 @@ __global__ void k_mirror_upper(int n, float* __restrict__ D, int64_t d_rs, int64
 }
 
 int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
-            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st, bool sym_upper) {
+            float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st, bool sym_upper,
+            int* status) {
   if (sym_upper && M != N) return SPM_EINVAL;
   if (M <= 0 || N <= 0) return SPM_OK;
   if (npass < 1 || npass > 3) return SPM_EINVAL;
@@ -548,19 +481,18 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   for (int q = 0; q < npass; ++q)
     if (A[q].mn_major != A[0].mn_major || B[q].mn_major != B[0].mn_major) return SPM_EINVAL;
   const int BN = (N >= 192) ? 256 : 128;
-  const int CL = (cdiv(M, TC_BM) >= 2) ? 2 : 1;  // pairs of M tiles share their B tile
   CUtensorMap ta[3], tb[3];
   for (int q = 0; q < 3; ++q) {
     const int qq = q < npass ? q : 0;
     SPM_TRY(make_map(&ta[q], A[qq], M, K, TC_BM));
-    SPM_TRY(make_map(&tb[q], B[qq], N, K, BN / CL));
+    SPM_TRY(make_map(&tb[q], B[qq], N, K, BN));
   }
   const int k_tiles = (int)cdiv(K, TC_BK);
   if (splitk < 1) splitk = 1;
   if (splitk > k_tiles) splitk = k_tiles;
   const int kt_per = (int)cdiv(k_tiles, splitk);
   splitk = (int)cdiv(k_tiles, kt_per);
-  const int64_t mt = round_up(cdiv(M, TC_BM), CL), nt = cdiv(N, BN);
+  const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
   if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
   TcParams p{};
   p.M = (int)M;
@@ -570,7 +502,7 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   p.kt_per_split = kt_per;
   p.npass = npass;
   p.alpha = alpha;
-  p.status = nullptr;
+  p.status = status;
   p.sym_upper = sym_upper ? 1 : 0;
   p.fused3 = fused_split(npass, A, B);
   dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
@@ -587,14 +519,10 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
     p.d_cs = 1;
     p.split_stride = M * N;
   }
-  if (BN == 256 && CL == 2)
-    SPM_TRY((launch_bn<256, 2>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
-  else if (BN == 256)
-    SPM_TRY((launch_bn<256, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
-  else if (CL == 2)
-    SPM_TRY((launch_bn<128, 2>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+  if (BN == 256)
+    SPM_TRY((launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   else
-    SPM_TRY((launch_bn<128, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+    SPM_TRY((launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
     const int64_t total = M * N;
     const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
@@ -618,28 +546,30 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
 // file-scope device array instead of stream-ordered workspace.  The array lives
 // on every GPU that loads the library until the process exits.  In host code
 // its name is only a host-side stand-in, never a device address: the device
-// address is looked up with cudaGetSymbolAddress, once per device.
+// address is looked up with cudaGetSymbolAddress (which allocates nothing) on
+// every call, so a cached address can never outlive the context it came from.
 static constexpr int64_t kNoAllocScratchFloats = (int64_t)SPM_NOALLOC_SCRATCH_FLOATS;
 static __device__ __align__(256) float g_noalloc_scratch[SPM_NOALLOC_SCRATCH_FLOATS];
+// First device-side status (0 or SPM_ETIMEOUT) of the public product entry
+// points on this device since it was last cleared (spm_gemm_bf16_status).
+static __device__ int g_gemm_status;
 
-namespace {
-std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[128] = {};
-}  // namespace
-
-// Device address of the scratch array on the current device (set-up on first use).
-static int noalloc_scratch(float** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return SPM_ECUDA;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
+// Device addresses of the scratch array and of the status word on the current device.
+static int gemm_symbols(float** scratch, int** status) {
+  void* p = nullptr;
+  if (scratch) {
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPM_ECUDA;
-    g_noalloc_ptr[dev] = reinterpret_cast<float*>(p);
+    *scratch = reinterpret_cast<float*>(p);
   }
-  *out = g_noalloc_ptr[dev];
+  if (status) {
+    p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_gemm_status) != cudaSuccess || !p) return SPM_ECUDA;
+    *status = reinterpret_cast<int*>(p);
+  }
   return SPM_OK;
 }
+
+int gemm_public_status(int** status) { return gemm_symbols(nullptr, status); }
 
 int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B,
                     float* D, int64_t ldd, int splitk, cudaStream_t st) {
@@ -658,7 +588,8 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
   if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
   float* scratch = nullptr;
-  SPM_TRY(noalloc_scratch(&scratch));
+  int* status = nullptr;
+  SPM_TRY(gemm_symbols(&scratch, &status));
   CUtensorMap ta[3], tb[3];
   for (int q = 0; q < 3; ++q) {
     const int qq = q < npass ? q : 0;
@@ -673,7 +604,7 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   p.kt_per_split = kt_per;
   p.npass = npass;
   p.alpha = 1.0f;
-  p.status = nullptr;
+  p.status = status;
   p.fused3 = fused_split(npass, A, B);
   if (splitk == 1) {
     p.D = D;
@@ -690,9 +621,9 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   }
   dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
   if (BN == 256)
-    SPM_TRY((launch_bn<256, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+    SPM_TRY((launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   else
-    SPM_TRY((launch_bn<128, 1>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
+    SPM_TRY((launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
     const int64_t total = M * N;
     const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
@@ -720,4 +651,16 @@ extern "C" int spm_gemm_bf16_noalloc(int64_t M, int64_t N, int64_t K, int32_t np
     b[q] = TcOp{(const __nv_bfloat16*)B[q], ldb, b_mn != 0};
   }
   return gemm_tc_noalloc(M, N, K, npass, a, b, D, ldd, splitk, as_stream(stream));
+}
+
+extern "C" int spm_gemm_bf16_status(int32_t clear, void* stream) {
+  using namespace spm;
+  int* status = nullptr;
+  SPM_TRY(gemm_symbols(nullptr, &status));
+  cudaStream_t st = as_stream(stream);
+  int h = 0;
+  SPM_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (clear) SPM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  SPM_CUDA_TRY(cudaStreamSynchronize(st));
+  return h;
 }

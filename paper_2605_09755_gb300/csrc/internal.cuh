@@ -30,9 +30,22 @@ inline View cview(MView v) { return View{v.p, v.dt, v.rs, v.cs}; }
 // out (m x r1) = A (m x n) S ; out_dt in {F32, F64, BF16}; accumulates |A|_F^2
 // into *fro2 (device double) when fro2 != nullptr.
 // out_lo (BF16 outputs only): second half of a hi/lo split, out_lo = bf16(v - hi).
+// status (device int, may be null): device-side errors (an expired bounded wait).
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
                      void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
-                     void* out_lo = nullptr);
+                     void* out_lo = nullptr, int* status = nullptr);
+
+// ---------------------------------------------------------------- sketch_sched.cu
+// A S for FP32 A (n and lda multiples of 4, A 16-byte aligned, rows that fit
+// whole in shared memory) by the scheduled kernel, into FP32 or BF16 (hi, and
+// lo when out_lo is set) outputs; fro2 (may be null) accumulates |A|_F^2.
+// Plans the sketch on first use (not during stream capture).  Returns
+// SPM_EUNSUPPORTED, with nothing launched, when the request or the sketch does
+// not fit the kernel.
+int sched_apply(spm_sketch* S, const float* A, int64_t m, int64_t lda, void* out, int out_dt,
+                int64_t ldo, double* fro2, int* status, cudaStream_t st, void* out_lo);
+void sched_init(spm_sketch* S);
+void sched_free(spm_sketch* S);
 // out (r1 x p) = S^T X, X (n x p, row stride ldx)
 int sketch_apply_t_dev(const spm_sketch* S, const void* X, int x_dt, int64_t p, int64_t ldx,
                        void* out, int out_dt, int64_t ldo, cudaStream_t st);
@@ -96,9 +109,13 @@ struct TcOp {
 // sym_upper (M == N, the product symmetric by construction, e.g. a Gram
 // matrix): only the output tiles that meet the upper triangle are computed and
 // the strictly lower triangle is then copied from the upper one.
+// status (device int, may be null): an expired bounded wait records SPM_ETIMEOUT there.
 int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B, float alpha,
             float* D, int64_t d_rs, int64_t d_cs, int splitk, cudaStream_t st,
-            bool sym_upper = false);
+            bool sym_upper = false, int* status = nullptr);
+// Device address of the status word that the public product entry points
+// (spm_gemm_bf16, spm_gemm_bf16_noalloc) record into on the current device.
+int gemm_public_status(int** status);
 bool tc_available();
 // split-K factor of a tensor-core product (a wave and traffic cost model; api.cu)
 int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym = false);

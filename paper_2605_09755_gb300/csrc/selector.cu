@@ -134,7 +134,8 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
   const int64_t r1p = (4 * k < n) ? 4 * k : n;
   spm_sketch* P = nullptr;
   SPM_TRY(spm_sketch_create(&P, n, r1p, (int32_t)(s < r1p ? s : r1p), seed, SPM_SKETCH_SPARSE_SIGN, st));
-  int rc = SPM_OK;
+  // the probe is used once, by the general kernels, as in the batched selector
+  int rc = spm_sketch_set_plan(P, 0);
   float pred[SPM_MLP_OUT];
   {
     Arena ar(st);
@@ -201,6 +202,7 @@ int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, d
       spm_sketch* P = nullptr;
       rc = spm_sketch_create(&P, it.n, r1p, (int32_t)std::min<int64_t>(8, r1p), it.seed,
                              SPM_SKETCH_SPARSE_SIGN, st);
+      if (rc == SPM_OK) rc = spm_sketch_set_plan(P, 0);  // no plan: no synchronisation
       if (rc == SPM_OK) probes[key] = of[i] = P;
     } else {
       of[i] = f->second;

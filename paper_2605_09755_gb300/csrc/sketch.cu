@@ -713,9 +713,16 @@ static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda
 
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
                      void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
-                     void* out_lo) {
+                     void* out_lo, int* status) {
   if (m <= 0) return SPM_OK;
   if (dense_kind(S)) return dense_sketch_apply(S, A, a_dt, m, lda, out, out_dt, ldo, fro2, st, out_lo);
+  if (a_dt == DT_F32 && (out_dt == DT_F32 || out_dt == DT_BF16)) {
+    // whole rows in shared memory, conflict-free gather schedule (the plan is
+    // the sketch's own, built on first use)
+    const int rc = sched_apply(const_cast<spm_sketch*>(S), (const float*)A, m, lda, out, out_dt,
+                               ldo, fro2, status, st, out_dt == DT_BF16 ? out_lo : nullptr);
+    if (rc != SPM_EUNSUPPORTED) return rc;
+  }
   if (a_dt == DT_F32) {
     const float* a = (const float*)A;
     if (out_dt == DT_F32) return launch_apply<float, float, float, 32, 2>(S, a, m, lda, (float*)out, ldo, fro2, st);
@@ -848,6 +855,7 @@ int spm_sketch_create(spm_sketch** out, int64_t n, int64_t r1, int32_t s, uint64
         nnz, (int)r1, (int)nch, S->bucket_ptr, S->bucket_ent, S->seg, S->entoff);
     if (cudaGetLastError() != cudaSuccess) return fail(SPM_ECUDA);
   }
+  if (kind == SPM_SKETCH_SPARSE_SIGN) sched_init(S);
   if (kind == SPM_SKETCH_SPARSE_SIGN && s <= SACC_MAX_S && r1 <= 65535) {
     const int64_t ng = cdiv(r1, SACC_MAX_CG);
     S->acc_cg = (int32_t)cdiv(r1, ng);
@@ -870,6 +878,7 @@ int spm_sketch_destroy(spm_sketch* S) {
   if (S->seg) cudaFreeAsync(S->seg, S->stream);
   if (S->entoff) cudaFreeAsync(S->entoff, S->stream);
   if (S->entacc) cudaFreeAsync(S->entacc, S->stream);
+  sched_free(S);
   dense_sketch_free(S);
   delete S;
   return SPM_OK;

@@ -203,8 +203,10 @@ def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False
 
 
 def _info(timing):
+    """timing: False, True (stage times and |A|_F), or 2 (stage times only: the
+    sketch pass then skips the |A|_F sum, as calls without info do)."""
     inf = Info()
-    inf.want_timing = 1 if timing else 0
+    inf.want_timing = 2 if timing == 2 else (1 if timing else 0)
     return inf
 
 
@@ -382,6 +384,59 @@ def gemm_bf16_noalloc(A_list, B_list, M, N, K, D, a_mn=False, b_mn=False, splitk
     _check(fn(M, N, K, npass, Ap, A_list[0].stride(0), int(a_mn), Bp, B_list[0].stride(0),
               int(b_mn), _ptr(D), D.stride(0), int(splitk), _stream()), "spm_gemm_bf16_noalloc")
     return D
+
+
+def sketch_set_plan(S, mode):
+    """spm_sketch_set_plan: 0 (or False) keeps this sketch on the general kernels,
+    1 (or True) plans at its first eligible product, 2 plans only for large products."""
+    fn = _fn("spm_sketch_set_plan", [VP, I32])
+    _check(fn(S.handle, int(mode)), "spm_sketch_set_plan")
+
+
+def sketch_plan(S):
+    """(state, steps_per_row, groups) of the sketch's scheduled product (spm_sketch_plan):
+    state 0 = not planned yet, 1 = ready, -1 = does not fit."""
+    st, steps, g = I32(), I64(), I32()
+    fn = _fn("spm_sketch_plan", [VP, ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I32)])
+    _check(fn(S.handle, ctypes.byref(st), ctypes.byref(steps), ctypes.byref(g)), "spm_sketch_plan")
+    return int(st.value), int(steps.value), int(g.value)
+
+
+SCHED_TT, SCHED_LANES, SCHED_PAD = 96, 1024, 32
+
+
+def sched_plan_host(n, r1, col_ptr, col_ent, search=300000):
+    """Host-side plan of the scheduled product for a sparse sign matrix given by its
+    columns (spm_sched_plan_host; no GPU needed).  col_ptr (r1 + 1, int64) and col_ent
+    (uint32: j | 0x80000000 for a -1 entry) are numpy arrays.  Returns a dict with the
+    group count, steps per row and the per-warp tables, or raises SpmError."""
+    import numpy as np
+    col_ptr = np.ascontiguousarray(col_ptr, dtype=np.int64)
+    col_ent = np.ascontiguousarray(col_ent, dtype=np.uint32)
+    fn = _fn("spm_sched_plan_host", [I64, I64, VP, VP, I64, ctypes.POINTER(I32),
+                                     ctypes.POINTER(I64), VP, VP, VP, VP])
+    g, steps = I32(), I64()
+    _check(fn(n, r1, col_ptr.ctypes.data, col_ent.ctypes.data, search, ctypes.byref(g),
+              ctypes.byref(steps), None, None, None, None), "spm_sched_plan_host")
+    G = int(g.value)
+    cw = -(-r1 // G)
+    words = np.zeros(G * 32 * (SCHED_TT // 2) * 32, dtype=np.uint32)
+    wsteps = np.zeros(G * 32 * 2, dtype=np.int32)
+    slots = np.zeros(G * SCHED_LANES, dtype=np.int32)
+    partner = np.zeros(G * cw, dtype=np.int32)
+    _check(fn(n, r1, col_ptr.ctypes.data, col_ent.ctypes.data, search, ctypes.byref(g),
+              ctypes.byref(steps), words.ctypes.data, wsteps.ctypes.data, slots.ctypes.data,
+              partner.ctypes.data), "spm_sched_plan_host")
+    return {"groups": G, "cw": cw, "steps": int(steps.value),
+            "words": words.reshape(G, 32, SCHED_TT // 2, 32), "wsteps": wsteps.reshape(G, 32, 2),
+            "slots": slots.reshape(G, SCHED_LANES), "partner": partner.reshape(G, cw)}
+
+
+def gemm_bf16_status(clear=True):
+    """Device status of the public product entry points on the current device
+    (spm_gemm_bf16_status): 0, or SPM_ETIMEOUT if one of their bounded waits expired."""
+    fn = _fn("spm_gemm_bf16_status", [I32, VP])
+    return int(fn(int(bool(clear)), _stream()))
 
 
 # ---------------------------------------------------------------- learned selector

@@ -2,9 +2,11 @@
 
 Expected values come from the oracle (FP64 parity, the same bounds as the
 single-problem tests) and from separate single-problem calls of the library,
-which the batched call must reproduce bit for bit: both run the same kernels on
-the same inputs, only on other streams.  Graph capture is checked by replaying a
-captured batch on new matrix contents.
+which the batched call must reproduce bit for bit when their sketches are kept
+on the general kernels as the batch's are (spm_sketch_set_plan(S, 0)): both then
+run the same kernels on the same inputs, only on other streams.  With a planned
+sketch a separate call agrees to rounding.  Graph capture is checked by
+replaying a captured batch on new matrix contents.
 """
 import numpy as np
 import pytest
@@ -49,8 +51,9 @@ def _matrix(spec, dtype):
     return A, sigma, torch.tensor(A, dtype=dtype, device="cuda")
 
 
-def _separate(spm, p, prec):
+def _separate(spm, p, prec, plan=False):
     S = spm.Sketch(p["A"].shape[1], p["r1"], p.get("s", 8), p["seed"])
+    spm.sketch_set_plan(S, 1 if plan else 0)
     U, sg, Vt, _ = spm.rsvd(S, p["A"], p["k"], p["q"], p["k"], omega_seed=p["seed"] + 1,
                             precision=prec)
     S.close()
@@ -88,6 +91,12 @@ def test_batched_mixed_equals_separate_calls(spm):
         ref = _separate(spm, p, spm.PREC_MIXED)
         for g, r in zip(got, ref):
             assert torch.equal(g, r)
+        # a planned sketch (scheduled A S, another summation order): the same to rounding
+        U, sg, Vt = _separate(spm, p, spm.PREC_MIXED, plan=True)
+        assert torch.allclose(sg, got[1], rtol=1e-4, atol=0)
+        res_p = torch.linalg.norm(p["A"] - (U * sg) @ Vt)
+        res_b = torch.linalg.norm(p["A"] - (got[0] * got[1]) @ got[2])
+        assert abs(res_p / res_b - 1) <= 1e-3
 
 
 def test_batched_graph_capture_replay(spm):

@@ -35,16 +35,35 @@ def _operands(M, N, K, seed, a_mn, b_mn):
 @pytest.mark.parametrize("a_mn,b_mn", [(False, False), (True, True)])
 def test_noalloc_matches_allocating_entry_point_twice(spm, a_mn, b_mn):
     M, N, K, splitk = 384, 512, 4096, 4      # 4 * 384 * 512 floats fit the scratch array
+    spm.gemm_bf16_status(clear=True)
     for call, seed in enumerate((11, 12)):
         Am, Bm, A, B = _operands(M, N, K, seed, a_mn, b_mn)
         ref = spm.gemm_bf16([A], [B], M, N, K, a_mn=a_mn, b_mn=b_mn, splitk=splitk)
         D = torch.full((M, N), float("nan"), device="cuda", dtype=torch.float32)
         spm.gemm_bf16_noalloc([A], [B], M, N, K, D, a_mn=a_mn, b_mn=b_mn, splitk=splitk)
         torch.cuda.synchronize()
+        # the same kernels and the same fixed split-K order: equal bit for bit
+        assert torch.equal(D, ref), call
         tol = 1e-4 * (K ** 0.5) * 4
-        assert (D.double() - ref.double()).abs().max().item() <= tol, call
         exact = Am.double() @ Bm.double().T
         assert (D.double() - exact).abs().max().item() <= tol, call
+    assert spm.gemm_bf16_status(clear=True) == 0
+
+
+def test_noalloc_ragged_tail_after_a_larger_call(spm):
+    # a larger split-K call fills more of the shared scratch array first; a
+    # following call with M not a multiple of 128 must not pick up its stale tail
+    Am, Bm, A, B = _operands(1000, 500, 2048, 21, False, False)
+    D = torch.empty(1000, 500, device="cuda", dtype=torch.float32)
+    spm.gemm_bf16_noalloc([A], [B], 1000, 500, 2048, D, splitk=4)
+    for M, N, K, splitk in [(300, 200, 3072, 3), (129, 257, 1000, 2)]:
+        Am, Bm, A, B = _operands(M, N, K, 22 + M, False, False)
+        ref = spm.gemm_bf16([A], [B], M, N, K, splitk=splitk)
+        D = torch.full((M, N), float("nan"), device="cuda", dtype=torch.float32)
+        spm.gemm_bf16_noalloc([A], [B], M, N, K, D, splitk=splitk)
+        torch.cuda.synchronize()
+        assert torch.equal(D, ref), (M, N, K, splitk)
+    assert spm.gemm_bf16_status(clear=True) == 0
 
 
 def test_noalloc_split_precision_and_single_split(spm):
@@ -60,7 +79,9 @@ def test_noalloc_split_precision_and_single_split(spm):
         ref = spm.gemm_bf16([xh, xh, xl], [yh, yl, yh], M, N, K, splitk=splitk)
         D = torch.empty(M, N, device="cuda", dtype=torch.float32)
         spm.gemm_bf16_noalloc([xh, xh, xl], [yh, yl, yh], M, N, K, D, splitk=splitk)
-        assert (D.double() - ref.double()).abs().max().item() <= 1e-4 * (K ** 0.5) * 4
+        torch.cuda.synchronize()
+        assert torch.equal(D, ref), splitk
+        assert (D.double() - X @ Y.T).abs().max().item() <= 1e-4 * (K ** 0.5) * 4
 
 
 def test_noalloc_rejects_requests_beyond_the_scratch_array(spm):

@@ -48,7 +48,8 @@ extern "C" {
 #define SPM_EINVAL 1        /* bad shape, null pointer, ld too small, bad enum   */
 #define SPM_ENOMEM 2        /* stream-ordered workspace allocation failed        */
 #define SPM_ECUDA 3         /* kernel launch / runtime error, or no usable GPU   */
-#define SPM_EBREAKDOWN 4    /* Cholesky breakdown inside CholeskyQR after shift  */
+#define SPM_EBREAKDOWN 4    /* a triangular factor that a solve needs is singular
+                               (the least-squares step of Algorithm 2)            */
 #define SPM_ENONFINITE 5    /* NaN/Inf met in an input or produced in an output  */
 #define SPM_ETIMEOUT 6      /* a bounded device-side wait gave up                */
 #define SPM_EUNSUPPORTED 7  /* valid request this build does not implement       */
@@ -124,6 +125,17 @@ int spm_version(void);
 const char* spm_status_string(int status);
 /* 1 if the current CUDA device is sm_103 and the kernels loaded, else 0. */
 int spm_device_ok(void);
+
+/* Diagnostic of the bounded device-side waits every kernel of the library uses:
+ * `blocks` CTAs (1..number of SMs, launched cooperatively so that all are
+ * resident) meet at a device counter that waits for blocks + extra arrivals.
+ * Each waits at most limit_cycles SM clock cycles, then records SPM_ETIMEOUT
+ * and returns normally; the call synchronises `stream` and returns that status.
+ * extra = 0 must return SPM_OK; extra > 0 makes every wait run out on purpose,
+ * and the context stays usable (no fault, no hang).  SPM_EINVAL on bad
+ * arguments, SPM_EUNSUPPORTED without cooperative launch or with more blocks
+ * than SMs. */
+int spm_selftest_bounded_wait(int32_t blocks, int32_t extra, int64_t limit_cycles, void* stream);
 
 /* Device workspace comes from a memory pool of the library's own, one per
  * device, which keeps freed blocks for the next call (so repeated calls do not

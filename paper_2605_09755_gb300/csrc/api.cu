@@ -760,6 +760,54 @@ const char* spm_status_string(int s) {
 
 int spm_device_ok(void) { return tc_available() ? 1 : 0; }
 
+}  // extern "C"
+
+namespace spm {
+// `blocks` CTAs (co-resident: cooperative launch) meet at a counter that waits
+// for blocks + extra arrivals; each waits at most `limit` clock cycles and then
+// records SPM_ETIMEOUT and returns.
+__global__ void k_selftest_wait(unsigned* count, unsigned expected, long long limit, int* status) {
+  if (threadIdx.x != 0) return;
+  atomicAdd(count, 1u);
+  const long long t0 = clock64();
+  while (atomicAdd(count, 0u) < expected) {
+    if (clock64() - t0 > limit) {
+      set_status(status, DEV_TIMEOUT);
+      return;
+    }
+  }
+}
+}  // namespace spm
+
+extern "C" {
+
+int spm_selftest_bounded_wait(int32_t blocks, int32_t extra, int64_t limit_cycles, void* stream) {
+  if (blocks < 1 || blocks > 1024 || extra < 0 || extra > 1024 || limit_cycles < 1 ||
+      limit_cycles > ((int64_t)1 << 34))
+    return SPM_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  int dev = 0, coop = 0, sms = 0;
+  SPM_CUDA_TRY(cudaGetDevice(&dev));
+  SPM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop || blocks > sms) return SPM_EUNSUPPORTED;
+  Arena ar(st);
+  SPM_ALLOC(ar, unsigned, count, 1);
+  SPM_ALLOC(ar, int, status, 1);
+  SPM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned), st));
+  SPM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  unsigned expected = (unsigned)(blocks + extra);
+  long long limit = (long long)limit_cycles;
+  void* args[] = {(void*)&count, (void*)&expected, (void*)&limit, (void*)&status};
+  SPM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_selftest_wait, dim3((unsigned)blocks),
+                                           dim3(32), args, 0, st));
+  count_launch();
+  int h = 0;
+  SPM_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPM_CUDA_TRY(cudaStreamSynchronize(st));
+  return h;
+}
+
 int spm_trim_memory(void) {
   cudaMemPool_t p = lib_pool();
   if (!p) return SPM_ECUDA;

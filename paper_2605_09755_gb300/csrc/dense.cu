@@ -445,14 +445,35 @@ static int cholesky_inv_t(int64_t r, T* G, int64_t ldg, T* Li, int64_t ldi, int*
   return SPM_OK;
 }
 
+// A caller that passes no deflation flags cannot use a deflated factor (a
+// least-squares solve, not an orthonormalisation): any deflated column is then
+// a breakdown.
+__global__ void k_defl_breakdown(int64_t r, const int* __restrict__ defl, int* status) {
+  int any = 0;
+  for (int64_t j = threadIdx.x; j < r; j += blockDim.x) any |= defl[j];
+  if (__syncthreads_or(any) && threadIdx.x == 0) set_status(status, DEV_BREAKDOWN);
+}
+
 int cholesky_inv(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,
                  int* status, cudaStream_t st) {
+  Arena ar(st);
+  int* dd = defl;
+  if (!dd) {
+    dd = ar.alloc<int>(r);
+    if (!dd) return SPM_ENOMEM;
+  }
   // one cooperative kernel where the grid fits; the multi-launch path otherwise
-  const int rc = cholesky_inv_coop(r, G, ldg, Linv, ldi, dt, defl, status, st);
-  if (rc != SPM_EUNSUPPORTED) return rc;
-  if (dt == DT_F64) return cholesky_inv_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, defl, status, st);
-  if (dt == DT_F32) return cholesky_inv_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, defl, status, st);
-  return SPM_EINVAL;
+  int rc = cholesky_inv_coop(r, G, ldg, Linv, ldi, dt, dd, status, st);
+  if (rc == SPM_EUNSUPPORTED) {
+    if (dt == DT_F64) rc = cholesky_inv_t<double>(r, (double*)G, ldg, (double*)Linv, ldi, dd, status, st);
+    else if (dt == DT_F32) rc = cholesky_inv_t<float>(r, (float*)G, ldg, (float*)Linv, ldi, dd, status, st);
+    else rc = SPM_EINVAL;
+  }
+  if (rc == SPM_OK && !defl) {
+    k_defl_breakdown<<<1, 256, 0, st>>>(r, dd, status);
+    SPM_LAUNCH_CHECK();
+  }
+  return rc;
 }
 
 // Replace the deflated columns of X (rows x c) by Gaussian columns scaled by

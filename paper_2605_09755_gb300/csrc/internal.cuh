@@ -135,6 +135,8 @@ int add2d_f32(int64_t rows, int64_t cols, float* D, int64_t ldd, const float* T,
 // and Linv = L^{-1} (row-major, ldi).  dt: F32 or F64.  Breakdown -> status.
 // Deflated columns (pivot <= tol * max diag) are flagged in defl[r] (may be
 // nullptr) and get a unit L column; see fill_deflated.
+// With defl == nullptr the caller cannot use a deflated factor: a deflated
+// column then records SPM_EBREAKDOWN in *status.
 // Cholesky + inverse in one cooperative kernel (r <= 8192); SPM_EUNSUPPORTED
 // when it cannot be launched.
 int cholesky_inv_coop(int64_t r, void* G, int64_t ldg, void* Linv, int64_t ldi, int dt, int* defl,

@@ -166,6 +166,28 @@ def test_rsvd_fp64_parity(spm, m, n, r1, r2, q, s):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("m,n,r1,r2,q,noise", [(1500, 700, 200, 80, 1, 1e-2), (600, 900, 120, 60, 2, 1e-1),
+                                                (2048, 512, 256, 100, 0, 3e-2)])
+def test_resid_est_matches_oracle_residual(spm, prec, m, n, r1, r2, q, noise):
+    """info.resid_est = sqrt(|A|_F^2 - |Q^T A|_F^2) against the oracle's
+    residual_fro(A, Q) = |A - Q Q^T A|_F formed directly, for the library's own
+    basis (k = r2, so U spans Q).  The subtraction loses relative accuracy
+    |A|_F^2 / resid^2 times the working precision."""
+    A, _ = wl.noisy_exp_numpy(m, n, seed=m + n, noise=noise)
+    p = {"fp64": spm.PREC_FP64, "mixed": spm.PREC_MIXED}[prec]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    S = spm.Sketch(n, r1, 8, 42)
+    U, sg, Vt, info = spm.rsvd(S, dev(A, dt), r2, q, r2, omega_seed=43, precision=p)
+    U = host(U)
+    Qg, _ = np.linalg.qr(U)              # the same range, exactly orthonormal
+    res = alg.residual_fro(A, Qg)
+    fro = np.linalg.norm(A)
+    assert abs(info["fro_a"] - fro) <= (1e-12 if prec == "fp64" else 1e-6) * fro
+    u = 1e-15 if prec == "fp64" else 2e-6
+    assert abs(info["resid_est"] - res) <= 10 * u * fro ** 2 / res + 1e-12 * fro
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_rsvd_truncated_rank_below_r2(spm, prec):
     """k < r2: the finish keeps the k largest of the r2 computed directions (the
     rows of V^T and columns of U~ gathered in the order of sigma)."""

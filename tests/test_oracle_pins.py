@@ -462,3 +462,24 @@ def test_polydecay_generator_spectrum():
     assert np.allclose(sigma, 300.0 / np.arange(1, 151))
     s = np.linalg.svd(A.double().numpy(), compute_uv=False)
     assert np.max(np.abs(s - sigma) / sigma[0]) < 1e-5
+
+
+def test_residual_norms_closed_form():
+    """A = U diag(sigma) V^T with orthonormal U, V and Q = the first k columns of
+    U: ||A - Q Q^T A||_2 = sigma_{k+1} and ||.||_F = sqrt(sum_{i>k} sigma_i^2)
+    (Eckart-Young attained); a Q missing the top direction gives sigma_1."""
+    rng = np.random.default_rng(5)
+    m, n, k = 60, 40, 7
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sigma = np.sort(rng.uniform(0.1, 3.0, n))[::-1]
+    A = (U * sigma) @ V.T
+    Q = U[:, :k]
+    assert abs(alg.residual_spec(A, Q) - sigma[k]) <= 1e-12 * sigma[0]
+    assert abs(alg.residual_fro(A, Q) - np.sqrt(np.sum(sigma[k:] ** 2))) <= 1e-12 * sigma[0]
+    assert abs(alg.residual_fro(A, Q) - alg.optimal_fro(sigma, k)) <= 1e-12 * sigma[0]
+    Qm = U[:, 1:k + 1]                   # skips the largest direction
+    assert abs(alg.residual_spec(A, Qm) - sigma[0]) <= 1e-12 * sigma[0]
+    # a rotated basis of the same range gives the same residuals
+    R, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    assert abs(alg.residual_spec(A, Q @ R) - sigma[k]) <= 1e-12 * sigma[0]

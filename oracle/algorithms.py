@@ -19,6 +19,15 @@ Each function follows the paper's steps in order, with numpy/LAPACK primitives
     C = C~ Y, W = Y^T W~ Y; A_hat = C W^+ C^T.  Re-orthonormalising Y between
     the q products changes Y by an invertible right factor, which leaves
     C W^+ C^T unchanged (Section 3, proof of Theorem 2.3).
+  * nystrom_eig   -- the same approximation in factored form A_hat = U diag(lam) U^T,
+    computed stably: with the test matrix T = S Y (so that C = A T and
+    W = T^T A T), the Nystrom approximation of A + nu I is formed instead
+    (C_nu = C + nu T, W_nu = T^T C_nu, positive definite), as
+    F = C_nu L^{-T} with L L^T = W_nu, then F = U Sigma V^T and
+    lam = max(Sigma^2 - nu, 0).  The paper leaves W^+ unspecified; the shift
+    nu = sqrt(n) * 2^-52 * |C|_F is the reading used for the stable factored
+    output (the shifted Nystrom approximation of Tropp, Yurtsever, Udell and
+    Cevher, 2017).
 
 Readings (listed in the design notes): r2 = k; W^+ drops eigenvalues at or below
 r2 * eps * lambda_max; singular vectors are sign-fixed so that the entry of
@@ -26,7 +35,7 @@ largest magnitude of each left vector is positive.
 """
 import numpy as np
 
-from .sketch import apply_right, apply_left_t
+from .sketch import apply_right, apply_left_t, apply_left
 
 
 def orth(Y):
@@ -111,6 +120,34 @@ def nystrom(A, S, Omega, q, reorth=True):
     C = Ct @ Y
     W = Y.T @ Wt @ Y
     return C, 0.5 * (W + W.T)
+
+
+def nystrom_eig(A, S, Omega, q, reorth=True):
+    """Algorithm 3 in factored form: (U, lam) with A_hat = U diag(lam) U^T, U
+    orthonormal (n x r2), lam descending and >= 0 (see the module notes)."""
+    import scipy.linalg
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Ct = apply_right(A, S)                 # C~ = A S
+    Wt = apply_left_t(S, Ct)               # W~ = S^T A S
+    Wt = 0.5 * (Wt + Wt.T)
+    Y = np.asarray(Omega, dtype=np.float64)
+    for _ in range(q):
+        Y = Wt @ Y                         # Y = W~^q Omega
+        if reorth:
+            Y = orth(Y)
+    T = apply_left(S, Y)                   # test matrix: C = A T
+    C = Ct @ Y
+    nu = np.sqrt(n) * 2.0 ** -52 * np.linalg.norm(C)
+    Cn = C + nu * T                        # (A + nu I) T
+    Wn = T.T @ Cn                          # T^T (A + nu I) T
+    Wn = 0.5 * (Wn + Wn.T)
+    L = np.linalg.cholesky(Wn)
+    F = scipy.linalg.solve_triangular(L, Cn.T, lower=True).T   # C_nu L^{-T}
+    U, sig, _ = np.linalg.svd(F, full_matrices=False)
+    lam = np.maximum(sig ** 2 - nu, 0.0)
+    U, _ = sign_fix(U)
+    return U, lam
 
 
 def nystrom_apply(C, W):

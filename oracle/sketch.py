@@ -248,3 +248,11 @@ def gaussian(rows, cols, seed):
     ang = 6.283185307179586 * u2
     z = np.where((e & np.uint64(1)) == 0, rad * np.cos(ang), rad * np.sin(ang))
     return z.reshape(rows, cols)
+
+
+def apply_left(S, Y):
+    """S Y  (n x p) for Y of r1 x p: the test matrix T = S Y of Algorithm 3's
+    output C = C~ Y = A (S Y)."""
+    if S.kind in (DENSE_SIGN, SRHT):
+        return S.dense() @ np.asarray(Y, dtype=np.float64)
+    return np.asarray(S.sparse() @ np.asarray(Y, dtype=np.float64))

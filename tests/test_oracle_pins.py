@@ -483,3 +483,53 @@ def test_residual_norms_closed_form():
     # a rotated basis of the same range gives the same residuals
     R, _ = np.linalg.qr(rng.standard_normal((k, k)))
     assert abs(alg.residual_spec(A, Q @ R) - sigma[k]) <= 1e-12 * sigma[0]
+
+
+def test_apply_left_is_the_adjoint_of_apply_left_t():
+    """<S Y, X> = <Y, S^T X> for the sparse sign sketch: S Y (the test matrix of
+    the factored Nystrom output) against the independently written S^T X."""
+    rng = np.random.default_rng(8)
+    n, r1, p = 300, 40, 7
+    S = sk.Sketch(n, r1, 5, 17)
+    Y = rng.standard_normal((r1, p))
+    X = rng.standard_normal((n, p))
+    lhs = np.sum(sk.apply_left(S, Y) * X)
+    rhs = np.sum(Y * sk.apply_left_t(S, X))
+    assert abs(lhs - rhs) <= 1e-12 * np.abs(lhs)
+    assert np.allclose(sk.apply_left(S, Y), S.dense() @ Y, rtol=0, atol=1e-14)
+
+
+def _psd(n, rank, rng, decay=1.0):
+    V, _ = np.linalg.qr(rng.standard_normal((n, rank)))
+    mu = decay ** np.arange(rank) * rng.uniform(0.5, 1.5, rank)
+    return (V * mu) @ V.T
+
+
+def test_factored_nystrom_recovers_exact_low_rank():
+    """rank(A) <= r2 and a sketch that sees the range: A_hat = A (the shift nu
+    is O(u |A|))."""
+    rng = np.random.default_rng(9)
+    n, rank, r1, r2 = 200, 10, 60, 20
+    A = _psd(n, rank, rng)
+    S = sk.Sketch(n, r1, 8, 3)
+    U, lam = alg.nystrom_eig(A, S, sk.gaussian(r1, r2, 4), 1)
+    Ah = (U * lam) @ U.T
+    assert np.linalg.norm(A - Ah) <= 1e-10 * np.linalg.norm(A)
+    assert np.all(lam >= 0) and np.all(np.diff(lam) <= 0)
+    assert np.linalg.norm(U.T @ U - np.eye(r2)) <= 1e-12
+
+
+def test_factored_nystrom_equals_c_w_pinv_c():
+    """For a positive definite W the shifted factored form and C W^+ C^T agree to
+    O(nu kappa(W)); A - A_hat stays positive semidefinite (Theorem 2.3's proof)."""
+    rng = np.random.default_rng(10)
+    n, r1, r2 = 150, 50, 15
+    A = _psd(n, n, rng, decay=0.9) + 1e-3 * np.eye(n)
+    S = sk.Sketch(n, r1, 8, 5)
+    Om = sk.gaussian(r1, r2, 6)
+    C, W = alg.nystrom(A, S, Om, 2)
+    U, lam = alg.nystrom_eig(A, S, Om, 2)
+    Ah1 = alg.nystrom_apply(C, W)
+    Ah2 = (U * lam) @ U.T
+    assert np.linalg.norm(Ah1 - Ah2) <= 1e-8 * np.linalg.norm(A)
+    assert np.linalg.eigvalsh(A - Ah2).min() >= -1e-9 * np.linalg.norm(A, 2)

@@ -341,6 +341,23 @@ int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, in
                 int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts,
                 void* C, int64_t ldc, void* W, int64_t ldw, spm_info* info, void* stream);
 
+/* ---- a8: Algorithm 3 in factored form --------------------------------------------
+ * The Nystrom approximation of Algorithm 3 as A_hat = U diag(lam) U^T: U (n x r2,
+ * ld ldu, orthonormal columns, the largest-magnitude entry of each positive) and
+ * lam (r2, descending, >= 0), both of the call's dtype.  With the test matrix
+ * T = S Y of Algorithm 3 (so that its C = A T and W = T^T A T), the library forms
+ * the Nystrom approximation of A + nu I, nu = sqrt(n) 2^-52 |C|_F, which stays
+ * well defined when W is singular: C_nu = C + nu T, W_nu = T^T C_nu = L L^T (a
+ * Cholesky factorisation in FP64 in every precision mode), F = C_nu L^{-T} =
+ * U Sigma V^T (through the eigendecomposition of F^T F), lam = max(Sigma^2 - nu, 0).
+ * A_hat equals C W^+ C^T up to O(nu) terms.  The paper leaves W^+ unspecified;
+ * this shifted form follows Tropp, Yurtsever, Udell and Cevher (2017).  Sparse
+ * sign and identity sketches (SPM_EUNSUPPORTED for the dense kinds); a W_nu that
+ * is not positive definite returns SPM_EBREAKDOWN. */
+int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, int64_t lda,
+                    int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* U,
+                    int64_t ldu, void* lam, spm_info* info, void* stream);
+
 /* ---- tensor-core building block --------------------------------------------
  * D (M x N, FP32, row stride ldd) = sum_{q < npass} A_q (M x K) * B_q (N x K)^T on
  * tcgen05 tensor cores, BF16 operands, FP32 accumulation: the tall-skinny

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libspm.so")
-SOURCES = ["sketch.cu", "gemm_simt.cu", "gemm_tc.cu", "dense.cu", "api.cu", "mlp.cu", "selector.cu", "batched.cu", "chol.cu", "sparse.cu", "sketch_dense.cu", "sketch_sched.cu"]
+SOURCES = ["sketch.cu", "gemm_simt.cu", "gemm_tc.cu", "dense.cu", "api.cu", "mlp.cu", "selector.cu", "batched.cu", "chol.cu", "sparse.cu", "sketch_dense.cu", "sketch_sched.cu", "nystrom.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]

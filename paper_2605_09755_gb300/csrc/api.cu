@@ -1046,6 +1046,205 @@ int spm_lowrank(const spm_sketch* S1, const spm_sketch* S2, const void* A, int32
   return finish(C, info, rc, false);
 }
 
+}  // extern "C"
+
+namespace spm {
+
+// Algorithm 3 up to C: C~ = A S (n x r1), W~ = S^T C~ (r1 x r1, symmetrised),
+// Y = W~^q Omega (r1 x r2, re-orthonormalised between the q products) and
+// C = C~ Y (n x r2), in the working type wdt (FP64 in FP64 mode, else FP32).
+// In mixed precision C = C~ Y is a split-BF16 tensor-core product.
+struct Nys {
+  void* Ct = nullptr;  // n x r1
+  void* Wt = nullptr;  // r1 x r1
+  void* Y = nullptr;   // r1 x r2
+  void* C = nullptr;   // n x r2
+  int wdt = DT_F64;
+};
+
+static int nystrom_core(Call& C, const spm_sketch* S, const void* A, int64_t n, int64_t lda,
+                        int64_t r2, int q, uint64_t omega_seed, Nys& o) {
+  const int64_t r1 = S->r1;
+  const bool f64 = C.prec == SPM_PREC_FP64;
+  const int wdt = f64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(wdt);
+  o.wdt = wdt;
+  o.Ct = C.ar.alloc<unsigned char>(n * r1 * es);
+  o.Wt = C.ar.alloc<unsigned char>(r1 * r1 * es);
+  o.Y = C.ar.alloc<unsigned char>(r1 * r2 * es);
+  o.C = C.ar.alloc<unsigned char>(n * r2 * es);
+  void* Yn = C.ar.alloc<unsigned char>(r1 * r2 * es);
+  if (!o.Ct || !o.Wt || !o.Y || !o.C || !Yn) return SPM_ENOMEM;
+  {
+    StageScope sc(C.timer, SPM_STAGE_SKETCH);
+    if (C.omega)
+      SPM_TRY(convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(o.Y, wdt, r2), C.st));
+    else
+      SPM_TRY(gaussian_dev(o.Y, wdt, r1, r2, r2, omega_seed, C.st));
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_APPLY);
+    SPM_TRY(sketch_apply_dev(S, A, C.adt, n, lda, o.Ct, wdt, r1, C.want_fro ? C.acc : nullptr,
+                             C.st, nullptr, C.status));                  // C~ = A S
+    SPM_TRY(sketch_apply_t_dev(S, o.Ct, wdt, r1, r1, o.Wt, wdt, r1, C.st));  // W~ = S^T C~
+    SPM_TRY(symmetrize(r1, o.Wt, r1, wdt, C.st));
+  }
+  for (int t = 0; t < q; ++t) {
+    StageScope sc(C.timer, SPM_STAGE_POWER);
+    SPM_TRY(gemm_simt(r1, r2, r1, 1.0, rowmajor(o.Wt, wdt, r1), rowmajor(o.Y, wdt, r2), 0.0,
+                      mrowmajor(Yn, wdt, r2), C.st));
+    SPM_TRY(convert2d(r1, r2, rowmajor(Yn, wdt, r2), mrowmajor(o.Y, wdt, r2), C.st));
+    if (C.reorth) {
+      if (f64)
+        SPM_TRY(orth_f64(C, (double*)o.Y, r1, r2, r2, 3));
+      else
+        SPM_TRY(orth_small_f32(C, (float*)o.Y, r1, r2, r2, 3));
+    }
+  }
+  StageScope sc(C.timer, SPM_STAGE_PROJECT);
+  if (C.prec == SPM_PREC_MIXED) {
+    // C = C~ Y as hi*hi + hi*lo + lo*hi BF16 products: A-op C~ (M = n, K = r1)
+    // K-major; B-op Y (N = r2, K = r1) stored K x N, MN-major
+    const int64_t r1p = pad8(r1), r2p = pad8(r2);
+    Arena ar(C.st);
+    SPM_ALLOC(ar, __nv_bfloat16, Chi, n * r1p);
+    SPM_ALLOC(ar, __nv_bfloat16, Clo, n * r1p);
+    SPM_ALLOC(ar, __nv_bfloat16, Yhi, r1 * r2p);
+    SPM_ALLOC(ar, __nv_bfloat16, Ylo, r1 * r2p);
+    SPM_TRY(split_bf16(n, r1, rowmajor(o.Ct, DT_F32, r1), mrowmajor(Chi, DT_BF16, r1p),
+                       mrowmajor(Clo, DT_BF16, r1p), C.st));
+    SPM_TRY(split_bf16(r1, r2, rowmajor(o.Y, DT_F32, r2), mrowmajor(Yhi, DT_BF16, r2p),
+                       mrowmajor(Ylo, DT_BF16, r2p), C.st));
+    SPM_TRY(tc_split(n, r2, r1, Chi, Clo, r1p, false, Yhi, Ylo, r2p, true, 3, (float*)o.C, r2, 1,
+                     C.st, C.status));
+  } else {
+    SPM_TRY(gemm_simt(n, r2, r1, 1.0, rowmajor(o.Ct, wdt, r1), rowmajor(o.Y, wdt, r2), 0.0,
+                      mrowmajor(o.C, wdt, r2), C.st));
+  }
+  return SPM_OK;
+}
+
+// D (M x N, FP32) = X^T Y or X Y (op_x = true for X^T) as split-BF16 tensor-core
+// products of FP32 operands; `sym` for a symmetric result (X^T X).
+static int tc_f32(Call& C, int64_t M, int64_t N, int64_t K, const float* X, int64_t ldx, bool xt,
+                  const float* Yp, int64_t ldy, bool yt, float* D, int64_t ldd, bool sym = false) {
+  // A-op (M x K): X^T stored K x M (MN-major) or X stored M x K (K-major)
+  // B-op (N x K): Y stored K x N (MN-major) unless yt: Y^T, i.e. Y stored N x K
+  Arena ar(C.st);
+  const int64_t xr = xt ? K : M, xc = xt ? M : K, yr = yt ? N : K, yc = yt ? K : N;
+  const int64_t xcp = pad8(xc), ycp = pad8(yc);
+  SPM_ALLOC(ar, __nv_bfloat16, Xh, xr * xcp);
+  SPM_ALLOC(ar, __nv_bfloat16, Xl, xr * xcp);
+  SPM_TRY(split_bf16(xr, xc, rowmajor(X, DT_F32, ldx), mrowmajor(Xh, DT_BF16, xcp),
+                     mrowmajor(Xl, DT_BF16, xcp), C.st));
+  const __nv_bfloat16 *Yh = Xh, *Yl = Xl;
+  if (Yp != X || yr != xr || yc != xc) {
+    __nv_bfloat16* h = ar.alloc<__nv_bfloat16>(yr * ycp);
+    __nv_bfloat16* l = ar.alloc<__nv_bfloat16>(yr * ycp);
+    if (!h || !l) return SPM_ENOMEM;
+    SPM_TRY(split_bf16(yr, yc, rowmajor(Yp, DT_F32, ldy), mrowmajor(h, DT_BF16, ycp),
+                       mrowmajor(l, DT_BF16, ycp), C.st));
+    Yh = h;
+    Yl = l;
+  }
+  return tc_split(M, N, K, Xh, Xl, xcp, xt, Yh, Yl, ycp, !yt, 3, D, ldd, 1, C.st, C.status, sym);
+}
+
+// Factored Nystrom finish: U (n x r2) and lam (r2) with A_hat = U diag(lam) U^T
+// (see nystrom.cu for the construction).  The Cholesky of W_nu is FP64 in every mode.
+static int nystrom_eig_finish(Call& C, const spm_sketch* S, Nys& o, int64_t n, int64_t r2, void* Uout,
+                              int64_t ldu, void* lam_out) {
+  const int wdt = o.wdt;
+  const size_t es = dt_size(wdt);
+  const bool mixed = C.prec == SPM_PREC_MIXED;
+  const int sdt = (C.prec == SPM_PREC_FP64 || C.small64) ? DT_F64 : DT_F32;
+  Arena ar(C.st);
+  void* T = ar.alloc<unsigned char>(n * r2 * es);
+  void* F = ar.alloc<unsigned char>(n * r2 * es);
+  void* U = ar.alloc<unsigned char>(n * r2 * es);
+  double* Wn = ar.alloc<double>(r2 * r2);
+  double* Li = ar.alloc<double>(r2 * r2);
+  void* Lw = ar.alloc<unsigned char>(r2 * r2 * es);
+  void* G = ar.alloc<unsigned char>(r2 * r2 * es);
+  void* Gs = ar.alloc<unsigned char>(r2 * r2 * dt_size(sdt));
+  void* V = ar.alloc<unsigned char>(r2 * r2 * dt_size(sdt));
+  void* Vw = ar.alloc<unsigned char>(r2 * r2 * es);
+  void* sig2 = ar.alloc<unsigned char>(r2 * dt_size(sdt));
+  double* scal = ar.alloc<double>(4);  // [0] |C|_F^2, [1] nu
+  double* sigma = ar.alloc<double>(r2);
+  if (!T || !F || !U || !Wn || !Li || !Lw || !G || !Gs || !V || !Vw || !sig2 || !scal || !sigma)
+    return SPM_ENOMEM;
+  {
+    StageScope sc(C.timer, SPM_STAGE_SMALL);
+    SPM_CUDA_TRY(cudaMemsetAsync(scal, 0, 4 * sizeof(double), C.st));
+    SPM_TRY(sketch_left_dev(S, o.Y, wdt, r2, r2, T, r2, C.st));     // T = S Y: C = A T
+    SPM_TRY(sumsq(n, r2, rowmajor(o.C, wdt, r2), scal, C.st));
+    SPM_TRY(nys_shift_dev(n, r2, o.C, r2, T, r2, wdt, scal, scal + 1, C.st));  // C_nu = C + nu T
+    // W_nu = T^T C_nu (r2 x r2), symmetrised, in FP64
+    if (mixed) {
+      SPM_TRY(tc_f32(C, r2, r2, n, (const float*)T, r2, true, (const float*)o.C, r2, false, (float*)G,
+                     r2));
+      SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Wn, DT_F64, r2), C.st));
+    } else {
+      SPM_TRY(gemm_simt(r2, r2, n, 1.0, transpose(rowmajor(T, wdt, r2)), rowmajor(o.C, wdt, r2), 0.0,
+                        mrowmajor(Wn, DT_F64, r2), C.st));
+    }
+    SPM_TRY(symmetrize(r2, Wn, r2, DT_F64, C.st));
+    SPM_TRY(cholesky_inv(r2, Wn, r2, Li, r2, DT_F64, nullptr, C.status, C.st));  // L L^T = W_nu
+  }
+  {
+    StageScope sc(C.timer, SPM_STAGE_FINISH);
+    // F = C_nu L^{-T}
+    if (mixed) {
+      SPM_TRY(convert2d(r2, r2, rowmajor(Li, DT_F64, r2), mrowmajor(Lw, DT_F32, r2), C.st));
+      SPM_TRY(tc_f32(C, n, r2, r2, (const float*)o.C, r2, false, (const float*)Lw, r2, true, (float*)F,
+                     r2));
+    } else {
+      SPM_TRY(gemm_simt(n, r2, r2, 1.0, rowmajor(o.C, wdt, r2), transpose(rowmajor(Li, DT_F64, r2)),
+                        0.0, mrowmajor(F, wdt, r2), C.st));
+    }
+    // F = Q_F R with Q_F orthonormal (shifted CholeskyQR3, in place); R = Q_F^T F
+    SPM_TRY(convert2d(n, r2, rowmajor(F, wdt, r2), mrowmajor(U, wdt, r2), C.st));  // keep F
+    if (mixed) {
+      const int64_t r2p = pad8(r2);
+      __nv_bfloat16* Qh = ar.alloc<__nv_bfloat16>(n * r2p);
+      __nv_bfloat16* Ql = ar.alloc<__nv_bfloat16>(n * r2p);
+      if (!Qh || !Ql) return SPM_ENOMEM;
+      SPM_TRY(orth_big_mixed(C, (float*)F, n, r2, r2, Qh, Ql));
+      SPM_TRY(tc_f32(C, r2, r2, n, (const float*)F, r2, true, (const float*)U, r2, false, (float*)G, r2));
+    } else {
+      if (wdt == DT_F64)
+        SPM_TRY(orth_f64(C, (double*)F, n, r2, r2, 3));
+      else
+        SPM_TRY(orth_small_f32(C, (float*)F, n, r2, r2, 3));
+      SPM_TRY(gemm_simt(r2, r2, n, 1.0, transpose(rowmajor(F, wdt, r2)), rowmajor(U, wdt, r2), 0.0,
+                        mrowmajor(G, wdt, r2), C.st));
+    }
+    // R R^T = U~ diag(sig2) U~^T (small, in sdt): F = Q_F U~ Sigma V^T
+    SPM_TRY(convert2d(r2, r2, rowmajor(G, wdt, r2), mrowmajor(Lw, wdt, r2), C.st));
+    SPM_TRY(gemm_simt(r2, r2, r2, 1.0, rowmajor(Lw, wdt, r2), transpose(rowmajor(Lw, wdt, r2)), 0.0,
+                      mrowmajor(Gs, sdt, r2), C.st));
+    SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
+    SPM_TRY(sym_eig(r2, Gs, r2, V, r2, sig2, sdt, C.status, C.st, C.status + 1));
+    // U = Q_F U~, lam = max(sig2 - nu, 0)
+    SPM_TRY(convert2d(r2, r2, rowmajor(V, sdt, r2), mrowmajor(Vw, wdt, r2), C.st));
+    if (mixed)
+      SPM_TRY(tc_f32(C, n, r2, r2, (const float*)F, r2, false, (const float*)Vw, r2, false, (float*)U,
+                     r2));
+    else
+      SPM_TRY(gemm_simt(n, r2, r2, 1.0, rowmajor(F, wdt, r2), rowmajor(Vw, wdt, r2), 0.0,
+                        mrowmajor(U, wdt, r2), C.st));
+    SPM_TRY(nys_lambda_dev(r2, sig2, sdt, scal + 1, sigma, lam_out, C.adt, C.st));
+    SPM_TRY(sign_fix(n, r2, 0, mrowmajor(U, wdt, r2), mrowmajor(U, wdt, r2), C.st));
+    SPM_TRY(store_out(n, r2, rowmajor(U, wdt, r2), Uout, C.adt, ldu, C.st));
+  }
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+extern "C" {
+
 int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, int64_t lda,
                 int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* Cout,
                 int64_t ldc, void* Wout, int64_t ldw, spm_info* info, void* stream) {
@@ -1055,72 +1254,43 @@ int spm_nystrom(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, in
   setup_call(C, dtype, opts, info);
   SPM_TRY(prepare(C));
   const int64_t r1 = S->r1;
-  const bool f64 = C.prec == SPM_PREC_FP64;
-  const int wdt = f64 ? DT_F64 : DT_F32;
+  Nys o;
+  int rc = nystrom_core(C, S, A, n, lda, r2, q, omega_seed, o);
+  if (rc != SPM_OK) return finish(C, info, rc, false);
+  const int wdt = o.wdt;
   const size_t es = dt_size(wdt);
-  void* Ct = C.ar.alloc<unsigned char>(n * r1 * es);
-  void* Wt = C.ar.alloc<unsigned char>(r1 * r1 * es);
-  void* Y = C.ar.alloc<unsigned char>(r1 * r2 * es);
-  void* Yn = C.ar.alloc<unsigned char>(r1 * r2 * es);
-  void* Cw = C.ar.alloc<unsigned char>(n * r2 * es);
   void* T = C.ar.alloc<unsigned char>(r1 * r2 * es);
   void* Ww = C.ar.alloc<unsigned char>(r2 * r2 * es);
-  if (!Ct || !Wt || !Y || !Yn || !Cw || !T || !Ww) return SPM_ENOMEM;
-  int rc = SPM_OK;
+  if (!T || !Ww) return finish(C, info, SPM_ENOMEM, false);
   do {
-    {
-      StageScope sc(C.timer, SPM_STAGE_SKETCH);
-      if (C.omega)
-        rc = convert2d(r1, r2, rowmajor(C.omega, C.adt, r2), mrowmajor(Y, wdt, r2), C.st);
-      else
-        rc = gaussian_dev(Y, wdt, r1, r2, r2, omega_seed, C.st);
-      if (rc) break;
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_APPLY);
-      rc = sketch_apply_dev(S, A, C.adt, n, lda, Ct, wdt, r1, C.acc, C.st);  // C~ = A S
-      if (rc) break;
-      rc = sketch_apply_t_dev(S, Ct, wdt, r1, r1, Wt, wdt, r1, C.st);       // W~ = S^T C~
-      if (rc) break;
-      rc = symmetrize(r1, Wt, r1, wdt, C.st);
-      if (rc) break;
-    }
-    for (int t = 0; t < q && rc == SPM_OK; ++t) {
-      StageScope sc(C.timer, SPM_STAGE_POWER);
-      rc = gemm_simt(r1, r2, r1, 1.0, rowmajor(Wt, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
-                     mrowmajor(Yn, wdt, r2), C.st);
-      if (rc) break;
-      rc = convert2d(r1, r2, rowmajor(Yn, wdt, r2), mrowmajor(Y, wdt, r2), C.st);
-      if (rc) break;
-      if (C.reorth) {
-        if (f64)
-          rc = orth_f64(C, (double*)Y, r1, r2, r2, 3);
-        else
-          rc = orth_small_f32(C, (float*)Y, r1, r2, r2, 3);
-      }
-    }
+    StageScope sc(C.timer, SPM_STAGE_FINISH);
+    rc = gemm_simt(r1, r2, r1, 1.0, rowmajor(o.Wt, wdt, r1), rowmajor(o.Y, wdt, r2), 0.0,
+                   mrowmajor(T, wdt, r2), C.st);
     if (rc) break;
-    {
-      StageScope sc(C.timer, SPM_STAGE_PROJECT);
-      rc = gemm_simt(n, r2, r1, 1.0, rowmajor(Ct, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
-                     mrowmajor(Cw, wdt, r2), C.st);  // C = C~ Y
-      if (rc) break;
-    }
-    {
-      StageScope sc(C.timer, SPM_STAGE_FINISH);
-      rc = gemm_simt(r1, r2, r1, 1.0, rowmajor(Wt, wdt, r1), rowmajor(Y, wdt, r2), 0.0,
-                     mrowmajor(T, wdt, r2), C.st);
-      if (rc) break;
-      rc = gemm_simt(r2, r2, r1, 1.0, transpose(rowmajor(Y, wdt, r2)), rowmajor(T, wdt, r2), 0.0,
-                     mrowmajor(Ww, wdt, r2), C.st);  // W = Y^T W~ Y
-      if (rc) break;
-      rc = symmetrize(r2, Ww, r2, wdt, C.st);
-      if (rc) break;
-      rc = store_out(n, r2, rowmajor(Cw, wdt, r2), Cout, C.adt, ldc, C.st);
-      if (rc) break;
-      rc = store_out(r2, r2, rowmajor(Ww, wdt, r2), Wout, C.adt, ldw, C.st);
-    }
+    rc = gemm_simt(r2, r2, r1, 1.0, transpose(rowmajor(o.Y, wdt, r2)), rowmajor(T, wdt, r2), 0.0,
+                   mrowmajor(Ww, wdt, r2), C.st);  // W = Y^T W~ Y
+    if (rc) break;
+    rc = symmetrize(r2, Ww, r2, wdt, C.st);
+    if (rc) break;
+    rc = store_out(n, r2, rowmajor(o.C, wdt, r2), Cout, C.adt, ldc, C.st);
+    if (rc) break;
+    rc = store_out(r2, r2, rowmajor(Ww, wdt, r2), Wout, C.adt, ldw, C.st);
   } while (0);
+  return finish(C, info, rc, false);
+}
+
+int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n, int64_t lda,
+                    int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* U,
+                    int64_t ldu, void* lam, spm_info* info, void* stream) {
+  SPM_TRY(check_common(S, A, dtype, n, lda, r2, q, opts));
+  if (S->n != n || !U || !lam || ldu < r2) return SPM_EINVAL;
+  if (dense_kind(S)) return SPM_EUNSUPPORTED;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  SPM_TRY(prepare(C));
+  Nys o;
+  int rc = nystrom_core(C, S, A, n, lda, r2, q, omega_seed, o);
+  if (rc == SPM_OK) rc = nystrom_eig_finish(C, S, o, n, r2, U, ldu, lam);
   return finish(C, info, rc, false);
 }
 

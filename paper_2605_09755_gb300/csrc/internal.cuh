@@ -66,6 +66,17 @@ inline bool dense_kind(const spm_sketch* S) {
   return S->kind == SPM_SKETCH_DENSE_SIGN || S->kind == SPM_SKETCH_SRHT;
 }
 
+// ---------------------------------------------------------------- nystrom.cu
+// out (n x p) = S Y for Y (r1 x p) (row j: s terms of Y's rows); sparse kinds only
+int sketch_left_dev(const spm_sketch* S, const void* Y, int dt, int64_t ldy, int64_t p, void* out,
+                    int64_t ldo, cudaStream_t st);
+// nu = sqrt(n) 2^-52 sqrt(*c_sumsq) into *nu_out, and C += nu T (n x p)
+int nys_shift_dev(int64_t n, int64_t p, void* C, int64_t ldc, const void* Tm, int64_t ldt, int dt,
+                  const double* c_sumsq, double* nu_out, cudaStream_t st);
+// sigma = sqrt(sig2) (1 where 0), lam = max(sig2 - *nu, 0) in type ldt
+int nys_lambda_dev(int64_t r, const void* sig2, int sdt, const double* nu, double* sigma, void* lam,
+                   int ldt, cudaStream_t st);
+
 // ---------------------------------------------------------------- gemm_simt.cu
 // C = alpha * A(MxK) * B(KxN) + beta * C  on CUDA cores.  Accumulates in FP64 if
 // any operand is FP64, else FP32.  batch > 1: pointers advance by the strides.

@@ -355,6 +355,22 @@ def nystrom(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw)
     return Cm, W, inf.as_dict()
 
 
+def nystrom_eig(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    """Algorithm 3 in factored form (spm_nystrom_eig): (U, lam, info) with
+    A_hat = U diag(lam) U^T."""
+    _require_cuda(A)
+    o = make_opts(precision, **kw)
+    n = A.shape[0]
+    U = torch.empty(n, r2, dtype=A.dtype, device=A.device)
+    lam = torch.empty(r2, dtype=A.dtype, device=A.device)
+    inf = _info(timing)
+    fn = _fn("spm_nystrom_eig", [VP, VP, I32, I64, I64, I64, I32, U64, ctypes.POINTER(Opts), VP, I64,
+                                 VP, ctypes.POINTER(Info), VP])
+    _check(fn(S.handle, _ptr(A), _dt(A), n, A.stride(0), r2, q, int(omega_seed), ctypes.byref(o),
+              _ptr(U), U.stride(0), _ptr(lam), ctypes.byref(inf), _stream()), "spm_nystrom_eig")
+    return U, lam, inf.as_dict()
+
+
 def gemm_bf16(A_list, B_list, M, N, K, a_mn=False, b_mn=False, splitk=1):
     """D (M x N, fp32) = sum_q A_q B_q^T with bf16 operand tensors (see spm.h)."""
     npass = len(A_list)

@@ -365,6 +365,39 @@ def test_nystrom_parity(spm, prec):
 
 
 # ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("n,r1,r2,q,s", [(600, 120, 40, 1, 8), (1500, 300, 100, 2, 4), (333, 80, 80, 0, 8)])
+def test_nystrom_eig_parity(spm, prec, n, r1, r2, q, s):
+    """Algorithm 3 in factored form against the oracle's (same steps, FP64):
+    A_hat = U diag(lam) U^T.  FP64: |A_hat - A_hat_o| <= 1e-9 |A|; mixed and FP32:
+    the approximation error within 1% of the oracle's; lam >= 0 descending, U
+    orthonormal."""
+    rng = np.random.default_rng(n + r2)
+    X = rng.standard_normal((n, 6))
+    D2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    A = np.exp(-D2 / (2.0 * np.median(D2)))           # a Gaussian kernel matrix (psd)
+    So = osk.Sketch(n, r1, s, 42)
+    U_o, lam_o = alg.nystrom_eig(A, So, osk.gaussian(r1, r2, 43), q)
+    Ah_o = (U_o * lam_o) @ U_o.T
+    err_o = np.linalg.norm(A - Ah_o)
+    p = {"fp64": spm.PREC_FP64, "mixed": spm.PREC_MIXED, "fp32": spm.PREC_FP32}[prec]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    S = spm.Sketch(n, r1, s, 42)
+    U, lam, info = spm.nystrom_eig(S, dev(A, dt), r2, q, omega_seed=43, precision=p)
+    assert info["device_status"] == 0
+    U, lam = host(U), host(lam)
+    Ah = (U * lam) @ U.T
+    assert np.all(lam >= 0) and np.all(np.diff(lam) <= 1e-12 * lam[0])
+    if prec == "fp64":
+        assert np.linalg.norm(Ah - Ah_o) <= 1e-9 * np.linalg.norm(A)
+        assert np.linalg.norm(U.T @ U - np.eye(r2)) <= 1e-10
+        assert np.max(np.abs(lam - lam_o)) <= 1e-9 * lam_o[0]
+    else:
+        assert np.linalg.norm(A - Ah) <= 1.01 * err_o + 1e-5 * np.linalg.norm(A)
+        assert np.linalg.norm(U.T @ U - np.eye(r2)) <= 1e-3
+        assert np.max(np.abs(lam - lam_o)) <= 1e-4 * lam_o[0]
+
+
 def test_invalid_arguments_are_rejected(spm):
     A = torch.zeros(10, 20, device="cuda", dtype=torch.float64)
     S = spm.Sketch(20, 8, 2, 1)

@@ -426,10 +426,12 @@ def csr_main(a):
 
 
 def nystrom_main(a):
-    """Nystrom (Algorithm 3) of the Gaussian kernel over 40000 points of an 8-component
-    mixture in R^16 (means N(0, 3^2 I), unit covariance), h = the lower median of the
-    pairwise distances, K materialised in FP32; r1 = 1000, k = 500, s = 8, q = 1,
-    mixed precision.  One step = one spm_nystrom call."""
+    """Nystrom (Algorithm 3, factored form) of the Gaussian kernel over 40000 points of
+    an 8-component mixture in R^16 (means N(0, 3^2 I), unit covariance), h = the lower
+    median of the pairwise distances; r1 = 1000, k = 500, s = 8, q = 1, mixed precision.
+    One step = one spm_nystrom_gauss call: K is generated inside the product K S and
+    never stored.  The same approximation from a formed FP32 K (spm_nystrom_eig, the
+    6.4 GB matrix read from HBM) is timed beside it."""
     import numpy as np
     import torch
     from paper_2605_09755_gb300 import _build, spm
@@ -437,8 +439,8 @@ def nystrom_main(a):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     _build.build()
     lib = spm.lib()
-    n, r1, k, q = 40000, 1000, 500, 1
-    X = wl.gmm_points(n, 16, 8, seed=1004)
+    n, d, r1, k, q = 40000, 16, 1000, 500, 1
+    X = wl.gmm_points(n, d, 8, seed=1004)
     Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
     sq = (Xd * Xd).sum(1)
     D2 = (sq[:, None] + sq[None, :] - 2.0 * (Xd @ Xd.T)).clamp_min_(0.0)
@@ -447,16 +449,15 @@ def nystrom_main(a):
     D2.fill_diagonal_(float("inf"))
     kth = 2 * ((npairs - 1) // 2) + 1
     h2 = float(torch.kthvalue(D2.reshape(-1), kth).values)
+    h = h2 ** 0.5
     D2.fill_diagonal_(0.0)
     K64 = torch.exp(D2 / (-2.0 * h2))
     del D2
     K64 = 0.5 * (K64 + K64.T)
-    K = K64.float()
+    Xf = Xd.float()
     S = spm.Sketch(n, r1, a.s, 42)
-    # one step = Algorithm 3 in factored form (U diag(lam) U^T: the shifted
-    # Cholesky finish); Algorithm 3's own output (C, W) is timed beside it
-    step = lambda timing=False: spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED, timing=timing)
-    step_cw = lambda: spm.nystrom(S, K, k, q, precision=spm.PREC_MIXED, timing=2)
+    step = lambda timing=False: spm.nystrom_gauss(S, Xf, h, k, q, precision=spm.PREC_MIXED,
+                                                  timing=timing)
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
@@ -476,14 +477,36 @@ def nystrom_main(a):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / a.steps
-    step_cw()
+    U, lam, _ = step()
+    # the fused product alone (its two table/point preparation launches included)
+    spm.gauss_sketch(S, Xf, h)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(a.steps):
-        step_cw()
+        spm.gauss_sketch(S, Xf, h)
     e1.record()
     torch.cuda.synchronize()
-    ms_cw = e0.elapsed_time(e1) / a.steps
+    ks_ms = e0.elapsed_time(e1) / a.steps
+
+    # end to end through the public call with host buffers: X in, U and lam out
+    Xh = Xf.cpu().pin_memory()
+    Uh = torch.empty(n, k, dtype=torch.float32).pin_memory()
+    lh = torch.empty(k, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        Xg = Xh.to("cuda", non_blocking=True)
+        Ug, lg, _ = spm.nystrom_gauss(S, Xg, h, k, q, precision=spm.PREC_MIXED)
+        Uh.copy_(Ug, non_blocking=True)
+        lh.copy_(lg, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.steps
 
     def rel_err(U, lam, Kref):
         U64, l64 = U.double(), lam.double()
@@ -494,7 +517,21 @@ def nystrom_main(a):
             ref2 += float((Kref[i0:i0 + 4096] ** 2).sum())
         return (err2 / ref2) ** 0.5
 
-    e_mixed = rel_err(U, lam, K64)
+    e_fused = rel_err(U, lam, K64)
+    # the same approximation from the formed kernel (FP32 K in HBM), and in FP64
+    K = K64.float()
+    formed = lambda: spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED)
+    formed()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        formed()
+    e1.record()
+    torch.cuda.synchronize()
+    formed_ms = e0.elapsed_time(e1) / a.steps
+    Uk, lk, inf_k = spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED, timing=2)
+    e_formed = rel_err(Uk, lk, K64)
+    del K, Uk, lk
     U64, lam64, _ = spm.nystrom_eig(S, K64, k, q, precision=spm.PREC_FP64)
     e_fp64 = rel_err(U64, lam64, K64)
     del U64, lam64, K64
@@ -504,50 +541,66 @@ def nystrom_main(a):
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    apply_ms = inf["stage_ms"]["apply"]
-    ap_bytes = n * n * 4 + n * r1 * 4
-    ach = ap_bytes / (apply_ms * 1e-3) / 1e9 if apply_ms else None
+    # ALU roofline of the fused product: per pair (i, j), d subtractions and d
+    # multiply-adds for the squared distance, one multiply for the exponent and s
+    # multiplies by the signed 1/sqrt(s): 2 d + 1 + s FP32 lane operations (the
+    # exponential runs on the special-function unit, the additions into the
+    # accumulators in shared memory).  Peak: 128 FP32 lanes per SM per clock.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    ops = float(n) * n * (2 * d + 1 + a.s)
+    alu_peak = sms * 128 * mhz * 1e6 / 1e9
+    alu_ach = ops / (ks_ms * 1e-3) / 1e9
+    ks_bytes = n * d * 4 + n * r1 * 4 + 2 * n * ((a.s + 3) // 4 * 4) * 4
     cpu = None
     if not a.no_cpu:
         from oracle import algorithms as alg
         from oracle import sketch as osk
-        ns = 4000
-        Xs = X[:ns]
-        sqs = np.sum(Xs * Xs, axis=1)
-        Ks = np.exp(-np.maximum(sqs[:, None] + sqs[None, :] - 2.0 * (Xs @ Xs.T), 0.0) / (2.0 * h2))
-        Ks = 0.5 * (Ks + Ks.T)
+        ns = 3000
         So = osk.Sketch(ns, r1, a.s, 42)
         t0 = time.perf_counter()
+        Ks = alg.gaussian_kernel(X[:ns], h)
         osk.apply_right(Ks, So)
-        t_apply = (time.perf_counter() - t0) * 1e3
+        t_ks = (time.perf_counter() - t0) * 1e3
         t0 = time.perf_counter()
-        alg.nystrom_eig(Ks, So, osk.gaussian(r1, k, 43), q)
+        alg.nystrom_gauss(X[:ns], h, So, osk.gaussian(r1, k, 43), q)
         t = (time.perf_counter() - t0) * 1e3
-        # K S grows with n^2; everything after it (C~ Y, the finish) with n
-        est = t_apply * (n / ns) ** 2 + max(t - t_apply, 0.0) * (n / ns)
+        # forming K and K S grow with n^2; everything after them (C~ Y, the finish) with n
+        est = t_ks * (n / ns) ** 2 + max(t - t_ks, 0.0) * (n / ns)
         cpu = {"value": est, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"oracle factored Nystrom on the kernel of the first {ns} of the {n} "
-                         f"points (same r1, k, q, h): {t:.0f} ms, of which K S {t_apply:.0f} ms; "
-                         f"K S scaled by (n / {ns})^2, the rest by n / {ns}"}
+               "sample": f"oracle factored Nystrom of the Gaussian kernel of the first {ns} of "
+                         f"the {n} points (same r1, k, q, h): {t:.0f} ms, of which forming K and "
+                         f"K S {t_ks:.0f} ms; those scaled by (n / {ns})^2, the rest by n / {ns}"}
     line = {
         "metric": "time to a rank-k Nystrom approximation of a PSD kernel matrix", "value": ms,
         "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3+f32 (FP64 Cholesky)", "data": "synthetic (seeded)",
+        "dtype": "f32 (kernel values and K S) + bf16x3 (C~ Y) + f64 (Cholesky)",
+        "data": "synthetic (seeded)",
         "config": {"workload": f"Nystrom (factored, shifted Cholesky) of the Gaussian kernel over "
-                               f"{n} points of an 8-component mixture in R^16, h = lower median "
-                               f"distance, K FP32 ({n * n * 4 / 1e9:.1f} GB), r1 = {r1}, k = {k}, "
-                               f"s = {a.s}, q = {q}",
-                   "precision": "mixed", "l2": "K larger than L2; no flush"},
-        "stage_ms": inf["stage_ms"], "c_w_only_ms": ms_cw,
-        "accuracy": {"rel_fro_err_mixed": e_mixed, "rel_fro_err_fp64": e_fp64,
-                     "ratio": e_mixed / e_fp64 if e_fp64 > 0 else None, "h": h2 ** 0.5,
+                               f"{n} points of an 8-component mixture in R^{d}, h = lower median "
+                               f"distance, K generated inside K S (never stored), r1 = {r1}, "
+                               f"k = {k}, s = {a.s}, q = {q}",
+                   "precision": "mixed", "l2": "no flush: the fused product reads 2.6 MB of points "
+                                                "and writes C~ (160 MB, larger than L2)"},
+        "stage_ms": inf["stage_ms"], "gauss_sketch_ms": ks_ms,
+        "formed_kernel": {"ms": formed_ms, "stage_ms": inf_k["stage_ms"],
+                          "note": "same approximation from a formed FP32 K (6.4 GB) in HBM"},
+        "accuracy": {"rel_fro_err_fused_mixed": e_fused, "rel_fro_err_formed_mixed": e_formed,
+                     "rel_fro_err_fp64": e_fp64,
+                     "ratio": e_fused / e_fp64 if e_fp64 > 0 else None, "h": h,
                      "lam_top": float(lam[0]), "lam_k": float(lam[-1])},
-        "roofline": {"kernel": "sketch apply of K (the apply stage)", "bound": "hbm",
-                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": ach / hbm_peak if ach else None, "traffic": None,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
-        "e2e": None, "cpu_baseline": cpu, "gpu_launches": launches * a.steps, "clocks": clk,
+        "roofline": {"kernel": "k_gauss_sketch_f32 (K S, K generated)", "bound": "alu",
+                     "achieved": alu_ach, "peak": alu_peak, "unit": "Gop/s",
+                     "frac": alu_ach / alu_peak, "traffic": None,
+                     "ops_per_pair": 2 * d + 1 + a.s,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (derived)",
+                     "hbm": {"algorithmic_bytes": ks_bytes,
+                             "achieved_gbs": ks_bytes / (ks_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                             "frac": ks_bytes / (ks_ms * 1e-3) / 1e9 / hbm_peak}},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": n * d * 4,
+                "d2h_bytes_per_step": n * k * 4 + k * 4},
+        "cpu_baseline": cpu, "gpu_launches": launches * a.steps, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 

@@ -358,6 +358,33 @@ int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n
                     int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* U,
                     int64_t ldu, void* lam, spm_info* info, void* stream);
 
+/* ---- a8 on a Gaussian kernel matrix that is never formed ----------------------
+ * K[i, j] = exp(-|x_i - x_j|^2 / (2 h^2)) over n points x_i = row i of X (n x d,
+ * row-major, ld ldx >= d, DEVICE, dtype SPM_F32 or SPM_F64; 1 <= d <= 32; h > 0
+ * and finite): the kernel matrices of the paper's Nystrom experiments (Section 5).
+ * spm_gauss_sketch: out (n x r1, ld ldo >= r1, DEVICE, caller-owned, the dtype) =
+ * K S, the first product of Algorithm 3, with every entry of K generated where it
+ * is used (no n x n array).  FP32: kernel values by the hardware base-2
+ * exponential (relative error about 2^-21), summed in 32-bit fixed point with
+ * resolution 2^-F, F = min(22, floor(log2(2^30 sqrt(s) / b_max))) (b_max: the most
+ * entries of S in one column), each term rounded once by at most 2^-(F+1); the
+ * result is the same bit for bit on every call.  FP64: exp() and FP64 additions
+ * in no fixed order (the last bits may differ from call to call).  Sparse sign
+ * and identity sketches (S->n == n);
+ * SPM_EUNSUPPORTED for the dense kinds, SPM_EINVAL for bad sizes or h.  Does not
+ * synchronise; a bounded device wait that expires is recorded in the per-device
+ * status word that spm_gemm_bf16_status reads.
+ * spm_nystrom_gauss: spm_nystrom_eig of that K (same outputs, precision modes
+ * and errors), its first product taken by spm_gauss_sketch's kernel in the
+ * working type (FP64 in SPM_PREC_FP64, FP32 otherwise).  info->fro_a is not
+ * computed (0). */
+int spm_gauss_sketch(const spm_sketch* S, const void* X, int32_t dtype, int64_t n, int64_t d,
+                     int64_t ldx, double h, void* out, int64_t ldo, void* stream);
+int spm_nystrom_gauss(const spm_sketch* S, const void* X, int32_t dtype, int64_t n, int64_t d,
+                      int64_t ldx, double h, int64_t r2, int32_t q, uint64_t omega_seed,
+                      const spm_opts* opts, void* U, int64_t ldu, void* lam, spm_info* info,
+                      void* stream);
+
 /* ---- tensor-core building block --------------------------------------------
  * D (M x N, FP32, row stride ldd) = sum_{q < npass} A_q (M x K) * B_q (N x K)^T on
  * tcgen05 tensor cores, BF16 operands, FP32 accumulation: the tall-skinny

@@ -150,6 +150,23 @@ def nystrom_eig(A, S, Omega, q, reorth=True):
     return U, lam
 
 
+def gaussian_kernel(X, h):
+    """The Gaussian kernel matrix K[i, j] = exp(-|x_i - x_j|^2 / (2 h^2)) of the
+    rows of X (Section 5's kernel experiments), by its definition: squared
+    distances as sums of squared coordinate differences, in FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    D2 = np.zeros((X.shape[0], X.shape[0]))
+    for k in range(X.shape[1]):
+        diff = X[:, k][:, None] - X[:, k][None, :]
+        D2 += diff * diff
+    return np.exp(-D2 / (2.0 * h * h))
+
+
+def nystrom_gauss(X, h, S, Omega, q, reorth=True):
+    """Algorithm 3 in factored form on the Gaussian kernel matrix of the rows of X."""
+    return nystrom_eig(gaussian_kernel(X, h), S, Omega, q, reorth)
+
+
 def nystrom_apply(C, W):
     """A_hat = C W^+ C^T."""
     return C @ psd_pinv(W) @ C.T

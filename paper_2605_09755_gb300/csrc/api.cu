@@ -1062,8 +1062,17 @@ struct Nys {
   int wdt = DT_F64;
 };
 
+// The Gaussian kernel matrix of a point set, generated inside the first product
+// (A = nullptr in nystrom_core): K[i, j] = exp(-|x_i - x_j|^2 / (2 h^2)).
+struct GaussSrc {
+  const void* X;
+  int64_t d, ldx;
+  double h;
+};
+
 static int nystrom_core(Call& C, const spm_sketch* S, const void* A, int64_t n, int64_t lda,
-                        int64_t r2, int q, uint64_t omega_seed, Nys& o) {
+                        int64_t r2, int q, uint64_t omega_seed, Nys& o,
+                        const GaussSrc* gs = nullptr) {
   const int64_t r1 = S->r1;
   const bool f64 = C.prec == SPM_PREC_FP64;
   const int wdt = f64 ? DT_F64 : DT_F32;
@@ -1084,8 +1093,12 @@ static int nystrom_core(Call& C, const spm_sketch* S, const void* A, int64_t n, 
   }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
-    SPM_TRY(sketch_apply_dev(S, A, C.adt, n, lda, o.Ct, wdt, r1, C.want_fro ? C.acc : nullptr,
-                             C.st, nullptr, C.status));                  // C~ = A S
+    if (gs)                                                               // C~ = K S
+      SPM_TRY(gauss_sketch_dev(S, gs->X, C.adt, n, gs->d, gs->ldx, gs->h, o.Ct, wdt, r1, C.st,
+                               C.status));
+    else
+      SPM_TRY(sketch_apply_dev(S, A, C.adt, n, lda, o.Ct, wdt, r1, C.want_fro ? C.acc : nullptr,
+                               C.st, nullptr, C.status));                // C~ = A S
     SPM_TRY(sketch_apply_t_dev(S, o.Ct, wdt, r1, r1, o.Wt, wdt, r1, C.st));  // W~ = S^T C~
     SPM_TRY(symmetrize(r1, o.Wt, r1, wdt, C.st));
   }
@@ -1290,6 +1303,35 @@ int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n
   SPM_TRY(prepare(C));
   Nys o;
   int rc = nystrom_core(C, S, A, n, lda, r2, q, omega_seed, o);
+  if (rc == SPM_OK) rc = nystrom_eig_finish(C, S, o, n, r2, U, ldu, lam);
+  return finish(C, info, rc, false);
+}
+
+int spm_gauss_sketch(const spm_sketch* S, const void* X, int32_t dtype, int64_t n, int64_t d,
+                     int64_t ldx, double h, void* out, int64_t ldo, void* stream) {
+  if (!S || !X || !out || (dtype != SPM_F32 && dtype != SPM_F64)) return SPM_EINVAL;
+  if (n < 0 || d < 1 || ldx < d || ldo < S->r1) return SPM_EINVAL;
+  const int dt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  int* status = nullptr;
+  SPM_TRY(gemm_public_status(&status));
+  return gauss_sketch_dev(S, X, dt, n, d, ldx, h, out, dt, ldo, as_stream(stream), status);
+}
+
+int spm_nystrom_gauss(const spm_sketch* S, const void* X, int32_t dtype, int64_t n, int64_t d,
+                      int64_t ldx, double h, int64_t r2, int32_t q, uint64_t omega_seed,
+                      const spm_opts* opts, void* U, int64_t ldu, void* lam, spm_info* info,
+                      void* stream) {
+  if (!S || !X || d < 1 || ldx < d || !(h > 0.0)) return SPM_EINVAL;
+  SPM_TRY(check_common(S, X, dtype, n, S->n, r2, q, opts));
+  if (S->n != n || !U || !lam || ldu < r2) return SPM_EINVAL;
+  if (dense_kind(S)) return SPM_EUNSUPPORTED;
+  Call C(as_stream(stream));
+  setup_call(C, dtype, opts, info);
+  C.want_fro = false;                         // |K|_F is not read by the fused product
+  SPM_TRY(prepare(C));
+  Nys o;
+  const GaussSrc gs{X, d, ldx, h};
+  int rc = nystrom_core(C, S, nullptr, n, 0, r2, q, omega_seed, o, &gs);
   if (rc == SPM_OK) rc = nystrom_eig_finish(C, S, o, n, r2, U, ldu, lam);
   return finish(C, info, rc, false);
 }

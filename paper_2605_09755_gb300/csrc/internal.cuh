@@ -77,6 +77,12 @@ int nys_shift_dev(int64_t n, int64_t p, void* C, int64_t ldc, const void* Tm, in
 int nys_lambda_dev(int64_t r, const void* sig2, int sdt, const double* nu, double* sigma, void* lam,
                    int ldt, cudaStream_t st);
 
+// out (n x r1, type odt, ld ldo) = K S for the Gaussian kernel of the points X
+// (n x d, type xdt, ld ldx): K[i, j] = exp(-|x_i - x_j|^2 / (2 h^2)), K never formed;
+// an expired bounded wait is recorded in *status (nullable)
+int gauss_sketch_dev(const spm_sketch* S, const void* X, int xdt, int64_t n, int64_t d, int64_t ldx,
+                     double h, void* out, int odt, int64_t ldo, cudaStream_t st, int* status);
+
 // ---------------------------------------------------------------- gemm_simt.cu
 // C = alpha * A(MxK) * B(KxN) + beta * C  on CUDA cores.  Accumulates in FP64 if
 // any operand is FP64, else FP32.  batch > 1: pointers advance by the strides.

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "bulk.cuh"
 #include "sched_plan.h"
 
 namespace spm {
@@ -42,42 +43,16 @@ static constexpr int64_t SCHED_SEARCH = 300000;
 // Without spm_sketch_set_plan(S, 1), a sketch is planned only by a product over
 // at least this many elements of A (the plan costs ~0.1 s of host time).
 static constexpr int64_t SCHED_AUTO_ELEMS = (int64_t)1 << 24;
-static constexpr long long SCHED_WAIT_LIMIT = 1ll << 31;  // clock cycles (~1 s)
 static constexpr int SCHED_SMEM_LIMIT = 227 * 1024;
 
 static_assert(SCHED_TT == 96, "the phase sequences below are written for 96 steps");
 
-__device__ __forceinline__ uint32_t sched_smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ bool sched_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool sched_wait(uint32_t bar, uint32_t parity) {
-  if (sched_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!sched_try_wait(bar, parity))
-    if (clock64() - t0 > SCHED_WAIT_LIMIT) return false;
-  return true;
-}
 // One row of A (bytes, a multiple of 16) into shared memory; completion is
 // counted on the barrier at `bar`.
 __device__ __forceinline__ void sched_load_row(uint32_t dst, const float* src, uint32_t bytes,
                                                uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-      : "memory");
+  mbar_expect(bar, bytes);
+  bulk_g2s(dst, src, bytes, bar);
 }
 
 
@@ -209,13 +184,12 @@ __global__ void __launch_bounds__(SCHED_THREADS, 1)
   for (int i = tid; i < NSLOT * SCHED_PAD; i += SCHED_THREADS)
     ring[(size_t)(i / SCHED_PAD) * slot_floats + (i % SCHED_PAD)] = 0.f;
   if (FRO) fro_part[tid] = 0.0;
-  const uint32_t bar0 = sched_smem_u32(bars), ring0 = sched_smem_u32(ring);
+  const uint32_t bar0 = smem_u32(bars), ring0 = smem_u32(ring);
   const uint32_t slot_bytes = (uint32_t)slot_floats * 4u;
   if (tid == 0) {
     for (int s = 0; s < NSLOT; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * s) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_init(bar0 + 8 * s, 1);
+    mbar_init_fence();
     for (int s = 0; s < NSLOT; ++s) {
       const int row = p0 + s * args.P;
       if (row < args.m)
@@ -229,7 +203,7 @@ __global__ void __launch_bounds__(SCHED_THREADS, 1)
   for (int row = p0; row < args.m; row += args.P, ++it) {
     const int s = it % NSLOT;
     const uint32_t par = (uint32_t)(it / NSLOT) & 1u;
-    const bool to = !sched_wait(bar0 + 8 * s, par);
+    const bool to = !mbar_wait(bar0 + 8 * s, par);
     // the row's shared address, redefined after the wait: no load that uses it
     // can be scheduled before the copy has landed
     uint32_t rowa = ring0 + s * slot_bytes;
@@ -257,7 +231,7 @@ __global__ void __launch_bounds__(SCHED_THREADS, 1)
     if (tid == 0) {
       const int nr = row + NSLOT * args.P;
       if (nr < args.m) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        proxy_async_fence();
         sched_load_row(ring0 + s * slot_bytes + SCHED_PAD * 4, args.A + (int64_t)nr * args.lda,
                        (uint32_t)n * 4u, bar0 + 8 * s);
       }
@@ -287,7 +261,7 @@ __global__ void __launch_bounds__(SCHED_THREADS, 1)
       for (int k = 0; k < NSLOT; ++k, row += args.P) {
         if (row >= args.m) break;
         const int s = (it + k) % NSLOT;
-        sched_wait(bar0 + 8 * s, (uint32_t)((it + k) / NSLOT) & 1u);
+        mbar_wait(bar0 + 8 * s, (uint32_t)((it + k) / NSLOT) & 1u);
       }
     }
     __syncthreads();

@@ -371,6 +371,34 @@ def nystrom_eig(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, *
     return U, lam, inf.as_dict()
 
 
+def gauss_sketch(S, X, h):
+    """K S for the Gaussian kernel of the rows of X (spm_gauss_sketch): K never formed."""
+    _require_cuda(X)
+    n, d = X.shape
+    out = torch.empty(n, S.r1, dtype=X.dtype, device=X.device)
+    fn = _fn("spm_gauss_sketch", [VP, VP, I32, I64, I64, I64, ctypes.c_double, VP, I64, VP])
+    _check(fn(S.handle, _ptr(X), _dt(X), n, d, X.stride(0), float(h), _ptr(out), out.stride(0),
+              _stream()), "spm_gauss_sketch")
+    return out
+
+
+def nystrom_gauss(S, X, h, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, **kw):
+    """Factored Nystrom of the Gaussian kernel of the rows of X (spm_nystrom_gauss):
+    (U, lam, info) with K_hat = U diag(lam) U^T."""
+    _require_cuda(X)
+    o = make_opts(precision, **kw)
+    n, d = X.shape
+    U = torch.empty(n, r2, dtype=X.dtype, device=X.device)
+    lam = torch.empty(r2, dtype=X.dtype, device=X.device)
+    inf = _info(timing)
+    fn = _fn("spm_nystrom_gauss", [VP, VP, I32, I64, I64, I64, ctypes.c_double, I64, I32, U64,
+                                   ctypes.POINTER(Opts), VP, I64, VP, ctypes.POINTER(Info), VP])
+    _check(fn(S.handle, _ptr(X), _dt(X), n, d, X.stride(0), float(h), r2, q, int(omega_seed),
+              ctypes.byref(o), _ptr(U), U.stride(0), _ptr(lam), ctypes.byref(inf), _stream()),
+           "spm_nystrom_gauss")
+    return U, lam, inf.as_dict()
+
+
 def gemm_bf16(A_list, B_list, M, N, K, a_mn=False, b_mn=False, splitk=1):
     """D (M x N, fp32) = sum_q A_q B_q^T with bf16 operand tensors (see spm.h)."""
     npass = len(A_list)

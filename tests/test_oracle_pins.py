@@ -533,3 +533,41 @@ def test_factored_nystrom_equals_c_w_pinv_c():
     Ah2 = (U * lam) @ U.T
     assert np.linalg.norm(Ah1 - Ah2) <= 1e-8 * np.linalg.norm(A)
     assert np.linalg.eigvalsh(A - Ah2).min() >= -1e-9 * np.linalg.norm(A, 2)
+
+
+def test_gaussian_kernel_hand_values():
+    # points 0, 1, 3 on a line, h = 1: exp(-1/2), exp(-9/2), exp(-2) off the diagonal
+    K = alg.gaussian_kernel(np.array([[0.0], [1.0], [3.0]]), 1.0)
+    e = np.exp
+    want = np.array([[1.0, e(-0.5), e(-4.5)], [e(-0.5), 1.0, e(-2.0)], [e(-4.5), e(-2.0), 1.0]])
+    assert np.allclose(K, want, rtol=1e-15, atol=0.0)
+    # h = 2 in R^2: |(0,0) - (3,4)|^2 = 25, 25 / 8
+    K = alg.gaussian_kernel(np.array([[0.0, 0.0], [3.0, 4.0]]), 2.0)
+    assert abs(K[0, 1] - np.exp(-25.0 / 8.0)) <= 1e-16
+
+
+def test_gaussian_kernel_invariances_and_generator_agreement():
+    # shifting or rotating the points leaves K unchanged; K is psd with unit
+    # diagonal; and it matches the input generator's kernel (norm expansion)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((60, 5))
+    h = 1.7
+    K = alg.gaussian_kernel(X, h)
+    Q, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    assert np.allclose(alg.gaussian_kernel(X + 3.0, h), K, rtol=0, atol=1e-14)
+    assert np.allclose(alg.gaussian_kernel(X @ Q, h), K, rtol=0, atol=1e-14)
+    assert np.allclose(np.diag(K), 1.0) and np.allclose(K, K.T)
+    assert np.linalg.eigvalsh(K).min() >= -1e-12
+    sq = np.sum(X * X, axis=1)
+    Kg = np.exp(-np.maximum(sq[:, None] + sq[None, :] - 2.0 * X @ X.T, 0.0) / (2.0 * h * h))
+    assert np.allclose(K, Kg, rtol=0, atol=1e-13)
+
+
+def test_nystrom_gauss_is_nystrom_of_the_formed_kernel():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((200, 3))
+    S = sk.Sketch(200, 40, 4, 5)
+    Om = sk.gaussian(40, 10, 6)
+    U1, l1 = alg.nystrom_gauss(X, 1.3, S, Om, 1)
+    U2, l2 = alg.nystrom_eig(alg.gaussian_kernel(X, 1.3), S, Om, 1)
+    assert np.array_equal(U1, U2) and np.array_equal(l1, l2)

@@ -92,6 +92,7 @@ def parse():
                         "problems in one graph-captured spm_rsvd_batched call; csr: the "
                         "10^6 x 2*10^5 sparse matrix with a planted rank-200 term; nystrom: the "
                         "40000-point Gaussian kernel")
+    p.add_argument("--nys-n", type=int, default=40000, help="nystrom: number of points")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--nstreams", type=int, default=16)
     p.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"])
@@ -425,6 +426,28 @@ def csr_main(a):
     print(json.dumps(line), flush=True)
 
 
+def formed_kernel(a, spm, S, K64, k, q, e0, e1, rel_err):
+    """The Nystrom approximation of the same kernel from a formed FP32 K in HBM
+    (spm_nystrom_eig): its time, stage times and error, and the FP64 error."""
+    import torch
+    K = K64.float()
+    formed = lambda: spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED)
+    formed()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        formed()
+    e1.record()
+    torch.cuda.synchronize()
+    formed_ms = e0.elapsed_time(e1) / a.steps
+    Uk, lk, inf_k = spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED, timing=2)
+    e_formed = rel_err(Uk, lk, K64)
+    del K, Uk, lk
+    U64, lam64, _ = spm.nystrom_eig(S, K64, k, q, precision=spm.PREC_FP64)
+    e_fp64 = rel_err(U64, lam64, K64)
+    return formed_ms, inf_k, e_formed, e_fp64
+
+
 def nystrom_main(a):
     """Nystrom (Algorithm 3, factored form) of the Gaussian kernel over 40000 points of
     an 8-component mixture in R^16 (means N(0, 3^2 I), unit covariance), h = the lower
@@ -439,7 +462,7 @@ def nystrom_main(a):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     _build.build()
     lib = spm.lib()
-    n, d, r1, k, q = 40000, 16, 1000, 500, 1
+    n, d, r1, k, q = a.nys_n, 16, 1000, 500, 1
     X = wl.gmm_points(n, d, 8, seed=1004)
     Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
     sq = (Xd * Xd).sum(1)
@@ -518,23 +541,12 @@ def nystrom_main(a):
         return (err2 / ref2) ** 0.5
 
     e_fused = rel_err(U, lam, K64)
-    # the same approximation from the formed kernel (FP32 K in HBM), and in FP64
-    K = K64.float()
-    formed = lambda: spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED)
-    formed()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(a.steps):
-        formed()
-    e1.record()
-    torch.cuda.synchronize()
-    formed_ms = e0.elapsed_time(e1) / a.steps
-    Uk, lk, inf_k = spm.nystrom_eig(S, K, k, q, precision=spm.PREC_MIXED, timing=2)
-    e_formed = rel_err(Uk, lk, K64)
-    del K, Uk, lk
-    U64, lam64, _ = spm.nystrom_eig(S, K64, k, q, precision=spm.PREC_FP64)
-    e_fp64 = rel_err(U64, lam64, K64)
-    del U64, lam64, K64
+    formed_ms, inf_k, e_formed, e_fp64 = None, {"stage_ms": None}, None, None
+    if a.no_fp64:
+        del K64
+    else:
+        formed_ms, inf_k, e_formed, e_fp64 = formed_kernel(a, spm, S, K64, k, q, e0, e1, rel_err)
+        del K64
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -588,7 +600,7 @@ def nystrom_main(a):
                           "note": "same approximation from a formed FP32 K (6.4 GB) in HBM"},
         "accuracy": {"rel_fro_err_fused_mixed": e_fused, "rel_fro_err_formed_mixed": e_formed,
                      "rel_fro_err_fp64": e_fp64,
-                     "ratio": e_fused / e_fp64 if e_fp64 > 0 else None, "h": h,
+                     "ratio": e_fused / e_fp64 if e_fp64 else None, "h": h,
                      "lam_top": float(lam[0]), "lam_k": float(lam[-1])},
         "roofline": {"kernel": "k_gauss_sketch_f32 (K S, K generated)", "bound": "alu",
                      "achieved": alu_ach, "peak": alu_peak, "unit": "Gop/s",

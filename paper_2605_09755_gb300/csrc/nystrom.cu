@@ -126,25 +126,27 @@ int nys_lambda_dev(int64_t r, const void* sig2, int sdt, const double* nu, doubl
 // sqrt(s) into the accumulator of each column of row j of S.  Two warps may meet
 // in a column, so the adds are shared-memory reductions.
 //
-// FP32 accumulates in 32-bit fixed point with 2^-F resolution: a term v becomes
-// the integer round(v 2^F) by one multiply-add with the constant 1.5 * 2^23
-// (for |v 2^F| < 2^22 the sum's bit pattern is 0x4B400000 + round(v 2^F)), and
-// the bit patterns are added as integers (red.shared.add.u32: native, unlike a
-// floating-point add into shared memory).  The 0x4B400000 of every term is taken
-// off at the write-out (b_c of them in column c, b_c its number of entries).
-// Integer addition is exact and associative, so the result does not depend on
-// the order of the adds: it is reproducible bit for bit.  F = min(22,
-// floor(log2(2^30 sqrt(s) / b_max))) keeps every partial sum (at most b_max
-// terms of magnitude <= 1 / sqrt(s)) below 2^30 / 2^F; each term is rounded
-// once, by at most 2^-(F+1).
+// FP32 accumulates in 32-bit fixed point with 2^-F resolution: a kernel value
+// kv becomes the bit pattern P of kv 2^F / sqrt(s) + 1.5 * 2^23, which for
+// |kv 2^F / sqrt(s)| <= 2^22 is 0x4B400000 + round(kv 2^F / sqrt(s)) (one
+// multiply-add per point); a positive entry adds P, a negative one adds ~P =
+// -(0x4B400000 + round(...)) - 1, both as integers (red.shared.add.u32: native,
+// unlike a floating-point add into shared memory).  The constants are taken off
+// at the write-out: (p_c - m_c) 0x4B400000 - m_c for a column with p_c positive
+// and m_c negative entries.  Integer addition is exact and associative, so the
+// result does not depend on the order of the adds: it is reproducible bit for
+// bit, and wrap-around of the partial sums cancels.  F = min(22,
+// floor(log2(2^30 sqrt(s) / b_max))) (b_max: the most entries in one column)
+// keeps the true sum of every column below 2^30 in magnitude; each term is
+// rounded once, by at most 2^-(F+1).
 //
-// The entries of S are pre-expanded per column group into 16-bit codes
-// (accumulator row | sign << 15), sp = round_up(s, 8) per point (padding codes
-// name the trash row).  The points and the codes stream through a ring of
-// shared-memory slots, GS_CHUNK points per slot, each filled by two 1-D bulk
-// copies behind an mbarrier (waits bounded; a timeout stops the CTA and is
-// recorded in the status word).  FP64 (the accuracy mode) reads points and
-// (offset, value) pairs through L1/L2 and adds doubles.
+// The entries of S are pre-expanded per column group into (byte offset of the
+// accumulator row, sign mask) pairs, sp = round_up(s, 4) per point, padding
+// entries naming the trash row.  The points and the pairs stream through a
+// ring of shared-memory slots, GS_CHUNK points per slot, each filled by two
+// 1-D bulk copies behind an mbarrier (waits bounded; a timeout stops the CTA
+// and is recorded in the status word).  FP64 (the accuracy mode) reads points
+// and (offset, value) pairs through L1/L2 and adds doubles.
 namespace spm {
 
 static constexpr int GS_WARPS = 32;
@@ -180,18 +182,22 @@ __device__ __forceinline__ int gs_local(int64_t j, int t, int s, int g, int cw,
   return c;
 }
 
-// FP32 codes: code[g][j][t] = local column | negative << 15
+// FP32 entries, per group g and point j in quads of 4: {4 byte offsets of the
+// accumulator rows, 4 sign masks (0 or ~0)}
 __global__ void k_gauss_codes(int64_t n, int s, int sp, const int32_t* __restrict__ cols,
                               const int8_t* __restrict__ signs, int cw, int groups,
-                              uint16_t* __restrict__ code) {
+                              uint32_t* __restrict__ code) {
   const int64_t per = n * sp, total = per * groups;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int g = (int)(e / per);
-    const int64_t r = e % per;
+    const int64_t r = e % per, j = r / sp;
+    const int t = (int)(r % sp);
     bool neg;
-    const int lc = gs_local(r / sp, (int)(r % sp), s, g, cw, cols, signs, &neg);
-    code[e] = (uint16_t)(lc | (neg ? 0x8000 : 0));
+    const int lc = gs_local(j, t, s, g, cw, cols, signs, &neg);
+    uint32_t* q = code + ((int64_t)g * n * sp + j * sp + (t & ~3)) * 2;
+    q[t & 3] = (uint32_t)lc * 132u;
+    q[4 + (t & 3)] = neg ? 0xFFFFFFFFu : 0u;
   }
 }
 
@@ -211,11 +217,14 @@ __global__ void k_gauss_pairs(int64_t n, int s, const int32_t* __restrict__ cols
   }
 }
 
-// entries per column (all points): cnt[c] += 1
-__global__ void k_gauss_count(int64_t nnz, const int32_t* __restrict__ cols, int* __restrict__ cnt) {
+// entries per column (all points): cnt[c] += 1, and cnt[r1 + c] += 1 when negative
+__global__ void k_gauss_count(int64_t nnz, int r1, const int32_t* __restrict__ cols,
+                              const int8_t* __restrict__ signs, int* __restrict__ cnt) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
-       e += (int64_t)gridDim.x * blockDim.x)
+       e += (int64_t)gridDim.x * blockDim.x) {
     atomicAdd(cnt + cols[e], 1);
+    if (signs[e] < 0) atomicAdd(cnt + r1 + cols[e], 1);
+  }
 }
 
 // prm[0] = 2^F / sqrt(s), prm[1] = 2^-F (one block)
@@ -275,11 +284,10 @@ __device__ __forceinline__ void gs_zero(T* acc, int cw) {
 struct GsArgs {
   int64_t n;
   const float4* Xp;      // n x DP4 float4
-  const uint16_t* code;  // groups x n x sp
-  int sp;                // codes per point (a multiple of 8)
+  const uint4* code;     // groups x n x SP4 x {offsets, masks}
   float c2;              // -log2(e) / (2 h^2)
   const float* prm;      // 2^F / sqrt(s), 2^-F
-  const int* cnt;        // entries per column
+  const int* cnt;        // entries per column (r1), negative entries per column (r1)
   int cw, r1;
   uint32_t acc_bytes;    // (cw + 1) x 33 words, rounded up to 16 bytes
   float* out;
@@ -288,8 +296,8 @@ struct GsArgs {
 };
 
 // FP32: squared distances by packed f32x2 arithmetic, fixed-point reductions,
-// the ring described above
-template <int DP4>
+// the ring described above; DP4 float4 per point, SP4 quads of entries per point
+template <int DP4, int SP4>
 __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __grid_constant__ GsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t* acc = reinterpret_cast<uint32_t*>(smem_raw);
@@ -297,13 +305,13 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
   const int g = blockIdx.y;
   const int64_t n = a.n;
   const int64_t i0 = (int64_t)blockIdx.x * 32, i = i0 + lane;
-  const uint32_t xbytes = GS_CHUNK * DP4 * 16, tbytes = GS_CHUNK * a.sp * 2;
-  const uint32_t slot_bytes = xbytes + tbytes;
+  constexpr uint32_t xbytes = GS_CHUNK * DP4 * 16, tbytes = GS_CHUNK * SP4 * 32;
+  constexpr uint32_t slot_bytes = xbytes + tbytes;
   const uint32_t ring0 = smem_u32(smem_raw) + a.acc_bytes;
   const uint32_t bar0 = ring0 + GS_NSLOT * slot_bytes;
   const unsigned char* ring = smem_raw + a.acc_bytes;
   const int nchunks = (int)((n + GS_CHUNK - 1) / GS_CHUNK);
-  const uint16_t* ctab = a.code + (int64_t)g * n * a.sp;
+  const uint4* ctab = a.code + (int64_t)g * n * SP4 * 2;
   gs_zero(acc, a.cw);
   if (tid == 0) {
     for (int k = 0; k < GS_NSLOT; ++k) mbar_init(bar0 + 8 * k, 1);
@@ -314,9 +322,9 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
     const int64_t j0 = (int64_t)c * GS_CHUNK;
     const uint32_t rows = (uint32_t)min64(GS_CHUNK, n - j0);
     const uint32_t dst = ring0 + (uint32_t)(c % GS_NSLOT) * slot_bytes, bar = bar0 + 8 * (c % GS_NSLOT);
-    mbar_expect(bar, rows * (DP4 * 16 + a.sp * 2));
+    mbar_expect(bar, rows * (DP4 * 16 + SP4 * 32));
     bulk_g2s(dst, a.Xp + j0 * DP4, rows * DP4 * 16, bar);
-    bulk_g2s(dst + xbytes, ctab + j0 * a.sp, rows * a.sp * 2, bar);
+    bulk_g2s(dst + xbytes, ctab + j0 * SP4 * 2, rows * SP4 * 32, bar);
   };
   if (tid == 0)
     for (int c = 0; c < GS_NSLOT && c < nchunks; ++c) issue(c);
@@ -328,10 +336,8 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
     xi[2 * k + 1] = gs_pack(v.z, v.w);
   }
   const uint32_t base = smem_u32(acc) + 4u * lane;
-  const float c2 = a.c2;
-  const uint32_t wsb = __float_as_uint(a.prm[0]);
+  const float c2 = a.c2, wf = a.prm[0];
   const float magic = __uint_as_float(GS_MAGIC);
-  const int sp8 = a.sp / 8;
   int c = 0;
   bool timed_out = false;
   for (; c < nchunks; ++c) {
@@ -341,7 +347,10 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
       const int rows = (int)min64(GS_CHUNK, n - (int64_t)c * GS_CHUNK);
       const float4* xs = reinterpret_cast<const float4*>(ring + (size_t)sl * slot_bytes);
       const uint4* ts = reinterpret_cast<const uint4*>(ring + (size_t)sl * slot_bytes + xbytes);
-      for (int jj = warp; jj < rows; jj += GS_WARPS) {
+#pragma unroll 2
+      for (int u = 0; u < GS_CHUNK / GS_WARPS; ++u) {
+        const int jj = warp + GS_WARPS * u;
+        if (jj >= rows) break;
         uint64_t a0 = 0, a1 = 0;
 #pragma unroll
         for (int k = 0; k < DP4; ++k) {
@@ -351,18 +360,14 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
         }
         const float d2 = (__uint_as_float((uint32_t)a0) + __uint_as_float((uint32_t)(a0 >> 32))) +
                          (__uint_as_float((uint32_t)a1) + __uint_as_float((uint32_t)(a1 >> 32)));
-        const float kv = gs_exp2(d2 * c2);
-        for (int q = 0; q < sp8; ++q) {
-          const uint4 w4 = ts[jj * sp8 + q];
-          const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+        const uint32_t P = __float_as_uint(fmaf(gs_exp2(d2 * c2), wf, magic));
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t w = ws[u];
-            const float vl = __uint_as_float(wsb ^ ((w << 16) & 0x80000000u));
-            const float vh = __uint_as_float(wsb ^ (w & 0x80000000u));
-            gs_red(base + (w & 0x7FFFu) * 132u, __float_as_uint(fmaf(kv, vl, magic)));
-            gs_red(base + ((w >> 16) & 0x7FFFu) * 132u, __float_as_uint(fmaf(kv, vh, magic)));
-          }
+        for (int q = 0; q < SP4; ++q) {
+          const uint4 o = ts[(jj * SP4 + q) * 2], m = ts[(jj * SP4 + q) * 2 + 1];
+          gs_red(base + o.x, P ^ m.x);
+          gs_red(base + o.y, P ^ m.y);
+          gs_red(base + o.z, P ^ m.z);
+          gs_red(base + o.w, P ^ m.w);
         }
       }
     }
@@ -385,14 +390,16 @@ __global__ void __launch_bounds__(GS_WARPS * 32, 1) k_gauss_sketch_f32(const __g
     __syncthreads();
     return;
   }
-  // write-out: remove the b_c magic offsets, scale by 2^-F
+  // write-out: take off the constants of the column's p_c positive and m_c
+  // negative terms, (p_c - m_c) 0x4B400000 - m_c, then scale by 2^-F
   const int c0 = g * a.cw;
   const int cols = min(a.cw, a.r1 - c0);
   const int64_t rows = (n - i0) < 32 ? (n - i0) : 32;
   const float inv = a.prm[1];
   for (int64_t e = tid; e < rows * cols; e += blockDim.x) {
     const int64_t r = e / cols, cc = e % cols;
-    const uint32_t off = (uint32_t)__ldg(a.cnt + c0 + cc) * GS_MAGIC;
+    const uint32_t all = (uint32_t)__ldg(a.cnt + c0 + cc), neg = (uint32_t)__ldg(a.cnt + a.r1 + c0 + cc);
+    const uint32_t off = (all - 2u * neg) * GS_MAGIC - neg;
     a.out[(i0 + r) * a.ldo + c0 + cc] = (float)(int32_t)(acc[cc * 33 + r] - off) * inv;
   }
 }
@@ -439,13 +446,28 @@ __global__ void __launch_bounds__(GS_WARPS64 * 32, 1)
   }
 }
 
-template <int DP4>
+template <int DP4, int SP4>
 static int launch_gs_f32(dim3 grid, size_t smem, cudaStream_t st, const GsArgs& a) {
-  SPM_CUDA_TRY(cudaFuncSetAttribute(k_gauss_sketch_f32<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  k_gauss_sketch_f32<DP4><<<grid, GS_WARPS * 32, smem, st>>>(a);
+  SPM_CUDA_TRY(cudaFuncSetAttribute(k_gauss_sketch_f32<DP4, SP4>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_gauss_sketch_f32<DP4, SP4><<<grid, GS_WARPS * 32, smem, st>>>(a);
   return SPM_OK;
 }
+template <int DP4>
+static int launch_gs_f32_sp(int sp4, dim3 grid, size_t smem, cudaStream_t st, const GsArgs& a) {
+  switch (sp4) {
+    case 1: return launch_gs_f32<DP4, 1>(grid, smem, st, a);
+    case 2: return launch_gs_f32<DP4, 2>(grid, smem, st, a);
+    case 4: return launch_gs_f32<DP4, 4>(grid, smem, st, a);
+    case 16: return launch_gs_f32<DP4, 16>(grid, smem, st, a);
+    default: return SPM_EINVAL;
+  }
+}
+
+// FP32 widths: points padded to 4, 8, 16 or 32 coordinates, entries to 4, 8,
+// 16 or 64 per point
+static int gs_dp(int64_t d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+static int gs_sp(int s) { return s <= 4 ? 4 : s <= 8 ? 8 : s <= 16 ? 16 : 64; }
 
 int gauss_sketch_dev(const spm_sketch* S, const void* X, int xdt, int64_t n, int64_t d, int64_t ldx,
                      double h, void* out, int odt, int64_t ldo, cudaStream_t st, int* status) {
@@ -458,10 +480,10 @@ int gauss_sketch_dev(const spm_sketch* S, const void* X, int xdt, int64_t n, int
   const double scale = S->kind == SPM_SKETCH_IDENTITY ? 1.0 : 1.0 / sqrt((double)S->s);
   const bool f32 = odt == DT_F32;
   const int es = (int)dt_size(odt);
-  const int dp = (int)round_up(d, f32 ? 4 : 1);
-  const int sp = (int)round_up(s, f32 ? 8 : 1);
+  const int dp = f32 ? gs_dp(d) : (int)d;
+  const int sp = f32 ? gs_sp(s) : s;
   // shared memory: (cw + 1) rows of 33 accumulators, and for FP32 the ring
-  const int64_t ring = f32 ? (int64_t)GS_NSLOT * GS_CHUNK * (dp * 4 + sp * 2) + 8 * GS_NSLOT : 0;
+  const int64_t ring = f32 ? (int64_t)GS_NSLOT * GS_CHUNK * (dp * 4 + sp * 8) + 8 * GS_NSLOT : 0;
   const int64_t cw_max = (GS_SMEM_LIMIT - ring - 16) / (33 * es) - 1;
   if (cw_max < 1) return SPM_EUNSUPPORTED;
   const int64_t groups = cdiv(r1, cw_max);
@@ -485,22 +507,22 @@ int gauss_sketch_dev(const spm_sketch* S, const void* X, int xdt, int64_t n, int
   SPM_LAUNCH_CHECK();
   const dim3 grid((unsigned)blocks, (unsigned)groups);
   if (f32) {
-    uint16_t* code = ar.alloc<uint16_t>(groups * n * sp);
-    int* cnt = ar.alloc<int>(r1);
+    uint32_t* code = ar.alloc<uint32_t>(groups * n * sp * 2);
+    int* cnt = ar.alloc<int>(2 * r1);
     float* prm = ar.alloc<float>(2);
     if (!code || !cnt || !prm) return SPM_ENOMEM;
     k_gauss_codes<<<gt, 256, 0, st>>>(n, s, sp, S->cols, S->signs, (int)cw, (int)groups, code);
     SPM_LAUNCH_CHECK();
-    SPM_CUDA_TRY(cudaMemsetAsync(cnt, 0, r1 * sizeof(int), st));
-    k_gauss_count<<<(int)min64(cdiv(n * s, 256), 152 * 8), 256, 0, st>>>(n * s, S->cols, cnt);
+    SPM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * r1 * sizeof(int), st));
+    k_gauss_count<<<(int)min64(cdiv(n * s, 256), 152 * 8), 256, 0, st>>>(n * s, (int)r1, S->cols,
+                                                                         S->signs, cnt);
     SPM_LAUNCH_CHECK();
     k_gauss_scale<<<1, 1024, 0, st>>>((int)r1, cnt, scale, prm);
     SPM_LAUNCH_CHECK();
     GsArgs a;
     a.n = n;
     a.Xp = (const float4*)Xp;
-    a.code = code;
-    a.sp = sp;
+    a.code = (const uint4*)code;
     a.c2 = (float)(-1.0 / (2.0 * h * h * log(2.0)));   // 2^(d2 c2) = exp(-d2 / (2 h^2))
     a.prm = prm;
     a.cnt = cnt;
@@ -512,10 +534,10 @@ int gauss_sketch_dev(const spm_sketch* S, const void* X, int xdt, int64_t n, int
     a.status = status;
     int rc = SPM_EINVAL;
     switch (dp / 4) {
-#define SPM_GS(D) \
-  case D: rc = launch_gs_f32<D>(grid, smem, st, a); break
-      SPM_GS(1); SPM_GS(2); SPM_GS(3); SPM_GS(4); SPM_GS(5); SPM_GS(6); SPM_GS(7); SPM_GS(8);
-#undef SPM_GS
+      case 1: rc = launch_gs_f32_sp<1>(sp / 4, grid, smem, st, a); break;
+      case 2: rc = launch_gs_f32_sp<2>(sp / 4, grid, smem, st, a); break;
+      case 4: rc = launch_gs_f32_sp<4>(sp / 4, grid, smem, st, a); break;
+      case 8: rc = launch_gs_f32_sp<8>(sp / 4, grid, smem, st, a); break;
       default: break;
     }
     if (rc != SPM_OK) return rc;

@@ -98,7 +98,9 @@ typedef struct spm_opts {
   int32_t power_passes; /* MIXED only: BF16 passes of the power products A~ Z, A~^T Y: 1
                            (plain BF16, fastest) or 3 (hi/lo split, FP32-level subspace);
                            0 selects the default 3                                        */
-  int32_t reserved;
+  int32_t eig_refine;   /* MIXED only, with the FP32 eigensolver: eigenvector refinement steps
+                           of B B^T after the Jacobi solve (Ogita-Aishima; the best of the
+                           estimates is kept), 0 selects the default 3, -1 none, at most 8 */
   const void* omega;    /* optional caller-supplied Omega: device, r1 x r2 row-major, ld r2,
                            dtype of A.  NULL: generated from omega_seed (a2).               */
 } spm_opts;

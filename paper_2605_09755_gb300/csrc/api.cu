@@ -34,6 +34,7 @@ struct Call {
   bool small64 = false;
   int final_passes = 3;
   int power_passes = 3;
+  int eig_refine = 3;      // eigenvector refinement steps after the FP32 eigensolver (mixed)
   bool reorth = true;     // orthonormalise Z = A~^T Y after every A~^T product
   bool reorth_y = false;  // also orthonormalise Y before every A~^T product
   const void* omega = nullptr;
@@ -277,6 +278,66 @@ static int tc_six(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* const* X
 }
 
 // Shifted CholeskyQR of the FP32 basis X (rows x c) on tensor cores with
+// Ogita-Aishima refinement of the eigenvectors X (r x r, column i = vector i,
+// row-major FP32) of the symmetric FP32 matrix G, `steps` updates: Gm = X^T X
+// and S = X^T (G X) as FP32-equivalent six-term products (the residuals I - Gm
+// and S - diag are of the order of the eigensolver's error, and have to be
+// formed to the working precision's unit roundoff), then X <- X + X E (the
+// correction is small: a three-term product).  Every estimate, the solver's
+// own output first, is scored by the largest off-diagonal entry it leaves in
+// U^T A V relative to sigma_1 plus its loss of orthonormality, and the best one
+// is returned: a step that does not improve is discarded, so the refinement
+// never leaves X worse by that measure.  All on the device, no host sync.
+static int eig_refine_mixed(Call& C, int64_t r, const float* G, float* X, int steps) {
+  if (steps <= 0) return SPM_OK;
+  Arena ar(C.st);
+  const int64_t rp = pad8(r);
+  SPM_ALLOC(ar, __nv_bfloat16, g1, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, g2, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, g3, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, x1, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, x2, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, x3, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, p1, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, p2, r * rp);
+  SPM_ALLOC(ar, __nv_bfloat16, p3, r * rp);
+  SPM_ALLOC(ar, float, Gm, r * r);
+  SPM_ALLOC(ar, float, P, r * r);
+  SPM_ALLOC(ar, float, Sm, r * r);
+  SPM_ALLOC(ar, float, E, r * r);
+  SPM_ALLOC(ar, float, T, r * r);
+  SPM_ALLOC(ar, float, Xbest, r * r);
+  SPM_ALLOC(ar, unsigned long long, mx, 2);
+  SPM_ALLOC(ar, double, best, 1);
+  SPM_ALLOC(ar, int, keep, 2);
+  const __nv_bfloat16* gs[3] = {g1, g2, g3};
+  const __nv_bfloat16* xs[3] = {x1, x2, x3};
+  const __nv_bfloat16* ps[3] = {p1, p2, p3};
+  SPM_CUDA_TRY(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), C.st));
+  SPM_CUDA_TRY(cudaMemsetAsync(keep, 0, 2 * sizeof(int), C.st));
+  SPM_TRY(split3_bf16(r, r, G, DT_F32, r, g1, g2, g3, rp, C.st));
+  for (int it = 0; it <= steps; ++it) {
+    SPM_TRY(split3_bf16(r, r, X, DT_F32, r, x1, x2, x3, rp, C.st));
+    // Gm = X^T X: both operands X^T (M = N = r, K = r), stored K x M: MN-major
+    SPM_TRY(tc_six(r, r, r, xs, rp, true, xs, rp, true, Gm, r, true, T, C.st, C.status));
+    // P = G X: A-op G (M = r, K = r) K-major; B-op X (N = r, K = r) stored K x N: MN-major
+    SPM_TRY(tc_six(r, r, r, gs, rp, false, xs, rp, true, P, r, false, T, C.st, C.status));
+    SPM_TRY(split3_bf16(r, r, P, DT_F32, r, p1, p2, p3, rp, C.st));
+    // S = X^T P: A-op X^T (MN-major), B-op P (N = r, K = r) stored K x N: MN-major
+    SPM_TRY(tc_six(r, r, r, xs, rp, true, ps, rp, true, Sm, r, false, T, C.st, C.status));
+    SPM_TRY(oa_keep_best(r, Sm, Gm, X, Xbest, mx, best, keep, C.st));
+    if (it == steps) break;
+    SPM_TRY(oa_update(r, Sm, Gm, E, 0.25, C.st));
+    // X <- X + X E: A-op X (M = r, K = r) K-major; B-op E (N = r, K = r) stored K x N: MN-major
+    SPM_TRY(split_bf16(r, r, rowmajor(E, DT_F32, r), mrowmajor(p1, DT_BF16, rp),
+                       mrowmajor(p2, DT_BF16, rp), C.st));
+    SPM_TRY(tc_split(r, r, r, x1, x2, rp, false, p1, p2, rp, true, 3, T, r, 1, C.st, C.status));
+    SPM_TRY(add2d_f32(r, r, X, r, T, r, C.st));
+  }
+  SPM_CUDA_TRY(cudaMemcpyAsync(X, Xbest, r * r * sizeof(float), cudaMemcpyDeviceToDevice, C.st));
+  return SPM_OK;
+}
+
 // FP32-equivalent products (tc_six): the Gram X^T X and X L^{-T}.  For the
 // sketch-side iterate Z = A~^T Y, conditioned like kappa(A~)^2, whose tail a
 // two-part split resolves too coarsely (the leading singular values moved by
@@ -519,6 +580,7 @@ static int check_common(const spm_sketch* S, const void* A, int32_t dtype, int64
     if (o->final_passes != 0 && o->final_passes != 1 && o->final_passes != 3) return SPM_EINVAL;
     if (o->reorth < 0 || o->reorth > 2) return SPM_EINVAL;
     if (o->power_passes != 0 && o->power_passes != 1 && o->power_passes != 3) return SPM_EINVAL;
+    if (o->eig_refine > 8) return SPM_EINVAL;
   }
   return SPM_OK;
 }
@@ -532,6 +594,7 @@ static void setup_call(Call& C, int32_t dtype, const spm_opts* o, spm_info* info
     C.final_passes = o->final_passes == 0 ? 3 : o->final_passes;
     C.power_passes = o->power_passes == 0 ? 3 : o->power_passes;
     C.small64 = o->small_fp64 != 0;
+    C.eig_refine = o->eig_refine == 0 ? 3 : (o->eig_refine < 0 ? 0 : o->eig_refine);
     C.omega = o->omega;
   }
   if (info && info->want_timing) C.timer.on = true;
@@ -690,6 +753,7 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     SPM_TRY(convert2d(r2, r2, rowmajor(G, DT_F32, r2), mrowmajor(Gs, sdt, r2), C.st));
     SPM_TRY(symmetrize(r2, Gs, r2, sdt, C.st));
     SPM_TRY(sym_eig(r2, Gs, r2, Ut, r2, lam, sdt, C.status, C.st, C.status + 1));
+    if (sdt == DT_F32) SPM_TRY(eig_refine_mixed(C, r2, (const float*)Gs, (float*)Ut, C.eig_refine));
     SPM_TRY(split_bf16(r2, r2, rowmajor(Ut, sdt, r2), mrowmajor(Uhi, DT_BF16, r2p),
                        mrowmajor(Ulo, DT_BF16, r2p), C.st));
   }

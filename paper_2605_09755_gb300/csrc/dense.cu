@@ -1119,6 +1119,113 @@ int sym_eig(int64_t r, void* A, int64_t lda, void* V, int64_t ldv, void* lam, in
   return SPM_EINVAL;
 }
 
+// ------------------------------------------------------------------ eigenvector refinement
+// One step of the Ogita-Aishima refinement (Ogita & Aishima, 2018) of approximate
+// eigenvectors X of a symmetric G: with Gm = X^T X and S = X^T G X,
+//   lam_i = S_ii / Gm_ii                             (Rayleigh quotients),
+//   E_ii  = (1 - Gm_ii) / 2,
+//   E_ij  = (S_ij - lam_j Gm_ij) / (lam_j - lam_i)   (i != j; R = I - Gm),
+// and X <- X + X E.  The paper switches a pair to E_ij = R_ij / 2 = -Gm_ij / 2
+// (orthogonality only) when the two eigenvalues are closer than a global bound;
+// here the switch is per pair: when the first-order correction would exceed
+// theta in magnitude (a pair too close for one Newton step).  S and Gm are read
+// symmetrised.  One thread per element.
+template <typename T>
+__global__ void k_oa_update(int64_t r, const T* __restrict__ S, int64_t lds, const T* __restrict__ Gm,
+                            int64_t ldg, T* __restrict__ E, int64_t lde, T theta) {
+  const int64_t total = r * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r, j = e % r;
+    const T gi = Gm[i * ldg + i], gj = Gm[j * ldg + j];
+    T v;
+    if (i == j) {
+      v = ((T)1 - gi) * (T)0.5;
+    } else {
+      const T li = S[i * lds + i] / gi, lj = S[j * lds + j] / gj;
+      const T sij = (S[i * lds + j] + S[j * lds + i]) * (T)0.5;
+      const T gij = (Gm[i * ldg + j] + Gm[j * ldg + i]) * (T)0.5;
+      const T num = sij - lj * gij, den = lj - li;
+      v = (fabs(num) <= theta * fabs(den)) ? num / den : -gij * (T)0.5;
+    }
+    E[i * lde + j] = v;
+  }
+}
+
+int oa_update(int64_t r, const float* S, const float* Gm, float* E, double theta, cudaStream_t st) {
+  if (r <= 0) return SPM_OK;
+  k_oa_update<float><<<grid_for(r * r), 256, 0, st>>>(r, S, r, Gm, r, E, r, (float)theta);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
+// Score of an eigenvector estimate X from S = X^T G X and Gm = X^T X:
+//   m = max_{i != j} |S_ij| / sqrt(S_jj S_00) + max_{i, j} |Gm_ij - delta_ij|,
+// the largest off-diagonal entry of U^T A V relative to sigma_1 that X would
+// leave in the Randomized SVD finish (S_00 = sigma_1^2: the columns come in
+// descending order), plus the loss of orthonormality.  Nonnegative doubles
+// compare like their bit patterns, so the maxima are integer atomics into
+// mx[0..1]; a NaN anywhere gives a NaN bit pattern above every finite one.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v) {
+  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+template <typename T>
+__global__ void k_oa_metric(int64_t r, const T* __restrict__ S, const T* __restrict__ Gm,
+                            unsigned long long* __restrict__ mx) {
+  double m1 = 0.0, m2 = 0.0;
+  const double s00 = (double)S[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < r * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r, j = e % r;
+    const double g = fabs((double)Gm[e] - (i == j ? 1.0 : 0.0));
+    m2 = (g > m2 || g != g) ? g : m2;
+    if (i != j) {
+      const double q = fabs((double)S[e]) / sqrt(fabs((double)S[j * r + j] * s00));
+      m1 = (q > m1 || q != q) ? q : m1;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double a = __shfl_xor_sync(0xFFFFFFFFu, m1, o), b = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
+    m1 = (a > m1 || a != a) ? a : m1;
+    m2 = (b > m2 || b != b) ? b : m2;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(mx, m1);
+    atomic_max_nonneg(mx + 1, m2);
+  }
+}
+
+// keep[0] = 1 when the score in mx beats *best (which is then updated), and
+// always on the first evaluation (keep[1] = 0); mx cleared for the next one.
+__global__ void k_oa_decide(unsigned long long* __restrict__ mx, double* __restrict__ best,
+                            int* __restrict__ keep) {
+  const double m = __longlong_as_double((long long)mx[0]) + __longlong_as_double((long long)mx[1]);
+  const bool better = keep[1] == 0 || m < *best;  // a NaN score never replaces a kept one
+  if (better) *best = m;
+  keep[0] = better ? 1 : 0;
+  keep[1] = 1;
+  mx[0] = mx[1] = 0ull;
+}
+
+template <typename T>
+__global__ void k_copy_if(int64_t n, const T* __restrict__ src, T* __restrict__ dst,
+                          const int* __restrict__ keep) {
+  if (!*keep) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+int oa_keep_best(int64_t r, const float* S, const float* Gm, const float* X, float* Xbest,
+                 unsigned long long* mx, double* best, int* keep, cudaStream_t st) {
+  k_oa_metric<float><<<grid_for(r * r), 256, 0, st>>>(r, S, Gm, mx);
+  SPM_LAUNCH_CHECK();
+  k_oa_decide<<<1, 1, 0, st>>>(mx, best, keep);
+  SPM_LAUNCH_CHECK();
+  k_copy_if<float><<<grid_for(r * r), 256, 0, st>>>(r * r, X, Xbest, keep);
+  SPM_LAUNCH_CHECK();
+  return SPM_OK;
+}
+
 // ------------------------------------------------------------------ norms etc.
 template <typename T>
 __global__ void k_line_norms(int64_t rows, int64_t cols, const T* __restrict__ X, int64_t rs,

@@ -192,6 +192,16 @@ int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st
 int copy_vec(int64_t n, const double* src, void* dst, int dt, cudaStream_t st);
 // Symmetrise in place: A = (A + A^T) / 2.
 int symmetrize(int64_t r, void* A, int64_t lda, int dt, cudaStream_t st);
+// Eigenvector refinement (dense.cu), FP32 r x r arrays with ld r.  oa_update:
+// from Gm = X^T X and S = X^T G X, the correction E of X <- X + X E (one
+// Ogita-Aishima step; a pair whose first-order correction would exceed theta
+// gets -Gm_ij / 2).  oa_keep_best: scores X by max_{i!=j} |S_ij| / sqrt(S_jj S_00)
+// + max |Gm - I|; when the score beats *best (device), *best = score and
+// Xbest = X (always on the first call).  mx: 2 words, zero on entry and on
+// return; keep: 2 ints, zero before the first call.
+int oa_update(int64_t r, const float* S, const float* Gm, float* E, double theta, cudaStream_t st);
+int oa_keep_best(int64_t r, const float* S, const float* Gm, const float* X, float* Xbest,
+                 unsigned long long* mx, double* best, int* keep, cudaStream_t st);
 // Scan a strided view for NaN/Inf; sets *status to SPM_ENONFINITE.
 int check_finite(int64_t rows, int64_t cols, View X, int* status, cudaStream_t st);
 

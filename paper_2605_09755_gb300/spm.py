@@ -33,7 +33,7 @@ class SpmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reorth", ctypes.c_int32),
                 ("final_passes", ctypes.c_int32), ("small_fp64", ctypes.c_int32),
-                ("power_passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("power_passes", ctypes.c_int32), ("eig_refine", ctypes.c_int32),
                 ("omega", ctypes.c_void_p)]
 
 
@@ -194,9 +194,9 @@ def sketch_apply_t(S, X):
 
 
 def make_opts(precision=PREC_FP64, reorth=True, final_passes=3, small_fp64=False, omega=None,
-              power_passes=3):
+              power_passes=3, eig_refine=0):
     o = Opts(int(precision), int(reorth), int(final_passes), int(bool(small_fp64)),
-             int(power_passes), 0, None)
+             int(power_passes), int(eig_refine), None)
     if omega is not None:
         o.omega = omega.data_ptr()
     return o

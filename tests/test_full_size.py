@@ -9,10 +9,11 @@ noise.  The oracle cannot run the whole problem in seconds, so:
     scale error is of order 1, the FP32 sums' rounding about u32 sqrt(n) / 5 ~ 2e-6);
   * properties of the mixed RandSVD that hold at any size: sigma positive and
     descending; U and V orthonormal (||U^T U - I||_F <= k u32 sqrt(m) = 2e-2, the
-    single-precision inner products over m rows); U^T A V = diag(sigma) up to
-    what the FP32 Jacobi eigensolver's stopping rule leaves off the diagonal
-    of U~^T (B B^T) U~ (Frobenius mass <= 4 n_pad u32 ||B B^T||_F, divided by
-    sigma_k; observed 1e-4 to 6e-4 sigma_1); the Pythagorean identity of
+    single-precision inner products over m rows); U^T A V = diag(sigma): off the
+    diagonal up to what the FP32 eigensolver and its refinement leave in
+    U~^T (B B^T) U~ (<= 1e-5 sigma_1 on the sparse and dense families; SRHT the
+    solver's own bound, Frobenius mass <= 4 n_pad u32 ||B B^T||_F / sigma_k), on
+    the diagonal within 2e-4 sigma_1 (the projection's precision); the Pythagorean identity of
     a projection, ||A - U S V^T||_F^2 = ||A||_F^2 - sum sigma_i^2 (within 1e-3);
   * the three sketch families at the same r1 reach residuals within 1% of each
     other (Lemma 3.2: each is a regularized spectral approximation; here the
@@ -85,20 +86,31 @@ def test_full_size_sketch_rows_and_factors(spm, big):
         eye = torch.eye(K, device="cuda", dtype=torch.float64)
         assert float(torch.linalg.norm(U.double().T @ U.double() - eye)) <= 2e-2, name
         assert float(torch.linalg.norm(Vt.double() @ Vt.double().T - eye)) <= 2e-2, name
-        UtAV = U.double().T @ (A @ Vt.T).double()
-        dev_uav = float(torch.max(torch.abs(UtAV - torch.diag(s)))) / float(s[0])
-        del UtAV
+        D = U.double().T @ (A @ Vt.T).double() - torch.diag(s)
+        dev_diag = float(torch.max(torch.abs(torch.diag(D)))) / float(s[0])
+        dev_uav = float(torch.max(torch.abs(D - torch.diag(torch.diag(D))))) / float(s[0])
+        del D
         r2 = _residual2(A, U, sg, Vt)
         pyth = abs(r2 - (fro2 - float((s ** 2).sum()))) / fro2
-        print(f"{name}: max|U^T A V - diag(sigma)| / sigma_1 = {dev_uav:.3g}, "
+        print(f"{name}: off-diagonal max|U^T A V| / sigma_1 = {dev_uav:.3g}, diagonal "
+              f"max|u_i^T A v_i - sigma_i| / sigma_1 = {dev_diag:.3g}, "
               f"Pythagoras {pyth:.3g}, residual {np.sqrt(r2):.6g}, sweeps {info['eig_sweeps']}",
               flush=True)
-        # U^T A V - diag(sigma) is, to first order, the off-diagonal part of
-        # U~^T G U~ (G = B B^T) scaled by 1/sigma_j; the FP32 Jacobi solver stops
-        # once that part's Frobenius mass is at most 4 n_pad u32 ||G||_F
-        # (n_pad <= 2 k), and ||G||_F = sqrt(sum sigma_i^4)
+        # The off-diagonal of U^T A V is, to first order, that of U~^T G U~
+        # (G = B B^T) scaled by 1/sigma_j.  The FP32 Jacobi solver stops once its
+        # Frobenius mass is at most 4 n_pad u32 ||G||_F (n_pad <= 2 k, ||G||_F =
+        # sqrt(sum sigma_i^4)); the refinement steps that follow keep an estimate
+        # only when it lowers the largest entry, and on the sparse and dense
+        # families bring it to ~1e-6 sigma_1 (bound 1e-5).  The SRHT run's
+        # estimates after three steps do not beat the solver's own within the
+        # noise floor's near-equal singular values: the solver's bound applies.
         tol = 4 * (2 * K) * 2.0 ** -24 * float(torch.sqrt((s ** 4).sum())) / float(s[-1])
         assert dev_uav * float(s[0]) <= tol, (name, dev_uav, tol)
+        if name in ("sparse", "dense"):
+            assert dev_uav <= 1e-5, (name, dev_uav)
+        # the diagonal: sigma_i against u_i^T A v_i, the three-pass projection's
+        # accuracy (sigma parity 1e-4 in the mixed mode)
+        assert dev_diag <= 2e-4, (name, dev_diag)
         assert pyth <= 1e-3, name
         res2[name] = r2
         del U, sg, Vt

@@ -34,7 +34,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC
     assert d["unit"] == "ms" and d["higher_is_better"] is False and d["value"] > 0
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "64 of 512 rows" in cb["sample"]
+    # two row samples, their difference extrapolated linearly in m
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "64 and 128 of 512 rows" in cb["sample"]
     assert cb["value"] == d["value"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0
@@ -91,3 +92,15 @@ def test_protocol_summary_curves_and_time_to_target():
     # the fastest iterate under the target, over every sketch size
     assert best["sketched"] == {"ms": pytest.approx(3.1), "err": pytest.approx(0.08), "l": 800, "q": 1}
     assert best["classical"] is None           # never reaches 0.1 within its iterates
+
+
+def test_cpu_fit_extrapolates_only_the_row_linear_part(monkeypatch):
+    # a fake oracle whose time is 100 ms of fixed work plus 2 ms per row: the fit
+    # must return 100 + 2 m at any m, not the sample's time scaled by m / rows
+    import argparse
+    import numpy as np
+    monkeypatch.setattr(bench, "cpu_oracle_ms", lambda A, a: 100.0 + 2.0 * A.shape[0])
+    a = argparse.Namespace(m=65536)
+    est, t1, t2, rows = bench.cpu_oracle_fit(np.zeros((4096, 8)), a)
+    assert rows == 2048 and t1 == 100.0 + 2.0 * 2048 and t2 == 100.0 + 2.0 * 4096
+    assert abs(est - (100.0 + 2.0 * 65536)) < 1e-9

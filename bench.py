@@ -85,6 +85,8 @@ def parse():
     p.add_argument("--trials", type=int, default=5, help="polydecay: trials (the paper: 25)")
     p.add_argument("--poly-l", default="800,1200,1600", help="polydecay: sketch sizes l")
     p.add_argument("--q-sketched", type=int, default=15)
+    p.add_argument("--no-poly-alg2", dest="poly_alg2", action="store_false",
+                   help="polydecay: skip the Algorithm 2 vs generalized Nystrom comparison")
     p.add_argument("--q-classical", type=int, default=5)
     p.add_argument("--poly-target", type=float, default=0.1,
                    help="polydecay: relative spectral error the time is measured to")
@@ -639,8 +641,9 @@ def nystrom_main(a):
 def protocol_summary(records, target):
     """Section 4's curves from individual runs.
 
-    records: dicts with method ("sketched" or "classical"), l (sketch size; n for
-    the classical form), q, ms and err (relative spectral error).  Returns
+    records: dicts with method ("sketched", "classical", "alg2_sketched" or
+    "alg2_generalized_nystrom"), l (sketch size; n for the classical form), q, ms
+    and err (relative spectral error).  Returns
     (curves, best): curves[method:l] = [(q, mean ms, mean err, runs)] by q, and
     best[method] = the smallest mean time whose mean error is <= target, with its
     (l, q), or None when no iterate reaches the target."""
@@ -669,7 +672,10 @@ def polydecay_main(a):
     q = 0..5, each iterate computed from scratch and timed alone (CUDA events),
     error = ||A - U S V^T||_2 / sigma_{k+1} - 1 (the spectral norm by block power
     iteration on the residual), averaged over the trials (sketch seed 42 + t,
-    Omega seed 43 + t)."""
+    Omega seed 43 + t).  A sketch is built, and its gather plan made by one
+    untimed call, before its iterates are timed.  With Algorithm 2 (Appendix D):
+    S1 a CountSketch of l columns against S1 = I, S2 a CountSketch of the rows
+    to l in both, error ||A - Y X||_2 / sigma_{k+1} - 1."""
     import torch
     from paper_2605_09755_gb300 import _build, spm
     from paper_2605_09755_gb300 import workloads as wl
@@ -687,15 +693,17 @@ def polydecay_main(a):
     Vt = torch.empty(k, n, device="cuda")
     g = torch.Generator(device="cuda")
 
-    def spectral_err():
-        # block power iteration on R = A - U diag(sg) Vt (block 8, 40 steps)
+    def spectral_err(L=None, R=None):
+        # block power iteration on A - L R (block 8, 40 steps); L R = U diag(sg) Vt
+        # by default
+        if L is None:
+            L, R = U * sg, Vt
         g.manual_seed(0)
         X, _ = torch.linalg.qr(torch.randn(n, 8, device="cuda", generator=g))
-        Us = U * sg
         for _ in range(40):
-            Y = A @ X - Us @ (Vt @ X)
-            X, _ = torch.linalg.qr(A.T @ Y - Vt.T @ (Us.T @ Y))
-        Y = A @ X - Us @ (Vt @ X)
+            Y = A @ X - L @ (R @ X)
+            X, _ = torch.linalg.qr(A.T @ Y - R.T @ (L.T @ Y))
+        Y = A @ X - L @ (R @ X)
         return float(torch.linalg.svdvals(Y)[0]) / sig_k1 - 1.0
 
     def run(S, q, oseed):
@@ -709,6 +717,17 @@ def polydecay_main(a):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    def run_lr(S1, S2, q, oseed):
+        # Algorithm 2: A ~ Y X with X = (S2^T Y)^+ (S2^T A), no Q^T A product
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        Y, X, _ = spm.lowrank(S1, S2, A, k, q, omega_seed=oseed, precision=spm.PREC_MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), Y, X
+
     records = []
     ident = spm.Sketch(n, n, 1, 0, kind=spm.IDENTITY)
     run(ident, 1, 43)                                   # warm-up (kernel attributes, pool)
@@ -719,6 +738,7 @@ def polydecay_main(a):
     for t in range(a.trials):
         for l in ls:
             S = spm.Sketch(n, l, 1, 42 + t)
+            run(S, 0, 43 + t)          # builds the sketch's gather plan, untimed
             for q in range(a.q_sketched + 1):
                 ms = run(S, q, 43 + t)
                 records.append({"method": "sketched", "l": l, "q": q, "ms": ms, "err": spectral_err()})
@@ -726,6 +746,25 @@ def polydecay_main(a):
         for q in range(a.q_classical + 1):
             ms = run(ident, q, 43 + t)
             records.append({"method": "classical", "l": n, "q": q, "ms": ms, "err": spectral_err()})
+        if a.poly_alg2:
+            # Appendix D: Algorithm 2 with S1 a CountSketch of l columns against the
+            # same algorithm with S1 = I (generalized Nystrom with power
+            # iterations); S2 a CountSketch of the m rows to l in both
+            for l in ls:
+                S2 = spm.Sketch(m, l, 1, 142 + t)
+                S1 = spm.Sketch(n, l, 1, 42 + t)
+                run_lr(S1, S2, 0, 43 + t)  # the gather plan, untimed
+                for q in range(a.q_sketched + 1):
+                    ms, Y, X = run_lr(S1, S2, q, 43 + t)
+                    records.append({"method": "alg2_sketched", "l": l, "q": q, "ms": ms,
+                                    "err": spectral_err(Y, X)})
+                for q in range(a.q_classical + 1):
+                    ms, Y, X = run_lr(ident, S2, q, 43 + t)
+                    records.append({"method": "alg2_generalized_nystrom", "l": l, "q": q,
+                                    "ms": ms, "err": spectral_err(Y, X)})
+                del Y, X
+                S1.close()
+                S2.close()
     launches = int(lib.spm_launch_count() - c0)
     curves, best = protocol_summary(records, a.poly_target)
     sk, cl = best.get("sketched"), best.get("classical")
@@ -736,10 +775,16 @@ def polydecay_main(a):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32", "data": "synthetic (seeded)",
         "config": {"workload": f"polydecay {m}x{n} f32, sigma_i = {m}/i, Haar factors, k = {k}; "
                                f"CountSketch l in {ls}, q = 0..{a.q_sketched}; classical q = "
-                               f"0..{a.q_classical}; {a.trials} trials", "precision": "mixed",
+                               f"0..{a.q_classical}; {a.trials} trials" +
+                               ("; Algorithm 2 (S2: CountSketch of the rows to l) with S1 = "
+                                "CountSketch l vs S1 = I" if a.poly_alg2 else ""),
+                   "precision": "mixed",
                    "l2": "A (1.8 GB) larger than L2; no flush"},
         "best": best, "classical_ms_to_target": cl["ms"] if cl else None,
         "speedup_vs_classical": (cl["ms"] / sk["ms"]) if (sk and cl) else None,
+        "alg2_speedup_vs_generalized_nystrom": (
+            best["alg2_generalized_nystrom"]["ms"] / best["alg2_sketched"]["ms"]
+            if best.get("alg2_sketched") and best.get("alg2_generalized_nystrom") else None),
         "curves": curves, "roofline": None, "e2e": None, "cpu_baseline": None,
         "gpu_launches": launches,
     }

@@ -100,6 +100,11 @@ def parse():
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--nstreams", type=int, default=16)
     p.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"])
+    p.add_argument("--batch-auto", action="store_true",
+                   help="batched: spm_rsvd_batched_auto (selector network + residual judge) "
+                        "at --target instead of the fixed (q, r1)")
+    p.add_argument("--target", type=float, default=1.05,
+                   help="batched --batch-auto: residual ratio target")
     return p.parse_args()
 
 
@@ -233,6 +238,137 @@ def residual(A, U, sg, Vt, chunk=4096):
         R = A[i:i + chunk] - Us[i:i + chunk] @ Vs
         tot += float((R.double() ** 2).sum())
     return tot ** 0.5
+
+
+def batched_auto_main(a):
+    """The same 512 problems through spm_rsvd_batched_auto at a residual target
+    (default 1.05 x the Eckart-Young optimum): the selector network picks (q, r1)
+    per problem from its q = 0 probe, the batch runs, and the residual judge adds
+    power steps (or an FP32 re-run) where the estimate has not settled.  One step =
+    one spm_rsvd_batched_auto call (eager: it reads the predictions and the judge's
+    estimates on the host).  Reported: time, the share of problems within the
+    target, the ratio distribution, against the fixed (q = 2, r1 = 2k) path and the
+    network's picks without the judge."""
+    import numpy as np
+    import torch
+    from paper_2605_09755_gb300 import _build, spm
+    from paper_2605_09755_gb300 import selector as sel
+    from paper_2605_09755_gb300 import workloads as wl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    lib = spm.lib()
+    params = sel.load_params()
+    specs = wl.batch_specs(a.batch)
+    probs, opts = [], []
+    for sp in specs:
+        A, sig = sel.make_matrix(sp)
+        probs.append(dict(A=A, k=sp["k"], seed=42))
+        opts.append(float(np.sqrt(np.sum(np.sort(np.asarray(sig))[::-1][sp["k"]:] ** 2))))
+    torch.cuda.synchronize()
+    prec = {"mixed": spm.PREC_MIXED, "fp32": spm.PREC_FP32}[a.batch_precision]
+
+    def ratios(batch):
+        out = []
+        for p, opt, (U, sg, Vt) in zip(probs, opts, batch.outputs):
+            R = p["A"] - (U * sg) @ Vt
+            out.append(float(torch.linalg.norm(R.double())) / opt if opt > 0 else 1.0)
+        return np.array(out)
+
+    # problems whose optimal residual is at least 1.4% of |A|_F: there the judge's
+    # estimate resolves the target's margin; below it the estimate is too coarse,
+    # and the optimum itself approaches the working precision's floor
+    fro = [float(torch.linalg.norm(p["A"].double())) for p in probs]
+    judgeable = np.array([o >= 0.014 * f for o, f in zip(opts, fro)])
+
+    def stats(r):
+        out = {"share_within_target": float(np.mean(r <= a.target)), "median": float(np.median(r)),
+               "p90": float(np.quantile(r, 0.9)), "max": float(np.max(r))}
+        if judgeable.any():
+            out["share_within_target_opt_ge_1.4pct"] = float(np.mean(r[judgeable] <= a.target))
+            out["median_opt_ge_1.4pct"] = float(np.median(r[judgeable]))
+        if (~judgeable).any():
+            out["median_opt_lt_1.4pct"] = float(np.median(r[~judgeable]))
+        return out
+
+    batch = spm.Batch(probs, precision=prec, nstreams=a.nstreams)
+    for _ in range(a.warmup):
+        picks = batch.run_auto(a.target, params)
+    torch.cuda.synchronize()
+    c0 = lib.spm_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        picks = batch.run_auto(a.target, params)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = int(lib.spm_launch_count() - c0)
+    batch.check_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    judged = ratios(batch)
+    kept = batch.item_params()
+    # the network's picks alone (no judge), and the fixed path, for comparison
+    pick_probs = [dict(A=p["A"], k=p["k"], seed=42, q=q, r1=min(c * p["k"], p["A"].shape[1]),
+                       s=min(8, min(c * p["k"], p["A"].shape[1]))) for p, (q, c) in zip(probs, picks)]
+    pb = spm.Batch(pick_probs, precision=prec, nstreams=a.nstreams)
+    pb.run()
+    torch.cuda.synchronize()
+    e0.record()
+    pb.run()
+    e1.record()
+    torch.cuda.synchronize()
+    pick_ms = e0.elapsed_time(e1)
+    picked = ratios(pb)
+    del pb
+    fixed_probs = [dict(A=p["A"], k=p["k"], seed=42, q=2, r1=min(2 * p["k"], p["A"].shape[1]),
+                        s=min(8, min(2 * p["k"], p["A"].shape[1]))) for p in probs]
+    fb = spm.Batch(fixed_probs, precision=prec, nstreams=a.nstreams)
+    fb.run()
+    torch.cuda.synchronize()
+    e0.record()
+    fb.run()
+    e1.record()
+    torch.cuda.synchronize()
+    fixed_ms = e0.elapsed_time(e1)
+    fixed = ratios(fb)
+    del fb
+    a_bytes = sum(p["A"].numel() * 4 for p in probs)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach = 2.0 * a_bytes / (pick_ms * 1e-3) / 1e9
+    line = {
+        "metric": f"time to rank-k approximations within {a.target:g} x optimal (batched, "
+                  f"selector + residual judge)", "value": ms, "unit": "ms", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32" if a.batch_precision == "mixed" else "f32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"{len(probs)} uneven dense problems (m in [512, 8192], n in "
+                               f"[256, 4096], k in [16, 256], decay i^-alpha or exp(-i/tau)); "
+                               f"spm_rsvd_batched_auto at target {a.target:g}",
+                   "precision": a.batch_precision, "nstreams": a.nstreams},
+        "accuracy": {"judged": stats(judged), "network_pick_only": stats(picked),
+                     "fixed_q2_r1_2k": stats(fixed)},
+        "problems_opt_ge_1.4pct_of_fro": int(judgeable.sum()),
+        "q_raised_by_judge": int(sum(1 for (qk, _, _), (q, _) in zip(kept, picks) if qk > q)),
+        "r1_raised_by_judge": int(sum(1 for (_, rk, _), (q, c), p in zip(kept, picks, probs)
+                                      if rk > min(c * p["k"], p["A"].shape[1]))),
+        "network_pick_only_ms": pick_ms, "fixed_ms": fixed_ms,
+        "roofline": {"kernel": "whole batch at the network's picks (two passes over every A: "
+                               "A S and Q^T A)", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
+        "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def batched_main(a):
@@ -797,7 +933,10 @@ def main():
         reference_main(a)
         return
     if a.workload == "batched":
-        batched_main(a)
+        if a.batch_auto:
+            batched_auto_main(a)
+        else:
+            batched_main(a)
         return
     if a.workload == "csr":
         csr_main(a)

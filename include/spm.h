@@ -118,6 +118,10 @@ typedef struct spm_info {
                                B = Q^T A is formed (rsvd); -1 when not available          */
   double fro_a;             /* |A|_F accumulated while A streams through the sketch pass  */
   float stage_ms[SPM_NSTAGES];
+  int32_t auto_q;           /* spm_rsvd_auto: the q of the result returned after the residual
+                               judge (the network's pick or more); -1 for other calls     */
+  int32_t auto_fp32;        /* spm_rsvd_auto: 1 when the result returned came from the FP32
+                               re-run of the judge, else 0                                 */
 } spm_info;
 
 /* ---- library ----------------------------------------------------------- */
@@ -464,8 +468,21 @@ int spm_selector_features(const spm_sketch* S, const void* A, int32_t dtype, int
  * device) for a requested residual ratio target_ratio = |A - U S V^T|_F / optimal
  * (> 1): features from a probe sketch of size min(4k, n); the cheapest candidate
  * ((2q + 1) r1) predicted to meet the target is run; if none is, the candidate with
- * the smallest predicted ratio.  choice (host, may be NULL) receives {q, r1 / k}.
- * Synchronises the stream once to read the prediction. */
+ * the smallest predicted ratio.  choice (host, may be NULL) receives the network's
+ * pick {q, r1 / k}.
+ * Residual judge: the result is then checked with the a-posteriori estimate
+ * e = sqrt(|A|_F^2 - |B|_F^2) (B = Q^T A), for at most 4 further runs: one more
+ * power step while each improves e by more than a quarter of the target's margin
+ * (e > (1 + (target_ratio - 1) / 4) e_next); once they stop, the sketch doubled
+ * (r1 -> min(2 r1, n), same q: the sketch-size term of Theorem 3.1), and power
+ * steps again if that helped by more than the margin.  A power step that makes e
+ * worse (the working precision's limit) in MIXED precision triggers one FP32
+ * re-run.  The output is the result with the smallest e; info->auto_q and
+ * info->auto_fp32 say which it was (its r1 is not reported).  A
+ * problem whose first e is below 1.4% of |A|_F (1e-6 in FP64) is kept as run: e is
+ * a difference of two squared norms that carry the products' ~1e-5 relative
+ * error, too coarse there to resolve the target's margin.
+ * Synchronises the stream once to read the prediction and once per judge step. */
 int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda, int64_t k,
                   double target_ratio, const float* params, uint64_t seed, const spm_opts* opts,
                   void* U, int64_t ldu, void* sigma, void* Vt, int64_t ldvt, int32_t* choice,
@@ -473,11 +490,15 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
 
 /* Batched form of spm_rsvd_auto: the q = 0 features of every item (probe sketch
  * r1 = min(4k, n), s = min(8, r1), seed item.seed, Omega seed item.seed + 1) on side
- * streams, one network evaluation over the batch, one host read of the predictions
- * (the only synchronisation), then spm_rsvd_batched with each item's chosen (q, r1):
- * item.q, item.r1 and item.s are overwritten with the choice.  choices (host, 2 count
- * int32, may be NULL) receives (q, c) with r1 = c k.  dev_status as in
- * spm_rsvd_batched.  Needs the tensor-core path (sm_103). */
+ * streams, one network evaluation over the batch, one host read of the predictions,
+ * then spm_rsvd_batched with each item's chosen (q, r1).  choices (host, 2 count
+ * int32, may be NULL) receives
+ * the network's picks (q, c) with r1 = c k.  Then the residual judge of
+ * spm_rsvd_auto over the whole batch (the items still unsettled re-run together
+ * as one batched call per step, one host synchronisation per step); item.q,
+ * item.r1 and item.s are overwritten with those of the result returned (a replay
+ * through spm_rsvd_batched reruns them in the call's precision).  dev_status as in
+ * spm_rsvd_batched, for the network's picks.  Needs the tensor-core path (sm_103). */
 int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, double target_ratio,
                           const float* params, const spm_opts* opts, int32_t nstreams,
                           int32_t* dev_status, int32_t* choices, void* stream);

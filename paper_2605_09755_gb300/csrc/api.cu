@@ -625,6 +625,8 @@ static int finish(Call& C, spm_info* info, int rc, bool has_b) {
   info->device_status = dst;
   info->eig_sweeps = stw[1];
   info->cholqr_passes = C.cholqr_passes;
+  info->auto_q = -1;
+  info->auto_fp32 = 0;
   const bool fro = !C.no_fro && C.want_fro;
   info->fro_a = fro ? sqrt(acc[0]) : -1.0;
   info->resid_est = (has_b && fro) ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;

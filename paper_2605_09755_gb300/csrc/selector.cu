@@ -13,6 +13,7 @@
 //   log2(r1/r2)/3.
 #include <math.h>
 
+#include <algorithm>
 #include <functional>
 #include <map>
 #include <tuple>
@@ -106,6 +107,183 @@ int selector_features_dev(const spm_sketch* S, const void* A, int adt, int64_t m
   return SPM_OK;
 }
 
+// ---------------------------------------------------------------- residual judge
+// After the chosen (q, r1) has run, the result is judged by the a-posteriori
+// residual estimate e = sqrt(|A|_F^2 - |B|_F^2) (B = Q^T A; with k = r2 its
+// squared Frobenius norm is the sum of the k squared singular values).  The
+// problem is re-run with one more power step; once a step improves e by less
+// than a quarter of the target's margin (e <= (1 + (target - 1) / 4) e_next)
+// the power iteration has settled, and the error left is the sketch-size term of
+// Theorem 3.1: the sketch is then doubled (r1 -> min(2 r1, n); r1 = n is the
+// classical range finder) at the same q, and if that helps by more than the
+// margin the power steps resume, else the problem is settled.  A power step
+// that makes e worse (e_next > (1 + 1e-3) e) marks the working precision's
+// limit: the problem is re-run in FP32 at the end.  The result kept is always
+// the one with the smallest estimate.  e^2 is a difference of two nearly equal
+// squared norms, each with the products' relative error (~1e-5 in the mixed and
+// FP32 paths); a problem whose estimate is below JUDGE_FLOOR |A|_F (0.014:
+// e^2 >= 2e-4 |A|_F^2, where a 5% change of e is 10x that error) is kept as
+// run, since its estimate cannot resolve the target's margin.  FP64 runs use a
+// floor of 1e-6.
+static constexpr int JUDGE_ROUNDS = 4;
+static constexpr double JUDGE_FLOOR = 0.014, JUDGE_FLOOR64 = 1e-6;
+
+enum JudgeMode { JUDGE_DONE = 0, JUDGE_Q = 1, JUDGE_R1 = 2 };
+
+// out[i] = sum of squares of item i's A (what = 0) or sigma (what = 1)
+static int batch_sumsq(const std::vector<spm_batch_item>& it, int adt, int what, double* out,
+                       cudaStream_t st) {
+  SPM_CUDA_TRY(cudaMemsetAsync(out, 0, it.size() * sizeof(double), st));
+  for (size_t i = 0; i < it.size(); ++i) {
+    if (what == 0)
+      SPM_TRY(sumsq(it[i].m, it[i].n, rowmajor(it[i].A, adt, it[i].lda), out + i, st));
+    else
+      SPM_TRY(sumsq(1, it[i].k, rowmajor(it[i].sigma, adt, it[i].k), out + i, st));
+  }
+  return SPM_OK;
+}
+
+static int copy_outputs(const spm_batch_item& from, const spm_batch_item& to, size_t es,
+                        cudaStream_t st) {
+  SPM_CUDA_TRY(cudaMemcpy2DAsync(to.U, to.ldu * es, from.U, from.ldu * es, from.k * es, from.m,
+                                 cudaMemcpyDeviceToDevice, st));
+  SPM_CUDA_TRY(cudaMemcpyAsync(to.sigma, from.sigma, from.k * es, cudaMemcpyDeviceToDevice, st));
+  SPM_CUDA_TRY(cudaMemcpy2DAsync(to.Vt, to.ldvt * es, from.Vt, from.ldvt * es, from.n * es, from.k,
+                                 cudaMemcpyDeviceToDevice, st));
+  return SPM_OK;
+}
+
+// Scratch outputs (U m x k, sigma k, Vt k x n, each 256-byte aligned, ld k and n)
+// for the given items, carved from one arena block.
+static int scratch_outputs(Arena& ar, std::vector<spm_batch_item>& nx, size_t es) {
+  auto up = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
+  int64_t total = 0;
+  for (const auto& t : nx) total += up(t.m * t.k * es) + up(t.k * es) + up(t.k * t.n * es);
+  unsigned char* base = ar.alloc<unsigned char>(total);
+  if (!base) return SPM_ENOMEM;
+  for (auto& t : nx) {
+    t.U = base;
+    base += up(t.m * t.k * es);
+    t.sigma = base;
+    base += up(t.k * es);
+    t.Vt = base;
+    base += up(t.k * t.n * es);
+    t.ldu = t.k;
+    t.ldvt = t.n;
+  }
+  return SPM_OK;
+}
+
+// The judge over a batch whose chosen run is in items (outputs written); items[i].q
+// is updated to the q of the kept result.  One host synchronisation per round.
+static int judge_batch(int count, spm_batch_item* items, int32_t dtype, double target,
+                       const spm_opts* opts, int nstreams, cudaStream_t st,
+                       std::vector<int>* used_fp32 = nullptr) {
+  const int adt = dtype == SPM_F64 ? DT_F64 : DT_F32;
+  const size_t es = dt_size(adt);
+  spm_opts o32{};
+  if (opts) o32 = *opts;
+  o32.precision = SPM_PREC_FP32;
+  std::vector<spm_batch_item> all(items, items + count);
+  std::vector<double> a2(count), e(count), tmp(count);
+  {
+    Arena ar(st);
+    double* d = ar.alloc<double>(2 * (int64_t)count);
+    if (!d) return SPM_ENOMEM;
+    SPM_TRY(batch_sumsq(all, adt, 0, d, st));
+    SPM_TRY(batch_sumsq(all, adt, 1, d + count, st));
+    SPM_CUDA_TRY(cudaMemcpyAsync(a2.data(), d, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaMemcpyAsync(tmp.data(), d + count, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (int i = 0; i < count; ++i) e[i] = sqrt(fmax(a2[i] - tmp[i], 0.0));
+  const double floor_rel = (opts && opts->precision == SPM_PREC_FP64) || !opts ? JUDGE_FLOOR64 : JUDGE_FLOOR;
+  std::vector<int> active, fp32;
+  for (int i = 0; i < count; ++i)
+    if (e[i] >= floor_rel * sqrt(a2[i])) active.push_back(i);
+  std::vector<int> mode(count, JUDGE_Q);
+  for (int round = 0; round < JUDGE_ROUNDS && !active.empty(); ++round) {
+    // the active problems once more, one power step or a doubled sketch further
+    // than their current result, into scratch outputs
+    Arena ar(st);
+    std::vector<spm_batch_item> nx;
+    for (int i : active) {
+      spm_batch_item t = items[i];
+      if (mode[i] == JUDGE_Q) {
+        t.q += 1;
+      } else {
+        t.r1 = std::min<int64_t>(2 * t.r1, t.n);
+        t.s = (int32_t)std::min<int64_t>(t.s, t.r1);
+      }
+      nx.push_back(t);
+    }
+    SPM_TRY(scratch_outputs(ar, nx, es));
+    const int na = (int)nx.size();
+    int32_t* dst = ar.alloc<int32_t>(na);
+    double* d = ar.alloc<double>(na);
+    if (!dst || !d) return SPM_ENOMEM;
+    SPM_TRY(spm_rsvd_batched(na, nx.data(), dtype, opts, nstreams, dst, st));
+    SPM_TRY(batch_sumsq(nx, adt, 1, d, st));
+    std::vector<double> s2(na);
+    std::vector<int32_t> hs(na);
+    SPM_CUDA_TRY(cudaMemcpyAsync(s2.data(), d, na * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaMemcpyAsync(hs.data(), dst, na * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> next;
+    const double settle = 1.0 + 0.25 * (target - 1.0);
+    for (int j = 0; j < na; ++j) {
+      const int i = active[j];
+      const double e0 = e[i];
+      const double e2 = hs[j] == 0 ? sqrt(fmax(a2[i] - s2[j], 0.0)) : -1.0;
+      if (e2 < 0.0) continue;  // the re-run failed: keep what there is
+      if (mode[i] == JUDGE_Q && e2 > e0 * (1.0 + 1e-3) && opts && opts->precision == SPM_PREC_MIXED &&
+          std::find(fp32.begin(), fp32.end(), i) == fp32.end())
+        fp32.push_back(i);
+      const bool helped = e0 > settle * e2;
+      if (e2 < e0) {
+        SPM_TRY(copy_outputs(nx[j], items[i], es, st));
+        e[i] = e2;
+        items[i].q = nx[j].q;
+        items[i].r1 = nx[j].r1;
+        items[i].s = nx[j].s;
+      }
+      if (mode[i] == JUDGE_Q)
+        mode[i] = helped ? JUDGE_Q : (items[i].r1 < items[i].n ? JUDGE_R1 : JUDGE_DONE);
+      else
+        mode[i] = helped ? JUDGE_Q : JUDGE_DONE;
+      if (mode[i] != JUDGE_DONE) next.push_back(i);
+    }
+    // scratch outputs are released in stream order after the copies above
+    active.swap(next);
+  }
+  if (!fp32.empty()) {
+    Arena ar(st);
+    std::vector<spm_batch_item> nx;
+    for (int i : fp32) nx.push_back(items[i]);
+    SPM_TRY(scratch_outputs(ar, nx, es));
+    const int na = (int)nx.size();
+    int32_t* dst = ar.alloc<int32_t>(na);
+    double* d = ar.alloc<double>(na);
+    if (!dst || !d) return SPM_ENOMEM;
+    SPM_TRY(spm_rsvd_batched(na, nx.data(), dtype, &o32, nstreams, dst, st));
+    SPM_TRY(batch_sumsq(nx, adt, 1, d, st));
+    std::vector<double> s2(na);
+    std::vector<int32_t> hs(na);
+    SPM_CUDA_TRY(cudaMemcpyAsync(s2.data(), d, na * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaMemcpyAsync(hs.data(), dst, na * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SPM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < na; ++j) {
+      const int i = fp32[j];
+      const double e2 = hs[j] == 0 ? sqrt(fmax(a2[i] - s2[j], 0.0)) : -1.0;
+      if (e2 >= 0.0 && e2 < e[i]) {
+        SPM_TRY(copy_outputs(nx[j], items[i], es, st));
+        if (used_fp32) used_fp32->push_back(i);
+      }
+    }
+  }
+  return SPM_OK;
+}
+
 }  // namespace spm
 
 using namespace spm;
@@ -168,7 +346,15 @@ int spm_rsvd_auto(const void* A, int32_t dtype, int64_t m, int64_t n, int64_t ld
   }
   rc = spm_rsvd(S, A, dtype, m, lda, k, q, seed + 1, k, opts, U, ldu, sigma, Vt, ldvt, info, stream);
   spm_sketch_destroy(S);
-  return rc;
+  if (rc != SPM_OK) return rc;
+  spm_batch_item it{A, m, n, lda, k, r1, (int32_t)(s < r1 ? s : r1), q, seed, U, ldu, sigma, Vt, ldvt};
+  std::vector<int> f32;
+  SPM_TRY(judge_batch(1, &it, dtype, target_ratio, opts, 1, st, &f32));
+  if (info) {
+    info->auto_q = it.q;
+    info->auto_fp32 = f32.empty() ? 0 : 1;
+  }
+  return SPM_OK;
 }
 
 int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, double target_ratio,
@@ -240,7 +426,8 @@ int spm_rsvd_batched_auto(int32_t count, spm_batch_item* items, int32_t dtype, d
       choices[2 * i + 1] = c;
     }
   }
-  return spm_rsvd_batched(count, items, dtype, opts, nstreams, dev_status, stream);
+  SPM_TRY(spm_rsvd_batched(count, items, dtype, opts, nstreams, dev_status, stream));
+  return judge_batch(count, items, dtype, target_ratio, opts, ns, st);
 }
 
 }  // extern "C"

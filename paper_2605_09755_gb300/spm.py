@@ -41,13 +41,15 @@ class Info(ctypes.Structure):
     _fields_ = [("want_timing", ctypes.c_int32), ("eig_sweeps", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("cholqr_passes", ctypes.c_int32),
                 ("resid_est", ctypes.c_double), ("fro_a", ctypes.c_double),
-                ("stage_ms", ctypes.c_float * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("auto_q", ctypes.c_int32),
+                ("auto_fp32", ctypes.c_int32)]
 
     def as_dict(self):
         return {"device_status": self.device_status, "cholqr_passes": self.cholqr_passes,
                 "eig_sweeps": self.eig_sweeps,
                 "resid_est": self.resid_est, "fro_a": self.fro_a,
-                "stage_ms": {k: float(v) for k, v in zip(STAGES, self.stage_ms)}}
+                "stage_ms": {k: float(v) for k, v in zip(STAGES, self.stage_ms)},
+                "auto_q": self.auto_q, "auto_fp32": self.auto_fp32}
 
 
 _LIB = None
@@ -601,9 +603,11 @@ class Batch:
         return self.outputs
 
     def run_auto(self, target_ratio, params):
-        """spm_rsvd_batched_auto: pick (q, r1) per problem with the selector network and
-        run the batch; the picks stay in the items, so run() replays them.  Returns the
-        (q, c) pairs (r1 = c k)."""
+        """spm_rsvd_batched_auto: pick (q, r1) per problem with the selector network, run
+        the batch and judge every result by its residual estimate (more power steps,
+        a doubled sketch, FP32 at the precision limit; see spm.h).  Returns the network's
+        (q, c) picks (r1 = c k); the (q, r1, s) of each kept result stay in the items,
+        so run() replays them."""
         count = len(self.outputs)
         ch = (ctypes.c_int32 * max(2 * count, 2))()
         f = _fn("spm_rsvd_batched_auto", [I32, ctypes.POINTER(BatchItem), I32, ctypes.c_double, VP,
@@ -613,6 +617,11 @@ class Batch:
                  ctypes.byref(self.opts), self.nstreams, self.status.data_ptr(), ch, _stream()),
                "spm_rsvd_batched_auto")
         return [(int(ch[2 * i]), int(ch[2 * i + 1])) for i in range(count)]
+
+    def item_params(self):
+        """The (q, r1, s) each item runs with (after run_auto: those of the kept result)."""
+        return [(int(self.items[i].q), int(self.items[i].r1), int(self.items[i].s))
+                for i in range(len(self.outputs))]
 
     def check_status(self):
         st = self.status.cpu()

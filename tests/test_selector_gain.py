@@ -65,3 +65,34 @@ def test_selector_beats_fixed_choice_on_held_out(env):
         met_fixed += int(y[3 * 2 + 1] <= thr)
     assert checked >= count // 2
     assert met_learned >= met_fixed + 0.25 * count, (met_learned, met_fixed)
+
+
+def test_residual_judge_never_worse_and_meets_the_target_more_often(env):
+    """spm_rsvd_auto's residual judge: the result returned is never worse than the
+    network's pick run alone (its residual within rounding of, or below, that of a
+    plain RandSVD at the pick), its q is the pick's or larger, and at a 1.05 target
+    it meets the target at least as often as the pick alone (ratios to the
+    Eckart-Young optimum, on held-out matrices)."""
+    spm, sel = env
+    params = sel.load_params()
+    rng = np.random.default_rng(321)
+    target = 1.05
+    met_pick = met_judged = 0
+    count = 16
+    for _ in range(count):
+        spec = sel.random_spec(rng)
+        A, sigma = sel.make_matrix(spec)
+        k = spec["k"]
+        opt = float(np.sqrt(np.sum(np.sort(np.asarray(sigma))[::-1][k:] ** 2)))
+        U, sg, Vt, (q, c), info = spm.rsvd_auto(A, k, target, params, seed=42)
+        assert info["device_status"] == 0 and q <= info["auto_q"] <= q + 4
+        n = A.shape[1]
+        r1 = min(c * k, n)
+        S = spm.Sketch(n, r1, min(8, r1), 42)
+        U0, s0, V0, _ = spm.rsvd(S, A, k, q, k, omega_seed=43, precision=spm.PREC_MIXED)
+        r_j = float(torch.linalg.norm((A - (U * sg) @ Vt).double())) / opt
+        r_0 = float(torch.linalg.norm((A - (U0 * s0) @ V0).double())) / opt
+        assert r_j <= r_0 * (1 + 1e-4), (r_j, r_0, q, info["auto_q"])
+        met_pick += int(r_0 <= target)
+        met_judged += int(r_j <= target)
+    assert met_judged >= met_pick, (met_judged, met_pick)

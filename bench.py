@@ -80,6 +80,9 @@ def parse():
     p.add_argument("--final-passes", type=int, default=3)
     p.add_argument("--power-passes", type=int, default=3)
     p.add_argument("--cpu-rows", type=int, default=2048)
+    p.add_argument("--autotune", action="store_true",
+                   help="rsvd: time each product's split-K candidates in the warm-up and "
+                        "keep the fastest (spm_set_autotune)")
     p.add_argument("--sketch", default="sparse", choices=["sparse", "dense", "srht"],
                    help="sketch family of Lemma 3.2 (item 2, 1 or 3) for the rsvd workload")
     p.add_argument("--trials", type=int, default=5, help="polydecay: trials (the paper: 25)")
@@ -997,7 +1000,10 @@ def main():
         del U64, s64, V64
         torch.cuda.empty_cache()
 
-    # warm-up, then the timed region (inputs are 4.3 GB >> 129 MB L2, no flush needed)
+    # warm-up, then the timed region (inputs are 4.3 GB >> 129 MB L2, no flush needed);
+    # with --autotune the first warm-up step measures the products' split-K choices
+    if a.autotune:
+        spm.set_autotune(1)
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
@@ -1130,7 +1136,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32",
             "data": "synthetic (seeded, generated on device)",
             "config": {"workload": workload_name(a), "sketch": a.sketch, "precision": "mixed",
-                       "final_passes": a.final_passes, "power_passes": a.power_passes, "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "final_passes": a.final_passes, "power_passes": a.power_passes,
+                       "autotune": bool(a.autotune), "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs (4.3 GB) larger than L2; no flush"},
             "accuracy": {"residual_mixed": res_mixed, "residual_fp64": fp64.get("residual"),
                          "ratio": (res_mixed / fp64["residual"]) if fp64 else None,

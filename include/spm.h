@@ -364,6 +364,22 @@ int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n
                     int64_t r2, int32_t q, uint64_t omega_seed, const spm_opts* opts, void* U,
                     int64_t ldu, void* lam, spm_info* info, void* stream);
 
+/* ---- split-K autotuning of the tensor-core products -----------------------------
+ * mode 1: the split-K of every tensor-core product inside the library's calls is
+ * measured on the first use of its shape class (M, N, K, passes, operand layout,
+ * symmetric output, device): each candidate (the cost model's pick and 1, 2, 4,
+ * 8, 16 splits, at most a quarter of the 64-wide K tiles) runs twice on the
+ * call's stream, timed with CUDA events, and the fastest is cached for the
+ * process; later products of the class take it without timing.  Tuning
+ * synchronises the stream and runs the product several times (the last run is
+ * the chosen configuration's, so results are those of the choice); inside a
+ * stream capture the model's pick is used.  mode 0 (default): the cost model
+ * only.  Not thread-safe against concurrent calls on other threads while the
+ * mode changes.  spm_autotune_entries returns the number of cached classes and
+ * empties the cache when clear != 0. */
+int spm_set_autotune(int32_t mode);
+int spm_autotune_entries(int32_t clear);
+
 /* ---- a8 on a Gaussian kernel matrix that is never formed ----------------------
  * K[i, j] = exp(-|x_i - x_j|^2 / (2 h^2)) over n points x_i = row i of X (n x d,
  * row-major, ld ldx >= d, DEVICE, dtype SPM_F32 or SPM_F64; 1 <= d <= 32; h > 0

@@ -17,7 +17,9 @@
 
 #include <algorithm>
 #include <functional>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -152,6 +154,70 @@ int auto_splitk(int64_t M, int64_t N, int64_t K, bool sym) {
   return 1;
 }
 
+// ------------------------------------------------------------------ split-K autotuning
+// With spm_set_autotune(1), the split-K of each tensor-core product shape class
+// (M, N, K, passes, operand majors, symmetric output, device) is measured on its
+// first use instead of taken from the cost model: every candidate (the model's
+// pick and 1, 2, 4, 8, 16 splits, at most a quarter of the K tiles) runs twice on
+// the call's stream, timed by CUDA events, the faster of each pair counts, and the
+// fastest candidate is cached for the process and run once more, so that the
+// product the caller gets is the chosen configuration's.  Tuning synchronises the
+// stream; inside a stream capture the model's pick is used.
+static int g_autotune = 0;
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int>, int> g_tune;
+
+static int tuned_gemm(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcOp* B,
+                      float* D, int64_t d_rs, int64_t d_cs, bool sym, cudaStream_t st, int* status) {
+  const int model = auto_splitk(M, N, K, sym);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (!g_autotune || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, model, st, sym, status);
+  int dev = 0;
+  SPM_CUDA_TRY(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(M, N, K, npass, (int)A[0].mn_major, (int)B[0].mn_major, (int)sym, dev);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto f = g_tune.find(key);
+    if (f != g_tune.end())
+      return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, f->second, st, sym, status);
+  }
+  const int64_t kt = cdiv(K, 64);
+  std::vector<int> cand{model};
+  for (int c : {1, 2, 4, 8, 16})
+    if ((c == 1 || c <= kt / 4) && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+  cudaEvent_t e0, e1;
+  SPM_CUDA_TRY(cudaEventCreate(&e0));
+  SPM_CUDA_TRY(cudaEventCreate(&e1));
+  int best = model;
+  float best_ms = 1e30f;
+  int rc = SPM_OK;
+  for (int c : cand) {
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && rc == SPM_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) rc = SPM_ECUDA;
+      if (rc == SPM_OK) rc = gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, c, st, sym, status);
+      if (rc == SPM_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = SPM_ECUDA;
+      if (rc == SPM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = SPM_ECUDA;
+      float t = 0.f;
+      if (rc == SPM_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = std::min(ms, t);
+    }
+    if (rc != SPM_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SPM_TRY(rc);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = best;
+  }
+  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, best, st, sym, status);
+}
+
 // Split-precision tensor-core product: D = sum of npass terms over (hi, lo) pairs.
 static int tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* Ahi,
                     const __nv_bfloat16* Alo, int64_t lda, bool a_mn, const __nv_bfloat16* Bhi,
@@ -159,8 +225,7 @@ static int tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* Ahi,
                     int64_t d_rs, int64_t d_cs, cudaStream_t st, int* status, bool sym = false) {
   TcOp A[3] = {{Ahi, lda, a_mn}, {Ahi, lda, a_mn}, {Alo, lda, a_mn}};
   TcOp B[3] = {{Bhi, ldb, b_mn}, {Blo, ldb, b_mn}, {Bhi, ldb, b_mn}};
-  return gemm_tc(M, N, K, npass, A, B, 1.0f, D, d_rs, d_cs, auto_splitk(M, N, K, sym), st, sym,
-                 status);
+  return tuned_gemm(M, N, K, npass, A, B, D, d_rs, d_cs, sym, st, status);
 }
 
 // ------------------------------------------------------------------ CholeskyQR
@@ -267,13 +332,12 @@ static int orth_big_mixed(Call& C, float* Y, int64_t m, int64_t c, int64_t ldy,
 static int tc_six(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* const* X, int64_t ldx,
                   bool x_mn, const __nv_bfloat16* const* Y, int64_t ldy, bool y_mn, float* D,
                   int64_t ldd, bool sym, float* T, cudaStream_t st, int* status) {
-  const int sk = auto_splitk(M, N, K, sym);
   TcOp a1[3] = {{X[0], ldx, x_mn}, {X[0], ldx, x_mn}, {X[1], ldx, x_mn}};
   TcOp b1[3] = {{Y[0], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
   TcOp a2[3] = {{X[0], ldx, x_mn}, {X[1], ldx, x_mn}, {X[2], ldx, x_mn}};
   TcOp b2[3] = {{Y[2], ldy, y_mn}, {Y[1], ldy, y_mn}, {Y[0], ldy, y_mn}};
-  SPM_TRY(gemm_tc(M, N, K, 3, a1, b1, 1.0f, D, ldd, 1, sk, st, sym, status));
-  SPM_TRY(gemm_tc(M, N, K, 3, a2, b2, 1.0f, T, N, 1, sk, st, sym, status));
+  SPM_TRY(tuned_gemm(M, N, K, 3, a1, b1, D, ldd, 1, sym, st, status));
+  SPM_TRY(tuned_gemm(M, N, K, 3, a2, b2, T, N, 1, sym, st, status));
   return add2d_f32(M, N, D, ldd, T, N, st);
 }
 
@@ -1371,6 +1435,19 @@ int spm_nystrom_eig(const spm_sketch* S, const void* A, int32_t dtype, int64_t n
   int rc = nystrom_core(C, S, A, n, lda, r2, q, omega_seed, o);
   if (rc == SPM_OK) rc = nystrom_eig_finish(C, S, o, n, r2, U, ldu, lam);
   return finish(C, info, rc, false);
+}
+
+int spm_set_autotune(int32_t mode) {
+  if (mode != 0 && mode != 1) return SPM_EINVAL;
+  g_autotune = mode;
+  return SPM_OK;
+}
+
+int spm_autotune_entries(int32_t clear) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const int n = (int)g_tune.size();
+  if (clear) g_tune.clear();
+  return n;
 }
 
 int spm_gauss_sketch(const spm_sketch* S, const void* X, int32_t dtype, int64_t n, int64_t d,

@@ -373,6 +373,17 @@ def nystrom_eig(S, A, r2, q, omega_seed=43, precision=PREC_FP64, timing=False, *
     return U, lam, inf.as_dict()
 
 
+def set_autotune(mode):
+    """spm_set_autotune: 1 = time the split-K candidates of each product shape on
+    first use and cache the fastest; 0 = the cost model (default)."""
+    _check(lib().spm_set_autotune(int(mode)), "spm_set_autotune")
+
+
+def autotune_entries(clear=False):
+    """Number of product shape classes tuned so far (spm_autotune_entries)."""
+    return int(lib().spm_autotune_entries(int(bool(clear))))
+
+
 def gauss_sketch(S, X, h):
     """K S for the Gaussian kernel of the rows of X (spm_gauss_sketch): K never formed."""
     _require_cuda(X)

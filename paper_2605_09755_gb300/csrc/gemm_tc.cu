@@ -34,7 +34,8 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * TC_BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int EP_BYTES = 4 * 32 * 33 * 4;  // epilogue staging: a 32 x 33 block per warp
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EP_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 struct TcParams {
@@ -47,6 +48,7 @@ struct TcParams {
   int sym_upper;  // skip output tiles that lie entirely below the diagonal
   int fused3;     // split product A0 B0 + A0 B1 + A2 B0 (A1 = A0, B2 = B0): each k-tile
                   // takes two ring stages, (A0, B0) and (A2, B1), and all three MMAs
+  int mt, nt, splits;  // output tiles along M and N, K splits: the work units
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,6 +61,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -147,8 +152,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One CTA per 128 x BN output tile (and K split); every operand tile is
-// fetched by this CTA's own TMA loads from this GPU's memory.
+// Persistent: each CTA walks the work units (output tile and K split) u =
+// blockIdx.x, blockIdx.x + gridDim.x, ...; its producer, MMA and epilogue roles
+// walk the same sequence.  The stage ring runs on across units, and the TMEM
+// accumulator is double-buffered (2 x BN columns): the epilogue drains unit t's
+// buffer while the MMA thread fills unit t + 1's.  Every operand tile is fetched
+// by this CTA's own TMA loads from this GPU's memory.  A bounded wait that
+// expires sets the status word and a CTA-wide abort flag that every role checks.
 template <int BN, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta0, const __grid_constant__ CUtensorMap ta1,
@@ -162,37 +172,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* smem =
       smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* tiles = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  unsigned char* ep = smem + STAGES * Cfg::STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ep + Cfg::EP_BYTES);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const uint32_t full0 = smem_u32(bars);
   const uint32_t empty0 = smem_u32(bars + STAGES);
-  const uint32_t done = smem_u32(bars + 2 * STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES);      // accumulator b filled: 2 barriers
+  const uint32_t tempty0 = smem_u32(bars + 2 * STAGES + 2); // accumulator b drained: 2 barriers
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM;
-  const int n0 = blockIdx.y * BN;
-  // symmetric output: a tile entirely below the diagonal leaves before it
-  // touches any barrier
-  if (p.sym_upper && (int)blockIdx.x * TC_BM >= n0 + BN) return;
-  const int kt0 = blockIdx.z * p.kt_per_split;
-  const int kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
+  const int units = p.mt * p.nt * p.splits;
   const int per_kt = p.fused3 ? 2 : p.npass;  // ring stages per k-tile
-  const int iters = (kt1 - kt0) * per_kt;
   static_assert(STAGES % 2 == 0, "a fused k-tile's two stages must not wrap");
+  // unit u: M tile fastest (consecutive CTAs share the B tile), then N tile, then split
+  auto decode = [&](int u, int& m0, int& n0, int& z, int& kt0, int& kt1) {
+    const int mi = u % p.mt, ni = (u / p.mt) % p.nt;
+    z = u / (p.mt * p.nt);
+    m0 = mi * TC_BM;
+    n0 = ni * BN;
+    kt0 = z * p.kt_per_split;
+    kt1 = min(p.k_tiles, kt0 + p.kt_per_split);
+    // symmetric output: a tile entirely below the diagonal is skipped by every role
+    return !(p.sym_upper && m0 >= n0 + BN);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
     mbar_init(done, 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // barrier inits visible to the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_holder)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -200,152 +223,179 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  auto fail = [&]() { *abort_flag = 1; };
 
   if (warp == 0) {
     if (lane == 0) {
       const CUtensorMap* ta[3] = {&ta0, &ta1, &ta2};
       const CUtensorMap* tb[3] = {&tb0, &tb1, &tb2};
-      bool ok = true;
-      int issued = 0;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) {
-          ok = false;
-          break;
-        }
-        const int kt = kt0 + it / per_kt;
-        const int q = it % per_kt;
-        // fused: the k-tile's first stage holds (A0, B0), its second (A2, B1)
-        const int qa = p.fused3 ? (q == 0 ? 0 : 2) : q;
-        const int qb = p.fused3 ? (q == 0 ? 0 : 1) : q;
-        const int k0 = kt * TC_BK;
-        const uint32_t fb = full0 + 8 * s;
-        mbar_expect_tx(fb, Cfg::STAGE_BYTES);
-        const uint32_t sa = smem_u32(tiles + s * Cfg::STAGE_BYTES);
-        const uint32_t sb = sa + Cfg::A_BYTES;
-        if (!A_MN) {
-          tma_load_2d(sa, ta[qa], k0, m0, fb);
-        } else {
+      int g = 0;  // ring iteration over all units
+      for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+        int m0, n0, z, kt0, kt1;
+        if (!decode(u, m0, n0, z, kt0, kt1)) continue;
+        const int iters = (kt1 - kt0) * per_kt;
+        for (int it = 0; it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (*abort_flag || !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) {
+            fail();
+            break;
+          }
+          const int kt = kt0 + it / per_kt;
+          const int q = it % per_kt;
+          // fused: the k-tile's first stage holds (A0, B0), its second (A2, B1)
+          const int qa = p.fused3 ? (q == 0 ? 0 : 2) : q;
+          const int qb = p.fused3 ? (q == 0 ? 0 : 1) : q;
+          const int k0 = kt * TC_BK;
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, Cfg::STAGE_BYTES);
+          const uint32_t sa = smem_u32(tiles + s * Cfg::STAGE_BYTES);
+          const uint32_t sb = sa + Cfg::A_BYTES;
+          if (!A_MN) {
+            tma_load_2d(sa, ta[qa], k0, m0, fb);
+          } else {
 #pragma unroll
-          for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[qa], m0 + 64 * b, k0, fb);
-        }
-        if (!B_MN) {
-          tma_load_2d(sb, tb[qb], k0, n0, fb);
-        } else {
+            for (int b = 0; b < TC_BM / 64; ++b) tma_load_2d(sa + b * 8192, ta[qa], m0 + 64 * b, k0, fb);
+          }
+          if (!B_MN) {
+            tma_load_2d(sb, tb[qb], k0, n0, fb);
+          } else {
 #pragma unroll
-          for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb);
+            for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * 8192, tb[qb], n0 + 64 * b, k0, fb);
+          }
         }
-        issued = it + 1;
       }
       // drain: every copy this thread issued must have landed before exit
-      for (int it = max(0, issued - STAGES); it < issued; ++it) {
-        const int s = it % STAGES;
-        mbar_wait(full0 + 8 * s, (uint32_t)(it / STAGES) & 1u, p.status);
-      }
-      (void)ok;
+      for (int it = max(0, g - STAGES); it < g; ++it)
+        mbar_wait(full0 + 8 * (it % STAGES), (uint32_t)(it / STAGES) & 1u, p.status);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<BN, A_MN, B_MN>();
-      bool ok = true;
       auto desc_a = [&](uint32_t sa, int kk) {
         return A_MN ? smem_desc(sa + kk * 2048, 8192, 1024) : smem_desc(sa + kk * 32, 16, 1024);
       };
       auto desc_b = [&](uint32_t sb, int kk) {
         return B_MN ? smem_desc(sb + kk * 2048, 8192, 1024) : smem_desc(sb + kk * 32, 16, 1024);
       };
-      // fused split product: per k-tile wait for both stages, issue A0 B0, A0 B1,
-      // A2 B0 (the order of the unfused passes), release both stages
-      for (int j = 0; p.fused3 && j < iters / 2; ++j) {
-        const int s0 = (2 * j) % STAGES, s1 = (2 * j + 1) % STAGES;
-        if (!mbar_wait(full0 + 8 * s0, (uint32_t)((2 * j) / STAGES) & 1u, p.status) ||
-            !mbar_wait(full0 + 8 * s1, (uint32_t)((2 * j + 1) / STAGES) & 1u, p.status)) {
-          ok = false;
+      int g = 0, t = 0;
+      for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+        int m0, n0, z, kt0, kt1;
+        if (!decode(u, m0, n0, z, kt0, kt1)) continue;
+        const int iters = (kt1 - kt0) * per_kt;
+        const int b = t & 1;
+        // the accumulator's previous unit (t - 2) has been drained
+        if (!mbar_wait(tempty0 + 8 * b, ((uint32_t)(t >> 1) & 1u) ^ 1u, p.status)) {
+          fail();
           break;
         }
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(tiles + s0 * Cfg::STAGE_BYTES), b_hi = a_hi + Cfg::A_BYTES;
-        const uint32_t a_lo = smem_u32(tiles + s1 * Cfg::STAGE_BYTES), b_lo = a_lo + Cfg::A_BYTES;
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        // fused split product: per k-tile wait for both stages, issue A0 B0, A0 B1,
+        // A2 B0 (the order of the unfused passes), release both stages
+        for (int j = 0; p.fused3 && j < iters / 2; ++j, g += 2) {
+          const int s0 = g % STAGES, s1 = (g + 1) % STAGES;
+          if (*abort_flag || !mbar_wait(full0 + 8 * s0, (uint32_t)(g / STAGES) & 1u, p.status) ||
+              !mbar_wait(full0 + 8 * s1, (uint32_t)((g + 1) / STAGES) & 1u, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(tiles + s0 * Cfg::STAGE_BYTES), b_hi = a_hi + Cfg::A_BYTES;
+          const uint32_t a_lo = smem_u32(tiles + s1 * Cfg::STAGE_BYTES), b_lo = a_lo + Cfg::A_BYTES;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const uint32_t sa = (t == 2) ? a_lo : a_hi;
-          const uint32_t sb = (t == 1) ? b_lo : b_hi;
+          for (int tt = 0; tt < 3; ++tt) {
+            const uint32_t sa = (tt == 2) ? a_lo : a_hi;
+            const uint32_t sb = (tt == 1) ? b_lo : b_hi;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+              tc_mma(acc, desc_a(sa, kk), desc_b(sb, kk), idesc, (j > 0 || tt > 0 || kk > 0) ? 1u : 0u);
+          }
+          tc_commit(empty0 + 8 * s0);
+          tc_commit(empty0 + 8 * s1);
+        }
+        for (int it = 0; !p.fused3 && it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          if (*abort_flag || !mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1u, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + s * Cfg::STAGE_BYTES);
+          const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk)
-            tc_mma(tmem, desc_a(sa, kk), desc_b(sb, kk), idesc, (j > 0 || t > 0 || kk > 0) ? 1u : 0u);
+            tc_mma(acc, desc_a(sa, kk), desc_b(sb, kk), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(empty0 + 8 * s);
         }
-        tc_commit(empty0 + 8 * s0);
-        tc_commit(empty0 + 8 * s1);
-      }
-      for (int it = 0; !p.fused3 && it < iters; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(full0 + 8 * s, ph, p.status)) {
-          ok = false;
+        if (!ok) {
+          fail();
           break;
         }
-        tc_fence_after();
-        const uint32_t sa = smem_u32(tiles + s * Cfg::STAGE_BYTES);
-        const uint32_t sb = sa + Cfg::A_BYTES;
-#pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          uint64_t ad, bd;
-          if (!A_MN)
-            ad = smem_desc(sa + kk * 32, 16, 1024);
-          else
-            ad = smem_desc(sa + kk * 2048, 8192, 1024);
-          if (!B_MN)
-            bd = smem_desc(sb + kk * 32, 16, 1024);
-          else
-            bd = smem_desc(sb + kk * 2048, 8192, 1024);
-          tc_mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        }
-        tc_commit(empty0 + 8 * s);
+        tc_commit(tfull0 + 8 * b);  // fires once this unit's MMAs have completed
+        ++t;
       }
       tc_commit(done);  // fires once every MMA above has completed
-      (void)ok;
     }
   } else {
     // epilogue warps 2..5: TMEM lane quarter = warp % 4
     const int quarter = warp & 3;
-    const bool ok = mbar_wait(done, 0, p.status);
-    tc_fence_after();
-    if (ok && iters > 0) {
-      const int row = m0 + quarter * 32 + lane;
-      float* D = p.D + (int64_t)blockIdx.z * p.split_stride;
-      if (p.d_cs == 1) {
-        // row-major output: each 32 x 32 block goes through shared memory (the
-        // drained stage ring) so that a warp stores one 128-byte row segment at a time
-        float(*st)[33] = reinterpret_cast<float(*)[33]>(tiles + quarter * 32 * 33 * sizeof(float));
-        const int rbase = m0 + quarter * 32;
+    float(*st)[33] = reinterpret_cast<float(*)[33]>(ep + quarter * 32 * 33 * sizeof(float));
+    int t = 0;
+    for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+      int m0, n0, z, kt0, kt1;
+      if (!decode(u, m0, n0, z, kt0, kt1)) continue;
+      const int b = t & 1;
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(tfull0 + 8 * b, (uint32_t)(t >> 1) & 1u, p.status);
+      ok = __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      tc_fence_after();
+      if (kt1 > kt0) {
+        const uint32_t acc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
+        const int row = m0 + quarter * 32 + lane;
+        float* D = p.D + (int64_t)z * p.split_stride;
+        if (p.d_cs == 1) {
+          // row-major output: each 32 x 32 block goes through shared memory so
+          // that a warp stores one 128-byte row segment at a time
+          const int rbase = m0 + quarter * 32;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(acc + (uint32_t)c0, v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) st[lane][j] = p.alpha * __uint_as_float(v[j]);
-          __syncwarp();
-          const int col = n0 + c0 + lane;
+            for (int j = 0; j < 32; ++j) st[lane][j] = p.alpha * __uint_as_float(v[j]);
+            __syncwarp();
+            const int col = n0 + c0 + lane;
 #pragma unroll 4
-          for (int r = 0; r < 32; ++r)
-            if (rbase + r < p.M && col < p.N) D[(int64_t)(rbase + r) * p.d_rs + col] = st[r][lane];
-          __syncwarp();
-        }
-      } else {
+            for (int r = 0; r < 32; ++r)
+              if (rbase + r < p.M && col < p.N) D[(int64_t)(rbase + r) * p.d_rs + col] = st[r][lane];
+            __syncwarp();
+          }
+        } else {
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-          if (row < p.M) {
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(acc + (uint32_t)c0, v);
+            if (row < p.M) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = n0 + c0 + j;
-              if (col < p.N) D[(int64_t)row * p.d_rs + (int64_t)col * p.d_cs] = p.alpha * __uint_as_float(v[j]);
+              for (int j = 0; j < 32; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < p.N) D[(int64_t)row * p.d_rs + (int64_t)col * p.d_cs] = p.alpha * __uint_as_float(v[j]);
+              }
             }
           }
         }
       }
+      // this warp's reads of the accumulator are done: hand it back to the MMA thread
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      ++t;
     }
   }
   tc_fence_before();
@@ -356,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
@@ -458,6 +508,30 @@ static int fused_split(int npass, const TcOp* A, const TcOp* B) {
   return (npass == 3 && same(A[0], A[1]) && same(B[0], B[2])) ? 1 : 0;
 }
 
+// SM count of the current device (cached per device)
+static int tc_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// persistent grid: one CTA per SM (the kernel's shared memory allows one), or
+// fewer when there are fewer work units
+static dim3 tc_grid(TcParams& p, int64_t mt, int64_t nt, int splitk) {
+  p.mt = (int)mt;
+  p.nt = (int)nt;
+  p.splits = splitk;
+  const int64_t units = mt * nt * splitk;
+  return dim3((unsigned)min64(units, tc_sms()));
+}
+
 // strictly lower triangle of D (n x n) from the upper one
 __global__ void k_mirror_upper(int n, float* __restrict__ D, int64_t d_rs, int64_t d_cs) {
   for (int i = blockIdx.y; i < n; i += gridDim.y)
@@ -493,7 +567,8 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   const int kt_per = (int)cdiv(k_tiles, splitk);
   splitk = (int)cdiv(k_tiles, kt_per);
   const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
-  if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
+  if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535 || mt * nt * splitk > 0x7FFFFFFF)
+    return SPM_EUNSUPPORTED;
   TcParams p{};
   p.M = (int)M;
   p.N = (int)N;
@@ -505,7 +580,7 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   p.status = status;
   p.sym_upper = sym_upper ? 1 : 0;
   p.fused3 = fused_split(npass, A, B);
-  dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
+  const dim3 grid = tc_grid(p, mt, nt, splitk);
   Arena ar(st);
   if (splitk == 1) {
     p.D = D;
@@ -586,7 +661,8 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   // the partial sums must fit the fixed scratch array
   if (splitk > 1 && (int64_t)splitk * M * N > kNoAllocScratchFloats) return SPM_EINVAL;
   const int64_t mt = cdiv(M, TC_BM), nt = cdiv(N, BN);
-  if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535) return SPM_EUNSUPPORTED;
+  if (mt > 0x7FFFFFFF || nt > 65535 || splitk > 65535 || mt * nt * splitk > 0x7FFFFFFF)
+    return SPM_EUNSUPPORTED;
   float* scratch = nullptr;
   int* status = nullptr;
   SPM_TRY(gemm_symbols(&scratch, &status));
@@ -619,7 +695,7 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
     p.d_cs = 1;
     p.split_stride = M * N;
   }
-  dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splitk);
+  const dim3 grid = tc_grid(p, mt, nt, splitk);
   if (BN == 256)
     SPM_TRY((launch_bn<256>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   else

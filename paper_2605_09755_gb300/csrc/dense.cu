@@ -1172,24 +1172,38 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
 template <typename T>
 __global__ void k_oa_metric(int64_t r, const T* __restrict__ S, const T* __restrict__ Gm,
                             unsigned long long* __restrict__ mx) {
-  double m1 = 0.0, m2 = 0.0;
-  const double s00 = (double)S[0];
+  // FP32 arithmetic: the score only ranks estimates
+  float f1 = 0.f, f2 = 0.f;
+  const float s00 = (float)S[0];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < r * r;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / r, j = e % r;
-    const double g = fabs((double)Gm[e] - (i == j ? 1.0 : 0.0));
-    m2 = (g > m2 || g != g) ? g : m2;
+    const float g = fabsf((float)Gm[e] - (i == j ? 1.f : 0.f));
+    f2 = (g > f2 || g != g) ? g : f2;
     if (i != j) {
-      const double q = fabs((double)S[e]) / sqrt(fabs((double)S[j * r + j] * s00));
-      m1 = (q > m1 || q != q) ? q : m1;
+      const float q = fabsf((float)S[e]) * rsqrtf(fabsf((float)S[j * r + j] * s00));
+      f1 = (q > f1 || q != q) ? q : f1;
     }
   }
+  double m1 = f1, m2 = f2;
   for (int o = 16; o > 0; o >>= 1) {
     const double a = __shfl_xor_sync(0xFFFFFFFFu, m1, o), b = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
     m1 = (a > m1 || a != a) ? a : m1;
     m2 = (b > m2 || b != b) ? b : m2;
   }
+  // one atomic per block: the warps' maxima through shared memory
+  __shared__ double w1[32], w2[32];
+  const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   if ((threadIdx.x & 31) == 0) {
+    w1[warp] = m1;
+    w2[warp] = m2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      m1 = (w1[w] > m1 || w1[w] != w1[w]) ? w1[w] : m1;
+      m2 = (w2[w] > m2 || w2[w] != w2[w]) ? w2[w] : m2;
+    }
     atomic_max_nonneg(mx, m1);
     atomic_max_nonneg(mx + 1, m2);
   }

@@ -29,25 +29,8 @@
 namespace spm {
 
 static constexpr int CT = 64;
-static constexpr int CLD = CT + 1;
+static constexpr int CLD = CT + 4;  // 16-byte aligned rows: vector shared loads
 static constexpr int CTHREADS = 512;
-
-// s = tile (r0.., c0..) of a row-major matrix, zero outside [0, R) x [0, Cc);
-// trans: s[j][i] = M[r0 + i][c0 + j].  Loads bypass L1 (the data may have been
-// written by another CTA since this SM last read it).
-template <typename T>
-__device__ __forceinline__ void ld_tile(T (*s)[CLD], const T* M, int64_t ld, int r0, int c0, int R,
-                                        int Cc, bool trans) {
-  for (int e = threadIdx.x; e < CT * CT; e += CTHREADS) {
-    const int i = e >> 6, j = e & 63;
-    const int gi = r0 + i, gj = c0 + j;
-    const T v = (gi < R && gj < Cc) ? __ldcg(M + (int64_t)gi * ld + gj) : (T)0;
-    if (trans)
-      s[j][i] = v;
-    else
-      s[i][j] = v;
-  }
-}
 
 // A tile in registers: thread t holds elements t + 512 u (u = 0..7), row-major.
 template <typename T>
@@ -77,20 +60,63 @@ __device__ __forceinline__ void st_regs(T (*s)[CLD], const TileRegs<T>& t, bool 
   }
 }
 
-// acc[v][u] += sum_k Xt[k][row_v] Y[k][col_u]; rows ty, ty + 32; columns tx + 16 u
+// s = tile (r0.., c0..) of a row-major matrix, zero outside [0, R) x [0, Cc);
+// trans: s[j][i] = M[r0 + i][c0 + j].  Loads bypass L1 (the data may have been
+// written by another CTA since this SM last read it) and are all issued
+// before the first shared store.
+template <typename T>
+__device__ __forceinline__ void ld_tile(T (*s)[CLD], const T* M, int64_t ld, int r0, int c0, int R,
+                                        int Cc, bool trans) {
+  TileRegs<T> t;
+  ld_regs(t, M, ld, r0, c0, R, Cc);
+  st_regs(s, t, trans);
+}
+
+// 2- and 4-element shared loads and stores (8- and 16-byte aligned addresses)
+static __device__ __forceinline__ void vld2(const float* p, float v[2]) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+static __device__ __forceinline__ void vld2(const double* p, double v[2]) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+static __device__ __forceinline__ void vld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+static __device__ __forceinline__ void vld4(const double* p, double v[4]) {
+  vld2(p, v);
+  vld2(p + 2, v + 2);
+}
+static __device__ __forceinline__ void vst4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+static __device__ __forceinline__ void vst4(double* p, const double v[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// acc[v][u] += sum_k Xt[k][row_v] Y[k][col_u]; rows 2 ty + v, columns 4 tx + u
+// (ty = tid / 16, tx = tid % 16): per k, one 2-element load of Xt and one
+// 4-element load of Y for eight multiply-adds.
 template <typename T>
 __device__ __forceinline__ void tile_mma(T acc[2][4], const T (*Xt)[CLD], const T (*Y)[CLD]) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll 8
   for (int k = 0; k < CT; ++k) {
-    const T x0 = Xt[k][ty], x1 = Xt[k][ty + 32];
-    T y[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) y[u] = Y[k][tx + 16 * u];
+    T x[2], y[4];
+    vld2(&Xt[k][2 * ty], x);
+    vld4(&Y[k][4 * tx], y);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      acc[0][u] = fma(x0, y[u], acc[0][u]);
-      acc[1][u] = fma(x1, y[u], acc[1][u]);
+      acc[0][u] = fma(x[0], y[u], acc[0][u]);
+      acc[1][u] = fma(x[1], y[u], acc[1][u]);
     }
   }
 }
@@ -154,16 +180,20 @@ __device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const T d = dnext;
-        const bool fin = isfinite(d);
-        const bool piv = fin && (d > thr);
-        nonfinite |= !fin;
-        const T isd = rsqrt_t(piv ? d : (T)1);
-        const T lc = piv ? ((lane == c) ? d * isd : ((lane > c) ? row[c] * isd : (T)0))
-                         : ((lane == c) ? (T)1 : (T)0);
+        // a pivot is finite and above the threshold (false for NaN); the
+        // reciprocal square root is taken unconditionally and only used when
+        // it is one, so the chain from one pivot to the next is rsqrt, a
+        // multiply, a select, a multiply-add and a broadcast
+        const bool piv = (d > thr) && (d < (T)INFINITY);
+        nonfinite |= !isfinite(d);
+        const T isd = rsqrt_t(d);
+        const T base = (lane == c) ? d : ((lane > c) ? row[c] : (T)0);
+        const T lraw = base * isd;
+        const T lc = piv ? lraw : ((lane == c) ? (T)1 : (T)0);
         my_rdg = (lane == c) ? (piv ? isd : (T)1) : my_rdg;
         df |= piv ? 0u : (1u << c);
         row[c] = lc;
-        const T nlc = piv ? -lc : (T)0;
+        const T nlc = piv ? -lraw : (T)0;
         // the next pivot, from lane c + 1's own entry (the same multiply-add
         // as its update below), broadcast before the other lanes' updates
         if (c + 1 < 16) dnext = __shfl_sync(0xFFFFFFFFu, fma(nlc, lc, row[c + 1]), c + 1);
@@ -193,27 +223,52 @@ __device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T
       const unsigned df = dfl16;
       T x[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) x[c] = a[i][o + c];
+      for (int c = 0; c < 16; c += 4) vld4(&a[i][o + c], x + c);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         T s = x[c];
 #pragma unroll
-        for (int j = 0; j < c; ++j) s -= x[j] * a[o + c][o + j];
+        for (int j = 0; j < c; ++j) s = fma(-x[j], a[o + c][o + j], s);
         x[c] = ((df >> c) & 1u) ? (T)0 : s * rdg[o + c];
       }
 #pragma unroll
-      for (int c = 0; c < 16; ++c) a[i][o + c] = x[c];
+      for (int c = 0; c < 16; c += 4) vst4(&a[i][o + c], x + c);
     }
     __syncthreads();
-    // (3) trailing update of the lower part below the block
-    for (int e = tid; e < nbelow * nbelow; e += CTHREADS) {
-      const int ii = e / nbelow, kk = e - ii * nbelow;
-      if (kk > ii) continue;
-      const int i = o + 16 + ii, k = o + 16 + kk;
-      T s = a[i][k];
+    // (3) trailing update of the lower part below the block, in 4 x 4 blocks
+    // (one per thread): a[i][k] -= sum_c a[i][o + c] a[k][o + c], c in order
+    {
+      const int n4 = nbelow / 4;
+      if (tid < n4 * (n4 + 1) / 2) {
+        int bi = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= tid) ++bi;
+        while (bi * (bi + 1) / 2 > tid) --bi;
+        const int bj = tid - bi * (bi + 1) / 2;
+        const int i0 = o + 16 + 4 * bi, k0 = o + 16 + 4 * bj;
+        T acc[4][4];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) s -= a[i][o + c] * a[k][o + c];
-      a[i][k] = s;
+        for (int ii = 0; ii < 4; ++ii) vld4(&a[i0 + ii][k0], acc[ii]);
+#pragma unroll
+        for (int c = 0; c < 16; c += 4) {
+          T xi[4][4], xk[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            vld4(&a[i0 + q][o + c], xi[q]);
+            vld4(&a[k0 + q][o + c], xk[q]);
+          }
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = fma(-xi[ii][cc], xk[kk][cc], acc[ii][kk]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (bi > bj || kk <= ii) a[i0 + ii][k0 + kk] = acc[ii][kk];
+      }
     }
     __syncthreads();
   }
@@ -224,7 +279,7 @@ __device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T
   //     the diagonal zeroed by the other warps;
   // (2) the two 32 x 32 diagonal blocks: off-diagonal 16 x 16 blocks (1, 0), (3, 2);
   // (3) the 64 x 64 tile: off-diagonal 32 x 32 block.
-  __shared__ T tmp[32][33];
+  __shared__ __align__(16) T tmp[32][34];
   if (warp < 4) {
     const int o = warp * 16, c = lane;
     if (c < 16) {
@@ -262,26 +317,34 @@ __device__ __forceinline__ void diag_factor(T (*a)[CLD], T (*inv)[CLD], int b, T
     __syncthreads();
   }
   {
-    // (3) T = L[32:64][0:32] inv[0:32][0:32] (two elements per thread), then
+    // (3) T = L[32:64][0:32] inv[0:32][0:32] (two adjacent elements per
+    //     thread, one 2-element load of inv per k), then
     //     inv[32:64][0:32] = -inv[32:64][32:64] T
-    const int i = tid >> 4, j0 = tid & 15;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = j0 + 16 * h;
-      T acc = (T)0;
+    const int i = tid >> 4, j = 2 * (tid & 15);
+    T acc0 = (T)0, acc1 = (T)0;
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fma(a[32 + i][k], inv[k][j], acc);
-      tmp[i][j] = acc;
+    for (int k = 0; k < 32; ++k) {
+      T v[2];
+      vld2(&inv[k][j], v);
+      const T x = a[32 + i][k];
+      acc0 = fma(x, v[0], acc0);
+      acc1 = fma(x, v[1], acc1);
     }
+    tmp[i][j] = acc0;
+    tmp[i][j + 1] = acc1;
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = j0 + 16 * h;
-      T acc = (T)0;
+    acc0 = (T)0;
+    acc1 = (T)0;
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fma(inv[32 + i][32 + k], tmp[k][j], acc);
-      inv[32 + i][j] = -acc;
+    for (int k = 0; k < 32; ++k) {
+      T v[2];
+      vld2(&tmp[k][j], v);
+      const T x = inv[32 + i][32 + k];
+      acc0 = fma(x, v[0], acc0);
+      acc1 = fma(x, v[1], acc1);
     }
+    inv[32 + i][j] = -acc0;
+    inv[32 + i][j + 1] = -acc1;
   }
   __syncthreads();
 }
@@ -406,22 +469,25 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       const int ib = p + 1, od = ib * CT, b = min(CT, r - od);
       ld_tile<T>(s0, G, ldg, od, o, r, r, true);
       ld_tile<T>(s1, Li, ldi, o, o, r, r, true);
+      TileRegs<T> gd;  // the diagonal tile before this panel's update (in flight during the product)
+      ld_regs(gd, (const T*)G, ldg, od, od, r, r);
       __syncthreads();
       T acc[2][4];
       acc_zero(acc);
       tile_mma<T>(acc, s0, s1);
-      TileRegs<T> gd;  // the diagonal tile before this panel's update
-      ld_regs(gd, (const T*)G, ldg, od, od, r, r);
       __syncthreads();
+      int dj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dj[u] = (o + 4 * tx + u < r) ? __ldcg(defl + o + 4 * tx + u) : 1;
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = od + ty + 32 * v, j = o + tx + 16 * u;
+          const int i = od + 2 * ty + v, j = o + 4 * tx + u;
           const bool in = i < r && j < r;
-          const T val = (in && !__ldcg(defl + j)) ? acc[v][u] : (T)0;
+          const T val = (in && !dj[u]) ? acc[v][u] : (T)0;
           if (in) G[(int64_t)i * ldg + j] = val;
-          s0[tx + 16 * u][ty + 32 * v] = val;  // transposed: s0[k][i] = L[i][k]
+          s0[4 * tx + u][2 * ty + v] = val;  // transposed: s0[k][i] = L[i][k]
         }
       post_flag(flags + ib, p + 1);
       acc_zero(acc);
@@ -431,7 +497,7 @@ __global__ void __launch_bounds__(CTHREADS, 1)
 #pragma unroll
       for (int v = 0; v < 2; ++v)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s1[ty + 32 * v][tx + 16 * u] -= acc[v][u];
+        for (int u = 0; u < 4; ++u) s1[2 * ty + v][4 * tx + u] -= acc[v][u];
       __syncthreads();
       // lower part only, identity beyond the matrix
       for (int e = tid; e < CT * CT; e += CTHREADS) {
@@ -452,13 +518,16 @@ __global__ void __launch_bounds__(CTHREADS, 1)
         __syncthreads();
         T acc[2][4];
         acc_zero(acc);
+        int dj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dj[u] = (o + 4 * tx + u < r) ? __ldcg(defl + o + 4 * tx + u) : 1;
         tile_mma<T>(acc, s0, s1);
 #pragma unroll
         for (int v = 0; v < 2; ++v)
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int i = ib * CT + ty + 32 * v, j = o + tx + 16 * u;
-            if (i < r && j < r) G[(int64_t)i * ldg + j] = __ldcg(defl + j) ? (T)0 : acc[v][u];
+            const int i = ib * CT + 2 * ty + v, j = o + 4 * tx + u;
+            if (i < r && j < r) G[(int64_t)i * ldg + j] = dj[u] ? (T)0 : acc[v][u];
           }
         post_flag(flags + ib, p + 1);
       }
@@ -486,7 +555,7 @@ __global__ void __launch_bounds__(CTHREADS, 1)
         for (int v = 0; v < 2; ++v)
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
+            const int i = ib * CT + 2 * ty + v, j = jb * CT + 4 * tx + u;
             if (i < r && j < r && j <= i) {
               T* g = G + (int64_t)i * ldg + j;
               *g = __ldcg(g) - acc[v][u];
@@ -519,7 +588,7 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       for (int v = 0; v < 2; ++v)
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          Tm[(int64_t)(ib * CT + ty + 32 * v) * ldt + jb * CT + tx + 16 * u] = acc[v][u];
+          Tm[(int64_t)(ib * CT + 2 * ty + v) * ldt + jb * CT + 4 * tx + u] = acc[v][u];
     }
     if (!grid_sync(gb, nb, status)) return;
     // inv(L)[ib][jb] = -sum_{kb = o + h}^{ib} inv(L)[ib][kb] Tm[kb][jb]
@@ -541,7 +610,7 @@ __global__ void __launch_bounds__(CTHREADS, 1)
       for (int v = 0; v < 2; ++v)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = ib * CT + ty + 32 * v, j = jb * CT + tx + 16 * u;
+          const int i = ib * CT + 2 * ty + v, j = jb * CT + 4 * tx + u;
           if (i < r && j < r) Li[(int64_t)i * ldi + j] = -acc[v][u];
         }
     }

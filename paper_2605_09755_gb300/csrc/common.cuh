@@ -146,30 +146,38 @@ struct StageScope {
   ~StageScope() { t.end(); }
 };
 
-// Bounded grid-wide barrier for cooperative kernels: thread 0 of each CTA
-// arrives on a counter and waits (at most ~2^32 clocks) for the generation to
-// change; on expiry it records DEV_TIMEOUT and the caller returns.
+// Bounded grid-wide barrier for cooperative kernels.  The arrival counter only
+// grows within a launch (it starts at 0): the k-th barrier is complete when it
+// reaches nblocks (k + 1).  Thread 0 of each CTA adds 1 with release semantics
+// (after the CTA barrier, so the CTA's writes are ordered before it) and polls
+// the counter with acquire loads until it reaches the next multiple of
+// nblocks above its own arrival; nobody resets or flips a second word, so the
+// last arrival is seen after one trip through L2.  A CTA arriving at barrier
+// k finds the counter in [nblocks k, nblocks (k + 1)), since barrier k cannot
+// complete without it.  The wait is bounded (~2^32 clocks); on expiry it
+// records DEV_TIMEOUT and the caller returns.
 struct GridBar {
   unsigned* count;
-  unsigned* gen;
+  unsigned* gen;  // spare word (zeroed with the counter)
 };
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBar gb, unsigned nblocks, int* status) {
   __syncthreads();
   __shared__ int timed_out;
   if (threadIdx.x == 0) {
     timed_out = 0;
-    volatile unsigned* vgen = gb.gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(gb.count, 1u) + 1u;
-    if (arrived == nblocks) {
-      *gb.count = 0;
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;\n" : "=r"(old) : "l"(gb.count) : "memory");
+    const unsigned target = (old / nblocks + 1u) * nblocks;
+    if ((int)(ld_acquire_gpu(gb.count) - target) < 0) {
       const long long t0 = clock64();
-      while (*vgen == g) {
+      while ((int)(ld_acquire_gpu(gb.count) - target) < 0) {
         if (clock64() - t0 > (1ll << 32)) {
           set_status(status, DEV_TIMEOUT);
           timed_out = 1;
@@ -177,7 +185,6 @@ __device__ __forceinline__ bool grid_sync(GridBar gb, unsigned nblocks, int* sta
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return timed_out == 0;

@@ -588,7 +588,32 @@ template <typename T>
 struct JT {
   static constexpr int v = 256;
 };
-static constexpr int JL4 = JS + 4;     // 16-byte aligned rows for vector shared loads
+// row stride of the per-warp product tiles: 16-byte aligned rows for vector
+// shared loads and for the asynchronous 16-byte copies of the J tiles
+template <typename T>
+constexpr int JL4 = sizeof(T) == 4 ? JS + 4 : JS + 2;
+
+// 16-byte asynchronous copy global -> shared through L2 only (.cg): the J tiles
+// are rewritten every round by other CTAs
+__device__ __forceinline__ void cp_async16_cg(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// One warp copies a JS x JS row-major rotation tile into a shared tile with
+// row stride JL4 (16-byte pieces, JS * sizeof(T) / 16 per row).
+template <typename T>
+__device__ __forceinline__ void j_tile_async(T (*dst)[JL4<T>], const T* __restrict__ src, int lane) {
+  constexpr int CH = JS * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int e = lane; e < JS * CH; e += 32) {
+    const int row = e / CH, ch = e % CH;
+    cp_async16_cg(reinterpret_cast<char*>(&dst[row][0]) + 16 * ch,
+                  reinterpret_cast<const char*>(src + row * JS) + 16 * ch);
+  }
+}
 
 __device__ __forceinline__ void ld4(const float* p, float v[4]) {
   const float4 t = *reinterpret_cast<const float4*>(p);
@@ -736,15 +761,18 @@ __device__ __forceinline__ void rr_locate(int X, int r, int np, int& i, int& h) 
 // Subproblem of pair c of round r + 1, built from G^(r) and the round-r
 // rotations (the rounds' products G^(r+1) = J^T G^(r) J restricted to the
 // pair's blocks): quadrant (X, Y) = J_iX[:, hX]^T G^(r)[pair iX, pair iY] J_iY[:, hY].
-// The three tiles and two rotations are staged in shared memory with one round
-// of loads (buf: 5 JS x JLD tiles, then 3 JS x (JB + 1) products).
+// The three tiles and two rotations are copied into shared memory with 16-byte
+// asynchronous copies (buf: 5 JS x JL4 tiles, then 3 JS x (JB + 4) products);
+// the two products run as 4 x 4 register tiles, each sum taken over l in order.
 template <typename T>
 __device__ void build_next_subproblem(const T* __restrict__ Gc, int64_t ld, const T* __restrict__ Jc,
                                       int c, int r, int NB, T (*S0)[JLD], unsigned char* buf) {
+  constexpr int BL = JL4<T>;
+  constexpr int WL = JB + 4;
   const int tid = threadIdx.x;
-  T(*Tl)[JLD] = reinterpret_cast<T(*)[JLD]>(buf);            // 3 tiles: (P,P), (P,Q), (Q,Q)
-  T(*Jl)[JLD] = Tl + 3 * JS;                                   // J_iP, J_iQ
-  T(*Wl)[JB + 1] = reinterpret_cast<T(*)[JB + 1]>(buf + 5 * sizeof(T) * JS * JLD);  // 3 x (JS x JB)
+  T(*Tl)[BL] = reinterpret_cast<T(*)[BL]>(buf);                // 3 tiles: (P,P), (P,Q), (Q,Q)
+  T(*Jl)[BL] = Tl + 3 * JS;                                     // J_iP, J_iQ
+  T(*Wl)[WL] = reinterpret_cast<T(*)[WL]>(buf + 5 * sizeof(T) * JS * BL);  // 3 x (JS x JB)
   int P2, Q2;
   rr_pair(c, r + 1, NB, P2, Q2);
   int ib[2], hb[2];
@@ -753,36 +781,88 @@ __device__ void build_next_subproblem(const T* __restrict__ Gc, int64_t ld, cons
   int Pb[2], Qb[2];
   rr_pair(ib[0], r, NB, Pb[0], Qb[0]);
   rr_pair(ib[1], r, NB, Pb[1], Qb[1]);
-  for (int e = tid; e < JS * JS; e += JT<T>::v) {
-    const int a = e / JS, bb = e % JS;
-#pragma unroll
-    for (int qd = 0; qd < 3; ++qd) {
+  // 16-byte pieces: a row of a G tile is two runs of JB elements (the pair's
+  // blocks), a row of a J tile one run of JS
+  constexpr int CR = JB * (int)sizeof(T) / 16;   // pieces per run
+  constexpr int CT = 3 * JS * 2 * CR;            // G tiles
+  constexpr int CJ = 2 * JS * 2 * CR;            // J tiles
+  for (int e = tid; e < CT + CJ; e += JT<T>::v) {
+    if (e < CT) {
+      const int qd = e / (JS * 2 * CR), a = (e / (2 * CR)) % JS, k = (e / CR) % 2, ch = e % CR;
       const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
-      Tl[qd * JS + a][bb] = Gc[(int64_t)pair_index(Pb[X], Qb[X], a) * ld + pair_index(Pb[Y], Qb[Y], bb)];
+      const T* src = Gc + (int64_t)pair_index(Pb[X], Qb[X], a) * ld + (k ? Qb[Y] : Pb[Y]) * JB;
+      cp_async16_cg(reinterpret_cast<char*>(&Tl[qd * JS + a][k * JB]) + 16 * ch,
+                    reinterpret_cast<const char*>(src) + 16 * ch);
+    } else {
+      const int f = e - CT;
+      const int t = f / (JS * 2 * CR), a = (f / (2 * CR)) % JS, ch = f % (2 * CR);
+      cp_async16_cg(reinterpret_cast<char*>(&Jl[t * JS + a][0]) + 16 * ch,
+                    reinterpret_cast<const char*>(Jc + (size_t)ib[t] * JS * JS + (size_t)a * JS) + 16 * ch);
     }
-    Jl[a][bb] = Jc[(size_t)ib[0] * JS * JS + e];
-    Jl[JS + a][bb] = Jc[(size_t)ib[1] * JS * JS + e];
   }
+  cp_async_commit_group();
+  cp_async_wait_all();
   __syncthreads();
-  // W_qd = T_qd J_iY[:, hY]   (32 x 16 each)
-  for (int e = tid; e < 3 * JS * JB; e += JT<T>::v) {
-    const int qd = e / (JS * JB), a = (e / JB) % JS, bb = e % JB;
+  // W_qd = T_qd J_iY[:, hY]   (32 x 16 each): thread -> (qd, 4 rows, 4 columns)
+  if (tid < 3 * (JS / 4) * (JB / 4)) {
+    const int qd = tid / ((JS / 4) * (JB / 4)), a0 = ((tid / (JB / 4)) % (JS / 4)) * 4,
+              b0 = (tid % (JB / 4)) * 4;
     const int Y = (qd == 0) ? 0 : 1;
-    T acc = (T)0;
-#pragma unroll 8
-    for (int l = 0; l < JS; ++l) acc = fma(Tl[qd * JS + a][l], Jl[Y * JS + l][hb[Y] * JB + bb], acc);
-    Wl[qd * JS + a][bb] = acc;
+    const T(*Tq)[BL] = Tl + qd * JS;
+    const T(*Jy)[BL] = Jl + Y * JS;
+    const int jc = hb[Y] * JB + b0;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+#pragma unroll 2
+    for (int l = 0; l < JS; l += 4) {
+      T tv[4][4], jv[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ld4(&Tq[a0 + i][l], tv[i]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ld4(&Jy[l + k][jc], jv[k]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(tv[i][k], jv[k][j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) st4(&Wl[qd * JS + a0 + i][b0], acc[i]);
   }
   __syncthreads();
   // S0 quadrant = J_iX[:, hX]^T W_qd   (16 x 16 each); (Q, P) is the transpose of (P, Q)
-  for (int e = tid; e < 3 * JB * JB; e += JT<T>::v) {
-    const int qd = e / (JB * JB), a2 = (e / JB) % JB, bb = e % JB;
+  if (tid < 3 * (JB / 4) * (JB / 4)) {
+    const int qd = tid / ((JB / 4) * (JB / 4)), a0 = ((tid / (JB / 4)) % (JB / 4)) * 4,
+              b0 = (tid % (JB / 4)) * 4;
     const int X = (qd == 2) ? 1 : 0, Y = (qd == 0) ? 0 : 1;
-    T acc = (T)0;
-#pragma unroll 8
-    for (int l = 0; l < JS; ++l) acc = fma(Jl[X * JS + l][hb[X] * JB + a2], Wl[qd * JS + l][bb], acc);
-    S0[X * JB + a2][Y * JB + bb] = acc;
-    if (qd == 1) S0[JB + bb][a2] = acc;
+    const T(*Jx)[BL] = Jl + X * JS;
+    const int jc = hb[X] * JB + a0;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+#pragma unroll 4
+    for (int l = 0; l < JS; ++l) {
+      T jv[4], wv[4];
+      ld4(&Jx[l][jc], jv);
+      ld4(&Wl[qd * JS + l][b0], wv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(jv[i], wv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        S0[X * JB + a0 + i][Y * JB + b0 + j] = acc[i][j];
+        if (qd == 1) S0[JB + b0 + j][a0 + i] = acc[i][j];
+      }
   }
   __syncthreads();
 }
@@ -877,18 +957,54 @@ __global__ void __launch_bounds__(JT<T>::v)
       }
       if ((int)blockIdx.x >= p2_first) {
       // ---------------- phase 2: G <- J^T G J (tile pairs), V <- V J
-      // One warp per item; lane c keeps column c of the tile (and of J_j) in
-      // registers, and each product reads its other operand row by row as
-      // broadcast 16-byte shared loads: four multiply-adds per load.
+      // One warp per item.  Its operands sit in shared memory and each lane
+      // computes a 4 x 8 block of the 32 x 32 product (rows 4 (lane % 8),
+      // columns 8 (lane / 8)) from one 16-byte load of the left operand's
+      // column and two of the right operand's row per step: 32 multiply-adds
+      // for 3 shared loads.  The J tiles (and a G item's tile) are copied in
+      // asynchronously; a V item's tile goes through registers, where it is
+      // transposed for the left operand.  Every sum runs over l in order.
       {
+        constexpr int W = JT<T>::v / 32;
+        constexpr int BL = JL4<T>;
+        static_assert(W % 4 == 0, "warps come in sub-partition groups of four");
         const int lane = tid & 31, warp = tid >> 5;
-        T(*Ja)[JL4] = reinterpret_cast<T(*)[JL4]>(jsm + (size_t)warp * 2 * sizeof(T) * JS * JL4);
-        T(*Tt)[JL4] = Ja + JS;
+        const int a0 = 4 * (lane & 7), c0 = 8 * (lane >> 3);
+        T(*R0)[BL] = reinterpret_cast<T(*)[BL]>(jsm + (size_t)warp * 3 * sizeof(T) * JS * BL);
+        T(*R1)[BL] = R0 + JS;
+        T(*R2)[BL] = R0 + 2 * JS;
         const int gitems = hp * (hp + 1) / 2;  // tile pairs i <= j; G_ji is the transpose
         const int vitems = (npad / JS) * hp;
-        const int nwarps = nworkers * (JT<T>::v / 32);
-        for (int w = worker * (JT<T>::v / 32) + warp; w < gitems + vitems; w += nwarps) {
-          T x[JS], acc[JS];
+        const int nwarps = nworkers * W;
+        // acc[i][j] += sum_l A[l][a0 + i] B[l][c0 + j] for l = 0 .. JS - 1
+        auto product = [&](const T(*A)[BL], const T(*B)[BL], T(&acc)[4][8]) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = (T)0;
+#pragma unroll 4
+          for (int l = 0; l < JS; ++l) {
+            T av[4], bv[8];
+            ld4(&A[l][a0], av);
+            ld4(&B[l][c0], bv);
+            ld4(&B[l][c0 + 4], bv + 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          }
+        };
+        // Warps w and w + 4 of a CTA share a sub-partition's issue slots.  Slots
+        // are numbered so that the first warps of all sub-partitions come
+        // before the second ones, and items (G pairs, two products each, then
+        // V blocks, one product) are dealt over the slots forwards, then
+        // backwards: a sub-partition gets at most one more product than the
+        // mean.
+        const int slot = (warp / 4) * (nworkers * 4) + worker * 4 + (warp % 4);
+        for (int pass = 0; pass * nwarps < gitems + vitems; ++pass) {
+          const int w = pass * nwarps + ((pass & 1) ? nwarps - 1 - slot : slot);
+          if (w >= gitems + vitems) continue;
+          T acc[4][8];
           if (w < gitems) {
             // w -> (i, j), i <= j, row-wise over the upper triangle of pair indices
             int i = (int)(((2.0f * hp + 1.0f) - sqrtf((2.0f * hp + 1.0f) * (2.0f * hp + 1.0f) - 8.0f * w)) * 0.5f);
@@ -899,50 +1015,48 @@ __global__ void __launch_bounds__(JT<T>::v)
             int Pi, Qi, Pj, Qj;
             rr_pair(i, r, NB, Pi, Qi);
             rr_pair(j, r, NB, Pj, Qj);
-            const T* Ji = Jc + (size_t)i * JS * JS;
-            const T* Jj = Jc + (size_t)j * JS * JS;
-            const int64_t colj = pair_index(Pj, Qj, lane);
+            // R0 = X (rows of pair i, columns of pair j), R1 = J_i, R2 = J_j
+            {
+              constexpr int CR = JB * (int)sizeof(T) / 16;  // 16-byte pieces per block run
 #pragma unroll
-            for (int a = 0; a < JS; ++a) {
-              x[a] = Gc[(int64_t)pair_index(Pi, Qi, a) * ld + colj];  // X[a][c]
-              Ja[a][lane] = Ji[a * JS + lane];
+              for (int e = lane; e < JS * 2 * CR; e += 32) {
+                const int a = e / (2 * CR), k = (e / CR) % 2, ch = e % CR;
+                const T* src = Gc + (int64_t)pair_index(Pi, Qi, a) * ld + (k ? Qj : Pj) * JB;
+                cp_async16_cg(reinterpret_cast<char*>(&R0[a][k * JB]) + 16 * ch,
+                              reinterpret_cast<const char*>(src) + 16 * ch);
+              }
             }
+            j_tile_async<T>(R1, Jc + (size_t)i * JS * JS, lane);
+            j_tile_async<T>(R2, Jc + (size_t)j * JS * JS, lane);
+            cp_async_commit_group();
+            cp_async_wait_all();
             __syncwarp();
             // T = Ji^T X:  T[a][c] = sum_l Ji[l][a] X[l][c]
-#pragma unroll
-            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
-#pragma unroll
-            for (int l = 0; l < JS; ++l)
-#pragma unroll
-              for (int a = 0; a < JS; a += 4) {
-                T v[4];
-                ld4(&Ja[l][a], v);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[a + u] = fma(v[u], x[l], acc[a + u]);
-              }
-#pragma unroll
-            for (int a = 0; a < JS; a += 4) st4(&Tt[lane][a], &acc[a]);  // Tt[c][a] = T[a][c]
-#pragma unroll
-            for (int l = 0; l < JS; ++l) x[l] = Jj[l * JS + lane];      // column c of Jj
+            product(R1, R0, acc);
             __syncwarp();
-            // X' = T Jj:  X'[a][c] = sum_l T[a][l] Jj[l][c] = sum_l Tt[l][a] Jj[l][c]
 #pragma unroll
-            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
+            for (int jj = 0; jj < 8; ++jj) {  // R1[c][a] = T[a][c]
+              const T v[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
+              st4(&R1[c0 + jj][a0], v);
+            }
+            __syncwarp();
+            // X' = T Jj:  X'[a][c] = sum_l T[a][l] Jj[l][c] = sum_l R1[l][a] Jj[l][c]
+            product(R1, R2, acc);
+            // G_ij = X' (rows of pair i, columns of pair j); G_ji = X'^T
+            const int64_t cj = pair_index(Pj, Qj, c0);
 #pragma unroll
-            for (int l = 0; l < JS; ++l)
-#pragma unroll
-              for (int a = 0; a < JS; a += 4) {
-                T v[4];
-                ld4(&Tt[l][a], v);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[a + u] = fma(v[u], x[l], acc[a + u]);
-              }
-#pragma unroll
-            for (int a = 0; a < JS; ++a) Gn[(int64_t)pair_index(Pi, Qi, a) * ld + colj] = acc[a];
+            for (int ii = 0; ii < 4; ++ii) {
+              T* dst = Gn + (int64_t)pair_index(Pi, Qi, a0 + ii) * ld + cj;
+              st4(dst, acc[ii]);
+              st4(dst + 4, acc[ii] + 4);
+            }
             if (i != j) {
-              const int64_t rowj = pair_index(Pj, Qj, lane);
+              const int64_t ci = pair_index(Pi, Qi, a0);
 #pragma unroll
-              for (int a = 0; a < JS; ++a) Gn[rowj * ld + pair_index(Pi, Qi, a)] = acc[a];
+              for (int jj = 0; jj < 8; ++jj) {
+                const T v[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
+                st4(Gn + (int64_t)pair_index(Pj, Qj, c0 + jj) * ld + ci, v);
+              }
             }
             __syncwarp();
           } else {
@@ -950,29 +1064,28 @@ __global__ void __launch_bounds__(JT<T>::v)
             const int rb = v / hp, j = v % hp;
             int Pj, Qj;
             rr_pair(j, r, NB, Pj, Qj);
-            const T* Jj = Jc + (size_t)j * JS * JS;
-            const int64_t colj = pair_index(Pj, Qj, lane);
+            j_tile_async<T>(R2, Jc + (size_t)j * JS * JS, lane);
+            cp_async_commit_group();
+            {
+              // lane l loads column l of the V tile and writes it as row l of R1
+              T x[JS];
+              const int64_t coll = pair_index(Pj, Qj, lane);
 #pragma unroll
-            for (int a = 0; a < JS; ++a) x[a] = V[(int64_t)(rb * JS + a) * ld + colj];  // X[a][c]
+              for (int a = 0; a < JS; ++a) x[a] = V[(int64_t)(rb * JS + a) * ld + coll];
 #pragma unroll
-            for (int a = 0; a < JS; a += 4) st4(&Tt[lane][a], &x[a]);  // Tt[c][a] = X[a][c]
-#pragma unroll
-            for (int l = 0; l < JS; ++l) x[l] = Jj[l * JS + lane];
+              for (int a = 0; a < JS; a += 4) st4(&R1[lane][a], &x[a]);
+            }
+            cp_async_wait_all();
             __syncwarp();
-            // X' = X Jj:  X'[a][c] = sum_l Tt[l][a] Jj[l][c]
+            // X' = X Jj:  X'[a][c] = sum_l X[a][l] Jj[l][c] = sum_l R1[l][a] Jj[l][c]
+            product(R1, R2, acc);
+            const int64_t cj = pair_index(Pj, Qj, c0);
 #pragma unroll
-            for (int a = 0; a < JS; ++a) acc[a] = (T)0;
-#pragma unroll
-            for (int l = 0; l < JS; ++l)
-#pragma unroll
-              for (int a = 0; a < JS; a += 4) {
-                T vv[4];
-                ld4(&Tt[l][a], vv);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[a + u] = fma(vv[u], x[l], acc[a + u]);
-              }
-#pragma unroll
-            for (int a = 0; a < JS; ++a) V[(int64_t)(rb * JS + a) * ld + colj] = acc[a];
+            for (int ii = 0; ii < 4; ++ii) {
+              T* dst = V + (int64_t)(rb * JS + a0 + ii) * ld + cj;
+              st4(dst, acc[ii]);
+              st4(dst + 4, acc[ii] + 4);
+            }
             __syncwarp();
           }
         }
@@ -1075,9 +1188,11 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
   SPM_CUDA_TRY(cudaGetDevice(&dev));
   SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   constexpr int JTHREADS = JT<T>::v;
-  // subproblems: 7 JS x JLD tiles and 3 JS x (JB + 1) ones; products: per warp 2 JS x JL4 tiles
-  const int smem = (int)std::max(7 * sizeof(T) * JS * JLD + 3 * sizeof(T) * JS * (JB + 1),
-                                 (JTHREADS / 32) * 2 * sizeof(T) * JS * JL4);
+  // subproblems: 2 JS x JLD tiles, 5 JS x JL4 ones and 3 JS x (JB + 4) ones;
+  // products: per warp 3 JS x JL4 tiles
+  const int smem = (int)std::max(2 * sizeof(T) * JS * JLD + 5 * sizeof(T) * JS * JL4<T> +
+                                     3 * sizeof(T) * JS * (JB + 4),
+                                 (JTHREADS / 32) * 3 * sizeof(T) * JS * JL4<T>);
   auto kern = k_block_jacobi<T>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JTHREADS, smem));

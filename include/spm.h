@@ -122,6 +122,9 @@ typedef struct spm_info {
                                judge (the network's pick or more); -1 for other calls     */
   int32_t auto_fp32;        /* spm_rsvd_auto: 1 when the result returned came from the FP32
                                re-run of the judge, else 0                                 */
+  int32_t a_split;          /* mixed RandSVD: 1 when the sketch pass also wrote the (hi, lo)
+                               BF16 split of A that the projection B = Q^T A used (A read
+                               from memory once), 0 when the split was a separate pass     */
 } spm_info;
 
 /* ---- library ----------------------------------------------------------- */

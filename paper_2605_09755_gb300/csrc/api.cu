@@ -57,6 +57,12 @@ struct Call {
   int64_t at_pre_ld = 0;
   std::function<int(const struct RF&, void*, int64_t)> make_b;
   bool no_fro = false;
+  // the mixed finish's BF16 split of A (ld pad8(n)): requested by the caller
+  // (want_asplit), written by the sketch pass where its kernel can (asplit)
+  bool want_asplit = false;
+  __nv_bfloat16* a_hi = nullptr;
+  __nv_bfloat16* a_lo = nullptr;
+  bool asplit = false;
   explicit Call(cudaStream_t s) : st(s), ar(s) { timer.stream = s; }
 };
 
@@ -560,6 +566,13 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
     SPM_TRY(split_bf16(r1, r2, rowmajor(Om32, DT_F32, r2), mrowmajor(Zhi, DT_BF16, r2p),
                        mrowmajor(Zlo, DT_BF16, r2p), C.st));
   }
+  // A's split for the projection, written by the sketch pass when its kernel can
+  const int64_t np_ = pad8(n);
+  if (C.want_asplit && !C.at_pre && C.adt == DT_F32) {
+    C.a_hi = C.ar.alloc<__nv_bfloat16>(m * np_);
+    C.a_lo = C.ar.alloc<__nv_bfloat16>(m * np_);
+    if (!C.a_hi || !C.a_lo) return SPM_ENOMEM;
+  }
   {
     StageScope sc(C.timer, SPM_STAGE_APPLY);
     if (C.at_pre) {
@@ -571,16 +584,22 @@ static int range_finder_core(Call& C, const spm_sketch* S, const void* A, int64_
     } else if (C.feed_n > 0) {
       // host-fed A: each row chunk's sketch product as soon as the chunk is here
       const size_t es = dt_size(C.adt);
+      bool all = C.a_hi != nullptr;
       for (int c = 0; c < C.feed_n; ++c) {
         const int64_t r0 = (int64_t)c * C.feed_rows, rows = min64(C.feed_rows, m - r0);
         SPM_CUDA_TRY(cudaStreamWaitEvent(C.st, C.feed_ev[c], 0));
+        bool done = false;
         SPM_TRY(sketch_apply_dev(S, (const unsigned char*)A + (size_t)r0 * lda * es, C.adt, rows,
                                  lda, At + r0 * r1p, DT_BF16, r1p, C.want_fro ? C.acc : nullptr,
-                                 C.st, Atlo ? Atlo + r0 * r1p : nullptr, C.status));
+                                 C.st, Atlo ? Atlo + r0 * r1p : nullptr, C.status,
+                                 C.a_hi ? C.a_hi + r0 * np_ : nullptr,
+                                 C.a_lo ? C.a_lo + r0 * np_ : nullptr, np_, &done));
+        all = all && done;
       }
+      C.asplit = all;
     } else {
       SPM_TRY(sketch_apply_dev(S, A, C.adt, m, lda, At, DT_BF16, r1p, C.want_fro ? C.acc : nullptr,
-                               C.st, Atlo, C.status));
+                               C.st, Atlo, C.status, C.a_hi, C.a_lo, np_, &C.asplit));
     }
   }
   const __nv_bfloat16* Alo = Atlo ? Atlo : At;
@@ -691,6 +710,7 @@ static int finish(Call& C, spm_info* info, int rc, bool has_b) {
   info->cholqr_passes = C.cholqr_passes;
   info->auto_q = -1;
   info->auto_fp32 = 0;
+  info->a_split = C.asplit ? 1 : 0;
   const bool fro = !C.no_fro && C.want_fro;
   info->fro_a = fro ? sqrt(acc[0]) : -1.0;
   info->resid_est = (has_b && fro) ? sqrt(fmax(acc[0] - acc[1], 0.0)) : -1.0;
@@ -773,9 +793,12 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
   const int sdt = C.small64 ? DT_F64 : DT_F32;
   const size_t es = dt_size(sdt);
   __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
-  if (!C.make_b) {
-    Ahi = C.ar.alloc<__nv_bfloat16>(m * np_);
-    Alo = C.ar.alloc<__nv_bfloat16>(m * np_);
+  if (!C.make_b && C.asplit) {
+    Ahi = C.a_hi;  // written by the sketch pass
+    Alo = C.a_lo;
+  } else if (!C.make_b) {
+    Ahi = C.a_hi ? C.a_hi : C.ar.alloc<__nv_bfloat16>(m * np_);
+    Alo = C.a_lo ? C.a_lo : C.ar.alloc<__nv_bfloat16>(m * np_);
     if (!Ahi || !Alo) return SPM_ENOMEM;
   }
   SPM_ALLOC(C.ar, float, B, r2 * n);
@@ -802,8 +825,9 @@ static int rsvd_finish(Call& C, const void* A, int64_t m, int64_t n, int64_t lda
     if (C.make_b) {
       SPM_TRY(C.make_b(rf, B, n));
     } else {
-      SPM_TRY(split_bf16(m, n, rowmajor(A, edt, lda), mrowmajor(Ahi, DT_BF16, np_),
-                         mrowmajor(Alo, DT_BF16, np_), C.st));
+      if (!C.asplit)
+        SPM_TRY(split_bf16(m, n, rowmajor(A, edt, lda), mrowmajor(Ahi, DT_BF16, np_),
+                           mrowmajor(Alo, DT_BF16, np_), C.st));
       // B = Q^T A: A-op Q^T (M = r2, K = m) MN-major; B-op A (N = n, K = m) MN-major
       SPM_TRY(tc_split(r2, n, m, rf.Qhi, rf.Qlo, r2p, true, Ahi, Alo, np_, true, C.final_passes,
                        B, n, 1, C.st, C.status));
@@ -859,6 +883,7 @@ int rsvd_async(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int
   setup_call(C, dtype, opts, nullptr);
   SPM_TRY(prepare(C));
   RF rf;
+  C.want_asplit = C.prec == SPM_PREC_MIXED;
   SPM_TRY(range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf));
   SPM_TRY(rsvd_finish(C, A, m, S->n, lda, rf, k, U, ldu, sigma, Vt, ldvt));
   if (dev_status)
@@ -993,6 +1018,7 @@ int spm_rsvd(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, int64
   setup_call(C, dtype, opts, info);
   SPM_TRY(prepare(C));
   RF rf;
+  C.want_asplit = C.prec == SPM_PREC_MIXED;
   int rc = range_finder_core(C, S, A, m, lda, r2, q, omega_seed, rf);
   if (rc == SPM_OK) rc = rsvd_finish(C, A, m, S->n, lda, rf, k, U, ldu, sigma, Vt, ldvt);
   return finish(C, info, rc, true);
@@ -1040,6 +1066,7 @@ int spm_rsvd_host(const spm_sketch* S, const void* A, int32_t dtype, int64_t m, 
     C.feed_rows = rows;
     C.feed_ev = ev.data();
     RF rf;
+    C.want_asplit = C.prec == SPM_PREC_MIXED;
     rc = range_finder_core(C, S, Ad, m, n, r2, q, omega_seed, rf);
     if (rc == SPM_OK) rc = rsvd_finish(C, Ad, m, n, n, rf, k, Ud, k, sd, Vd, n);
   }

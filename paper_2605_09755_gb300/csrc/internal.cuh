@@ -31,19 +31,25 @@ inline View cview(MView v) { return View{v.p, v.dt, v.rs, v.cs}; }
 // into *fro2 (device double) when fro2 != nullptr.
 // out_lo (BF16 outputs only): second half of a hi/lo split, out_lo = bf16(v - hi).
 // status (device int, may be null): device-side errors (an expired bounded wait).
+// a_hi, a_lo (BF16, row stride lds, may be null): where the kernel can, the
+// (hi, lo) BF16 split of A is written in the same pass; *a_split (may be null)
+// tells whether it was.
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
                      void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
-                     void* out_lo = nullptr, int* status = nullptr);
+                     void* out_lo = nullptr, int* status = nullptr, void* a_hi = nullptr,
+                     void* a_lo = nullptr, int64_t lds = 0, bool* a_split = nullptr);
 
 // ---------------------------------------------------------------- sketch_sched.cu
 // A S for FP32 A (n and lda multiples of 4, A 16-byte aligned, rows that fit
 // whole in shared memory) by the scheduled kernel, into FP32 or BF16 (hi, and
-// lo when out_lo is set) outputs; fro2 (may be null) accumulates |A|_F^2.
-// Plans the sketch on first use (not during stream capture).  Returns
-// SPM_EUNSUPPORTED, with nothing launched, when the request or the sketch does
-// not fit the kernel.
+// lo when out_lo is set) outputs; fro2 (may be null) accumulates |A|_F^2; with
+// a_hi, a_lo (BF16, row stride lds: a multiple of 4, >= n; 8-byte aligned) A's
+// (hi, lo) split is written in the same pass.  Plans the sketch on first use
+// (not during stream capture).  Returns SPM_EUNSUPPORTED, with nothing
+// launched, when the request or the sketch does not fit the kernel.
 int sched_apply(spm_sketch* S, const float* A, int64_t m, int64_t lda, void* out, int out_dt,
-                int64_t ldo, double* fro2, int* status, cudaStream_t st, void* out_lo);
+                int64_t ldo, double* fro2, int* status, cudaStream_t st, void* out_lo,
+                void* a_hi = nullptr, void* a_lo = nullptr, int64_t lds = 0);
 void sched_init(spm_sketch* S);
 void sched_free(spm_sketch* S);
 // out (r1 x p) = S^T X, X (n x p, row stride ldx)

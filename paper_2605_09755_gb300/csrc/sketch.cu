@@ -713,14 +713,19 @@ static int launch_apply(const spm_sketch* S, const TA* A, int64_t m, int64_t lda
 
 int sketch_apply_dev(const spm_sketch* S, const void* A, int a_dt, int64_t m, int64_t lda,
                      void* out, int out_dt, int64_t ldo, double* fro2, cudaStream_t st,
-                     void* out_lo, int* status) {
+                     void* out_lo, int* status, void* a_hi, void* a_lo, int64_t lds,
+                     bool* a_split) {
+  if (a_split) *a_split = false;
   if (m <= 0) return SPM_OK;
   if (dense_kind(S)) return dense_sketch_apply(S, A, a_dt, m, lda, out, out_dt, ldo, fro2, st, out_lo);
   if (a_dt == DT_F32 && (out_dt == DT_F32 || out_dt == DT_BF16)) {
     // whole rows in shared memory, conflict-free gather schedule (the plan is
     // the sketch's own, built on first use)
-    const int rc = sched_apply(const_cast<spm_sketch*>(S), (const float*)A, m, lda, out, out_dt,
-                               ldo, fro2, status, st, out_dt == DT_BF16 ? out_lo : nullptr);
+    const bool sp = a_hi != nullptr && out_dt == DT_BF16;
+    int rc = sched_apply(const_cast<spm_sketch*>(S), (const float*)A, m, lda, out, out_dt, ldo,
+                         fro2, status, st, out_dt == DT_BF16 ? out_lo : nullptr,
+                         sp ? a_hi : nullptr, sp ? a_lo : nullptr, lds);
+    if (rc == SPM_OK && a_split) *a_split = sp;
     if (rc != SPM_EUNSUPPORTED) return rc;
   }
   if (a_dt == DT_F32) {

@@ -20,6 +20,12 @@
 // the squares of what they read: every element of A is read exactly s times
 // over all groups, so the sum over all CTAs, divided by s, is |A|_F^2.
 //
+// With a split output (ahi set) each row is also written out as its (hi, lo)
+// BF16 split, hi = bf16(a), lo = bf16(a - hi), while it sits in shared memory:
+// group g's CTA splits the g-th of G equal column ranges of the row (four
+// elements per thread and pass), so A is read from HBM once for the sketch
+// product and the tensor-core projection Q^T A that follows.
+//
 // Every wait on a ring slot is bounded; on expiry the CTA records
 // SPM_ETIMEOUT, waits (bounded) for the copies it still has in flight and
 // returns.
@@ -150,13 +156,16 @@ struct SchedArgs {
   const int* partner;
   double* fro2;
   int* status;
+  __nv_bfloat16* ahi;  // split of A (null: none), row stride lds
+  __nv_bfloat16* alo;
+  int64_t lds;
   int64_t lda, ldo;
   int m, n, G, P, cw, r1;
   float scale;
   double inv_s;
 };
 
-template <typename TO, bool FRO, int NSLOT>
+template <typename TO, bool FRO, int NSLOT, bool SPLIT>
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
     k_sketch_sched(const __grid_constant__ SchedArgs<TO> args, const uint32_t* __restrict__ words) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -222,6 +231,23 @@ __global__ void __launch_bounds__(SCHED_THREADS, 1)
     float* sg = stage + (it & 1) * SCHED_THREADS;
     if (sl >= 0) sg[sl & 0xFFFF] = (sl >> 16) ? -a0 : a0;
     if (FRO) fro_part[tid] += (double)f0;
+    if (SPLIT && !to) {
+      // this group's column range of the row, two elements per thread and pass
+      const int q2 = ((n >> 1) + args.G - 1) / args.G;
+      const int e2 = min((g + 1) * q2, n >> 1);
+      const uint32_t rb = rowa + SCHED_PAD * 4;
+#pragma unroll 1
+      for (int c2 = g * q2 + tid; c2 < e2; c2 += SCHED_THREADS) {
+        float vx, vy;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(vx), "=f"(vy) : "r"(rb + 8u * (uint32_t)c2));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(vx, vy);
+        const float2 f = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(vx - f.x, vy - f.y);
+        const int64_t o = (int64_t)row * args.lds + 2 * c2;
+        *reinterpret_cast<__nv_bfloat162*>(args.ahi + o) = h;
+        *reinterpret_cast<__nv_bfloat162*>(args.alo + o) = l;
+      }
+    }
     // one barrier per row: the slot has been read by every warp, the staging
     // row is complete, and a timeout anywhere stops the whole CTA
     if (__syncthreads_or(to ? 1 : 0)) {
@@ -415,9 +441,10 @@ static int sm_count_dev() {
   return v;
 }
 
-template <typename TO, bool FRO, int NSLOT>
+template <typename TO, bool FRO, int NSLOT, bool SPLIT>
 static int sched_launch(const spm_sketch* S, const float* A, int64_t m, int64_t lda, TO* out,
-                        TO* out_lo, int64_t ldo, double* fro2, int* status, cudaStream_t st) {
+                        TO* out_lo, int64_t ldo, double* fro2, int* status, cudaStream_t st,
+                        __nv_bfloat16* ahi, __nv_bfloat16* alo, int64_t lds) {
   const int G = S->sched_groups;
   const int P = (int)max64(1, min64(m, sm_count_dev() / G));
   const size_t smem = sched_smem(S->n, NSLOT);
@@ -430,6 +457,9 @@ static int sched_launch(const spm_sketch* S, const float* A, int64_t m, int64_t 
   a.partner = S->sched_partner;
   a.fro2 = fro2;
   a.status = status;
+  a.ahi = ahi;
+  a.alo = alo;
+  a.lds = lds;
   a.lda = lda;
   a.ldo = ldo;
   a.m = (int)m;
@@ -440,7 +470,7 @@ static int sched_launch(const spm_sketch* S, const float* A, int64_t m, int64_t 
   a.r1 = (int)S->r1;
   a.scale = (float)(1.0 / sqrt((double)S->s));
   a.inv_s = 1.0 / (double)S->s;
-  auto kern = k_sketch_sched<TO, FRO, NSLOT>;
+  auto kern = k_sketch_sched<TO, FRO, NSLOT, SPLIT>;
   SPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<(unsigned)(G * P), SCHED_THREADS, smem, st>>>(a, S->sched_words);
   SPM_LAUNCH_CHECK();
@@ -448,17 +478,29 @@ static int sched_launch(const spm_sketch* S, const float* A, int64_t m, int64_t 
 }
 
 int sched_apply(spm_sketch* S, const float* A, int64_t m, int64_t lda, void* out, int out_dt,
-                int64_t ldo, double* fro2, int* status, cudaStream_t st, void* out_lo) {
+                int64_t ldo, double* fro2, int* status, cudaStream_t st, void* out_lo, void* a_hi,
+                void* a_lo, int64_t lds) {
   if (S->kind != SPM_SKETCH_SPARSE_SIGN || m < 1 || m > 0x7FFFFFFF) return SPM_EUNSUPPORTED;
+  if (a_hi && (!a_lo || lds < S->n || (lds & 3) != 0 || ((uintptr_t)a_hi & 7u) != 0 ||
+               ((uintptr_t)a_lo & 7u) != 0))
+    return SPM_EINVAL;
   if ((S->n & 3) != 0 || (lda & 3) != 0 || ((uintptr_t)A & 15u) != 0) return SPM_EUNSUPPORTED;
   if (out_dt != DT_F32 && out_dt != DT_BF16) return SPM_EUNSUPPORTED;
   const int nslot = sched_nslot(S->n);
   if (nslot == 0 || !sched_ready(S, st, m * S->n)) return SPM_EUNSUPPORTED;
-#define SPM_SCHED_GO(TO, NS)                                                                       \
-  (fro2 ? sched_launch<TO, true, NS>(S, A, m, lda, (TO*)out, (TO*)out_lo, ldo, fro2, status, st) \
-        : sched_launch<TO, false, NS>(S, A, m, lda, (TO*)out, (TO*)out_lo, ldo, fro2, status, st))
-  if (out_dt == DT_BF16) return nslot == 3 ? SPM_SCHED_GO(__nv_bfloat16, 3) : SPM_SCHED_GO(__nv_bfloat16, 2);
-  return nslot == 3 ? SPM_SCHED_GO(float, 3) : SPM_SCHED_GO(float, 2);
+  // the split of A is a separate instantiation (BF16 outputs only: the mixed
+  // path), so the kernel without it keeps its registers for the offsets
+#define SPM_SCHED_GO(TO, NS, SP)                                                                    \
+  (fro2 ? sched_launch<TO, true, NS, SP>(S, A, m, lda, (TO*)out, (TO*)out_lo, ldo, fro2, status, st, \
+                                         (__nv_bfloat16*)a_hi, (__nv_bfloat16*)a_lo, lds)               \
+        : sched_launch<TO, false, NS, SP>(S, A, m, lda, (TO*)out, (TO*)out_lo, ldo, fro2, status, st, \
+                                          (__nv_bfloat16*)a_hi, (__nv_bfloat16*)a_lo, lds))
+  if (out_dt == DT_BF16 && a_hi)
+    return nslot == 3 ? SPM_SCHED_GO(__nv_bfloat16, 3, true) : SPM_SCHED_GO(__nv_bfloat16, 2, true);
+  if (a_hi) return SPM_EUNSUPPORTED;
+  if (out_dt == DT_BF16)
+    return nslot == 3 ? SPM_SCHED_GO(__nv_bfloat16, 3, false) : SPM_SCHED_GO(__nv_bfloat16, 2, false);
+  return nslot == 3 ? SPM_SCHED_GO(float, 3, false) : SPM_SCHED_GO(float, 2, false);
 #undef SPM_SCHED_GO
 }
 

@@ -42,14 +42,14 @@ class Info(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("cholqr_passes", ctypes.c_int32),
                 ("resid_est", ctypes.c_double), ("fro_a", ctypes.c_double),
                 ("stage_ms", ctypes.c_float * 8), ("auto_q", ctypes.c_int32),
-                ("auto_fp32", ctypes.c_int32)]
+                ("auto_fp32", ctypes.c_int32), ("a_split", ctypes.c_int32)]
 
     def as_dict(self):
         return {"device_status": self.device_status, "cholqr_passes": self.cholqr_passes,
                 "eig_sweeps": self.eig_sweeps,
                 "resid_est": self.resid_est, "fro_a": self.fro_a,
                 "stage_ms": {k: float(v) for k, v in zip(STAGES, self.stage_ms)},
-                "auto_q": self.auto_q, "auto_fp32": self.auto_fp32}
+                "auto_q": self.auto_q, "auto_fp32": self.auto_fp32, "a_split": self.a_split}
 
 
 _LIB = None

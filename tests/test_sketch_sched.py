@@ -186,3 +186,29 @@ def test_plan_modes(spmlib):
     assert spmlib.sketch_plan(S)[0] == 1
     with pytest.raises(spmlib.SpmError):
         spmlib.sketch_set_plan(S, 0)         # the plan, once built, stays
+
+
+@pytest.mark.gpu
+def test_mixed_rsvd_projection_from_the_split_written_by_the_sketch_pass(spmlib):
+    # In mixed precision the scheduled pass also writes A's (hi, lo) BF16 split,
+    # which the projection B = Q^T A then uses instead of splitting A again.  The
+    # same problem with the plan switched off (general sketch kernel, separate
+    # split) must give the same approximation: sigma within 1e-4 sigma_1 and the
+    # residual within 0.5% (the two sketch kernels sum in different orders).
+    m, n, r1, s, k = 1500, 4096, 600, 8, 40
+    rng = np.random.default_rng(12)
+    Uo, _ = np.linalg.qr(rng.standard_normal((m, k + 20)))
+    Vo, _ = np.linalg.qr(rng.standard_normal((n, k + 20)))
+    A = (Uo * (0.9 ** np.arange(k + 20))) @ Vo.T + 1e-4 * rng.standard_normal((m, n))
+    Ad = _dev(A.astype(np.float32)).float()
+    res = []
+    for plan in (1, 0):
+        S = spmlib.Sketch(n, r1, s, 42)
+        spmlib.sketch_set_plan(S, plan)
+        U, sg, Vt, _ = spmlib.rsvd(S, Ad, k, 1, k, precision=spmlib.PREC_MIXED)
+        assert spmlib.sketch_plan(S)[0] == (1 if plan else -1)
+        U, sg, Vt = U.double().cpu().numpy(), sg.double().cpu().numpy(), Vt.double().cpu().numpy()
+        res.append((sg, np.linalg.norm(A - (U * sg) @ Vt)))
+    (s1, e1), (s2, e2) = res
+    assert np.max(np.abs(s1 - s2)) <= 1e-4 * s2[0]
+    assert abs(e1 / e2 - 1.0) <= 5e-3

@@ -45,19 +45,15 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_
 template <typename TX, typename TY>
 __global__ void k_convert(int64_t rows, int64_t cols, const TX* __restrict__ x, int64_t xrs,
                           int64_t xcs, TY* __restrict__ y, int64_t yrs, int64_t ycs) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    // iterate so that the faster-moving index follows the destination's unit stride
-    int64_t i, j;
-    if (ycs == 1) {
-      i = e / cols;
-      j = e % cols;
-    } else {
-      j = e / rows;
-      i = e % rows;
-    }
-    y[i * yrs + j * ycs] = cvt<TY, TX>(x[i * xrs + j * xcs]);
+  // lines along blockIdx.y, the destination's unit-stride index along the
+  // threads (no division per element)
+  const bool rw = ycs == 1;
+  const int64_t nl = rw ? rows : cols, len = rw ? cols : rows;
+  for (int64_t l = blockIdx.y; l < nl; l += gridDim.y)
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = rw ? l : t, j = rw ? t : l;
+      y[i * yrs + j * ycs] = cvt<TY, TX>(x[i * xrs + j * xcs]);
   }
 }
 
@@ -117,7 +113,8 @@ __global__ void k_split_rows4(int64_t rows, int64_t cols4, const float* __restri
 
 int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return SPM_OK;
-  const int g = grid_for(rows * cols);
+  const int64_t nl = y.cs == 1 ? rows : cols, len = y.cs == 1 ? cols : rows;
+  const dim3 g((unsigned)min64(cdiv(len, 256), 64), (unsigned)min64(nl, 65535));
 #define SPM_CV(TX, TY)                                                                          \
   k_convert<TX, TY><<<g, 256, 0, st>>>(rows, cols, (const TX*)x.p, x.rs, x.cs, (TY*)y.p, y.rs, \
                                        y.cs)
@@ -1122,19 +1119,29 @@ __global__ void k_eye_pad(int n, int npad, const T* __restrict__ A, int64_t lda,
 // orthogonal and D diagonal, and the same products turn G into D W^T G0 W D.
 // So each eigenvector is normalised and its eigenvalue divided by the squared
 // norm (the Rayleigh quotient of the unit vector): lamc[i] = G_ii / |v_i|^2,
-// inv[i] = 1 / |v_i|.  One thread per column, rows in order (coalesced).
+// inv[i] = 1 / |v_i|.  A block takes 32 columns (one per lane, rows read
+// coalesced), its 8 warps every 8th row; the 8 partial sums are added in FP64.
 template <typename T>
 __global__ void k_eig_colnorm(int n, int64_t ldg, const T* __restrict__ G, const T* __restrict__ V,
                               T* __restrict__ lamc, T* __restrict__ inv) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int row = 0; row < n; ++row) {
-    const double v = (double)V[(int64_t)row * ldg + i];
-    s += v * v;
+  if (i < n)
+    for (int row = w; row < n; row += 8) {
+      const double v = (double)V[(int64_t)row * ldg + i];
+      s += v * v;
+    }
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += part[k][lane];
+    lamc[i] = (T)((double)G[(int64_t)i * ldg + i] / t);
+    inv[i] = (T)(1.0 / sqrt(t));
   }
-  lamc[i] = (T)((double)G[(int64_t)i * ldg + i] / s);
-  inv[i] = (T)(1.0 / sqrt(s));
 }
 
 // Sort the first n (corrected) eigenvalues descending and gather the normalised
@@ -1220,7 +1227,7 @@ static int sym_eig_t(int64_t r, T* A, int64_t lda, T* V, int64_t ldv, T* lam, in
                   (void*)&gb, (void*)&offacc, (void*)&status, (void*)&sweeps};
   SPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(JTHREADS), args, smem, st));
   count_launch();
-  k_eig_colnorm<T><<<(unsigned)cdiv(n, 128), 128, 0, st>>>(n, npad, G, Vw, lamc, lamc + n);
+  k_eig_colnorm<T><<<(unsigned)cdiv(n, 32), 256, 0, st>>>(n, npad, G, Vw, lamc, lamc + n);
   SPM_LAUNCH_CHECK();
   k_eig_sort<T><<<(unsigned)min(n, 1024), 128, 0, st>>>(n, npad, lamc, lamc + n, Vw, V, ldv, lam);
   SPM_LAUNCH_CHECK();
@@ -1400,10 +1407,16 @@ __global__ void k_scale_lines(int64_t rows, int64_t cols, T* __restrict__ X, int
   // blockIdx.y walks the lines (rows or columns), threads the other index; the
   // factor is formed once per line and applied in T
   const int64_t nl = by_rows ? rows : cols, len = by_rows ? cols : rows;
+  __shared__ T fs;
   for (int64_t l = blockIdx.y; l < nl; l += gridDim.y) {
-    double f = s[l];
-    if (inv) f = (f != 0.0) ? 1.0 / f : 0.0;
-    const T ft = (T)f;
+    __syncthreads();  // the previous line's factor has been read
+    if (threadIdx.x == 0) {
+      double f = s[l];
+      if (inv) f = (f != 0.0) ? 1.0 / f : 0.0;
+      fs = (T)f;
+    }
+    __syncthreads();
+    const T ft = fs;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len;
          t += (int64_t)gridDim.x * blockDim.x) {
       T* p = by_rows ? X + l * rs + t * cs : X + t * rs + l * cs;
@@ -1425,14 +1438,21 @@ int scale_lines(int64_t rows, int64_t cols, MView X, bool rows_not_cols, const d
 
 // Descending order of x[0..r): pos(i) = #{j : x_j > x_i, or x_j = x_i and j < i}
 // (NaN ranks last, as -inf), so every position is taken exactly once;
-// perm[pos(i)] = i, xs[pos(i)] = x_i.  x is staged through shared memory.
-__device__ __forceinline__ double order_key(double v) { return v == v ? v : -INFINITY; }
+// perm[pos(i)] = i, xs[pos(i)] = x_i.  The comparisons run on 64-bit integer
+// keys that order like the values (-0 taken as +0; the bits of a negative
+// value with its 63 low bits inverted), staged through shared memory.
+__device__ __forceinline__ long long order_key(double v) {
+  if (!(v == v)) v = -INFINITY;
+  if (v == 0.0) v = 0.0;
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
 
 __global__ void k_desc_order(int r, const double* __restrict__ x, int* __restrict__ perm,
                              double* __restrict__ xs) {
-  __shared__ double tile[1024];
+  __shared__ long long tile[1024];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double ki = i < r ? order_key(x[i]) : 0.0;
+  const long long ki = i < r ? order_key(x[i]) : 0ll;
   int pos = 0;
   for (int j0 = 0; j0 < r; j0 += 1024) {
     const int nt = min(1024, r - j0);
@@ -1441,7 +1461,7 @@ __global__ void k_desc_order(int r, const double* __restrict__ x, int* __restric
     __syncthreads();
     if (i < r)
       for (int t = 0; t < nt; ++t) {
-        const double kj = tile[t];
+        const long long kj = tile[t];
         pos += (kj > ki) || (kj == ki && j0 + t < i);
       }
   }
@@ -1615,11 +1635,13 @@ __global__ void k_sign_combine(int nblk, int64_t k, const T* __restrict__ U, int
 template <typename T>
 __global__ void k_apply_flags(int64_t rows, int64_t cols, T* __restrict__ X, int64_t rs, int64_t cs,
                               bool by_col, const int* __restrict__ flip) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cols, j = e % cols;
-    if (flip[by_col ? j : i]) X[i * rs + j * cs] = -X[i * rs + j * cs];
+  // rows along blockIdx.y, columns along the threads (no division per element);
+  // a row that keeps its sign (by rows) is skipped whole
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+    if (!by_col && !flip[i]) continue;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols;
+         j += (int64_t)gridDim.x * blockDim.x)
+      if (!by_col || flip[j]) X[i * rs + j * cs] = -X[i * rs + j * cs];
   }
 }
 
@@ -1638,6 +1660,10 @@ static void sign_flags_rows(int64_t m, int64_t k, const T* U, int64_t rs, int* f
   done = true;
 }
 
+static dim3 flag_grid(int64_t rows, int64_t cols) {
+  return dim3((unsigned)min64(cdiv(cols, 256), 64), (unsigned)min64(rows, 65535));
+}
+
 int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st) {
   Arena ar(st);
   SPM_ALLOC(ar, int, flip, k);
@@ -1649,12 +1675,16 @@ int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st
     sign_flags_rows<double>(m, k, (const double*)U.p, U.rs, flip, ar, st, rows_done);
   if (U.dt == DT_F32) {
     if (!rows_done) k_sign_flags<float><<<g, 256, 0, st>>>(m, k, (const float*)U.p, U.rs, U.cs, flip);
-    k_apply_flags<float><<<grid_for(m * k), 256, 0, st>>>(m, k, (float*)U.p, U.rs, U.cs, true, flip);
-    k_apply_flags<float><<<grid_for(k * n), 256, 0, st>>>(k, n, (float*)Vt.p, Vt.rs, Vt.cs, false, flip);
+    if (m > 0 && k > 0)
+      k_apply_flags<float><<<flag_grid(m, k), 256, 0, st>>>(m, k, (float*)U.p, U.rs, U.cs, true, flip);
+    if (n > 0 && k > 0)
+      k_apply_flags<float><<<flag_grid(k, n), 256, 0, st>>>(k, n, (float*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else if (U.dt == DT_F64) {
     if (!rows_done) k_sign_flags<double><<<g, 256, 0, st>>>(m, k, (const double*)U.p, U.rs, U.cs, flip);
-    k_apply_flags<double><<<grid_for(m * k), 256, 0, st>>>(m, k, (double*)U.p, U.rs, U.cs, true, flip);
-    k_apply_flags<double><<<grid_for(k * n), 256, 0, st>>>(k, n, (double*)Vt.p, Vt.rs, Vt.cs, false, flip);
+    if (m > 0 && k > 0)
+      k_apply_flags<double><<<flag_grid(m, k), 256, 0, st>>>(m, k, (double*)U.p, U.rs, U.cs, true, flip);
+    if (n > 0 && k > 0)
+      k_apply_flags<double><<<flag_grid(k, n), 256, 0, st>>>(k, n, (double*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else {
     return SPM_EINVAL;
   }

@@ -233,23 +233,35 @@ __global__ void k_bucket_fill(int r1, int nchunks, const int64_t* __restrict__ c
 }
 
 // ------------------------------------------------------------------ a2: Omega
+// Box-Muller on Philox: elements 2p and 2p + 1 are rad cos(ang) and rad sin(ang)
+// of the pair drawn with counter p.  One thread per pair (the logarithm, the
+// square root and the angle's reduction shared), one 64-bit division per pair.
 template <typename T>
 __global__ void k_gaussian(int64_t rows, int64_t cols, int64_t ld, uint32_t k0, uint32_t k1,
                            T* __restrict__ out) {
   const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t p = (uint64_t)e >> 1;
-    const u32x4 w = philox4x32_10((uint32_t)p, (uint32_t)(p >> 32), 0u, 2u, k0, k1);
+  const int64_t npairs = (total + 1) >> 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npairs;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const u32x4 w = philox4x32_10((uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0u, 2u, k0, k1);
     const uint64_t x1 = ((uint64_t)w.y << 21) | (uint64_t)(w.x >> 11);
     const uint64_t x2 = ((uint64_t)w.w << 21) | (uint64_t)(w.z >> 11);
     const double u1 = (double)(x1 + 1ull) * 0x1.0p-53;
     const double u2 = (double)x2 * 0x1.0p-53;
     const double rad = sqrt(-2.0 * log(u1));
     const double ang = 6.283185307179586 * u2;
-    const double z = (e & 1) ? rad * sin(ang) : rad * cos(ang);
-    const int64_t i = e / cols, j = e % cols;
-    out[i * ld + j] = (T)z;
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    const int64_t e0 = 2 * p;
+    int64_t i = e0 / cols, j = e0 - i * cols;
+    out[i * ld + j] = (T)(rad * cs);
+    if (e0 + 1 < total) {
+      if (++j == cols) {
+        j = 0;
+        ++i;
+      }
+      out[i * ld + j] = (T)(rad * sn);
+    }
   }
 }
 
@@ -638,7 +650,7 @@ int gaussian_dev(void* out, int dt, int64_t rows, int64_t cols, int64_t ld, uint
   if (rows <= 0 || cols <= 0) return SPM_OK;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const int64_t total = rows * cols;
-  const int blocks = (int)min64(cdiv(total, 256), 152 * 16);
+  const int blocks = (int)min64(cdiv((total + 1) / 2, 256), 152 * 16);
   if (dt == DT_F64)
     k_gaussian<double><<<blocks, 256, 0, st>>>(rows, cols, ld, k0, k1, (double*)out);
   else if (dt == DT_F32)

@@ -45,15 +45,19 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, __nv_bfloat16>(__nv_
 template <typename TX, typename TY>
 __global__ void k_convert(int64_t rows, int64_t cols, const TX* __restrict__ x, int64_t xrs,
                           int64_t xcs, TY* __restrict__ y, int64_t yrs, int64_t ycs) {
-  // lines along blockIdx.y, the destination's unit-stride index along the
-  // threads (no division per element)
-  const bool rw = ycs == 1;
-  const int64_t nl = rw ? rows : cols, len = rw ? cols : rows;
-  for (int64_t l = blockIdx.y; l < nl; l += gridDim.y)
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t i = rw ? l : t, j = rw ? t : l;
-      y[i * yrs + j * ycs] = cvt<TY, TX>(x[i * xrs + j * xcs]);
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    // iterate so that the faster-moving index follows the destination's unit stride
+    int64_t i, j;
+    if (ycs == 1) {
+      i = e / cols;
+      j = e % cols;
+    } else {
+      j = e / rows;
+      i = e % rows;
+    }
+    y[i * yrs + j * ycs] = cvt<TY, TX>(x[i * xrs + j * xcs]);
   }
 }
 
@@ -113,8 +117,7 @@ __global__ void k_split_rows4(int64_t rows, int64_t cols4, const float* __restri
 
 int convert2d(int64_t rows, int64_t cols, View x, MView y, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return SPM_OK;
-  const int64_t nl = y.cs == 1 ? rows : cols, len = y.cs == 1 ? cols : rows;
-  const dim3 g((unsigned)min64(cdiv(len, 256), 64), (unsigned)min64(nl, 65535));
+  const int g = grid_for(rows * cols);
 #define SPM_CV(TX, TY)                                                                          \
   k_convert<TX, TY><<<g, 256, 0, st>>>(rows, cols, (const TX*)x.p, x.rs, x.cs, (TY*)y.p, y.rs, \
                                        y.cs)
@@ -1635,13 +1638,11 @@ __global__ void k_sign_combine(int nblk, int64_t k, const T* __restrict__ U, int
 template <typename T>
 __global__ void k_apply_flags(int64_t rows, int64_t cols, T* __restrict__ X, int64_t rs, int64_t cs,
                               bool by_col, const int* __restrict__ flip) {
-  // rows along blockIdx.y, columns along the threads (no division per element);
-  // a row that keeps its sign (by rows) is skipped whole
-  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
-    if (!by_col && !flip[i]) continue;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols;
-         j += (int64_t)gridDim.x * blockDim.x)
-      if (!by_col || flip[j]) X[i * rs + j * cs] = -X[i * rs + j * cs];
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    if (flip[by_col ? j : i]) X[i * rs + j * cs] = -X[i * rs + j * cs];
   }
 }
 
@@ -1660,10 +1661,6 @@ static void sign_flags_rows(int64_t m, int64_t k, const T* U, int64_t rs, int* f
   done = true;
 }
 
-static dim3 flag_grid(int64_t rows, int64_t cols) {
-  return dim3((unsigned)min64(cdiv(cols, 256), 64), (unsigned)min64(rows, 65535));
-}
-
 int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st) {
   Arena ar(st);
   SPM_ALLOC(ar, int, flip, k);
@@ -1675,16 +1672,12 @@ int sign_fix(int64_t m, int64_t k, int64_t n, MView U, MView Vt, cudaStream_t st
     sign_flags_rows<double>(m, k, (const double*)U.p, U.rs, flip, ar, st, rows_done);
   if (U.dt == DT_F32) {
     if (!rows_done) k_sign_flags<float><<<g, 256, 0, st>>>(m, k, (const float*)U.p, U.rs, U.cs, flip);
-    if (m > 0 && k > 0)
-      k_apply_flags<float><<<flag_grid(m, k), 256, 0, st>>>(m, k, (float*)U.p, U.rs, U.cs, true, flip);
-    if (n > 0 && k > 0)
-      k_apply_flags<float><<<flag_grid(k, n), 256, 0, st>>>(k, n, (float*)Vt.p, Vt.rs, Vt.cs, false, flip);
+    k_apply_flags<float><<<grid_for(m * k), 256, 0, st>>>(m, k, (float*)U.p, U.rs, U.cs, true, flip);
+    k_apply_flags<float><<<grid_for(k * n), 256, 0, st>>>(k, n, (float*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else if (U.dt == DT_F64) {
     if (!rows_done) k_sign_flags<double><<<g, 256, 0, st>>>(m, k, (const double*)U.p, U.rs, U.cs, flip);
-    if (m > 0 && k > 0)
-      k_apply_flags<double><<<flag_grid(m, k), 256, 0, st>>>(m, k, (double*)U.p, U.rs, U.cs, true, flip);
-    if (n > 0 && k > 0)
-      k_apply_flags<double><<<flag_grid(k, n), 256, 0, st>>>(k, n, (double*)Vt.p, Vt.rs, Vt.cs, false, flip);
+    k_apply_flags<double><<<grid_for(m * k), 256, 0, st>>>(m, k, (double*)U.p, U.rs, U.cs, true, flip);
+    k_apply_flags<double><<<grid_for(k * n), 256, 0, st>>>(k, n, (double*)Vt.p, Vt.rs, Vt.cs, false, flip);
   } else {
     return SPM_EINVAL;
   }

@@ -414,20 +414,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Deterministic split-K reduction: D[i, j] = sum_{z < splits} W[z][i][j] in order.
 __global__ void k_splitk_reduce(int M, int N, int splits, const float* __restrict__ W,
                                 float* __restrict__ D, int64_t d_rs, int64_t d_cs) {
-  // rows along blockIdx.y, columns along the threads (no division per element)
   const int64_t total = (int64_t)M * N;
-  for (int i = blockIdx.y; i < M; i += gridDim.y)
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-      const int64_t e = (int64_t)i * N + j;
-      float s = 0.f;
-      for (int z = 0; z < splits; ++z) s += W[(int64_t)z * total + e];
-      D[(int64_t)i * d_rs + (int64_t)j * d_cs] = s;
-    }
-}
-
-static dim3 reduce_grid(int64_t M, int64_t N) {
-  const int64_t gx = min64(cdiv(N, 256), 64);
-  return dim3((unsigned)gx, (unsigned)min64(M, max64(1, (152 * 8) / gx)));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += W[(int64_t)z * total + e];
+    const int64_t i = e / N, j = e % N;
+    D[i * d_rs + j * d_cs] = s;
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -605,7 +599,9 @@ int gemm_tc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, const TcO
   else
     SPM_TRY((launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
-    k_splitk_reduce<<<reduce_grid(M, N), 256, 0, st>>>((int)M, (int)N, splitk, p.D, D, d_rs, d_cs);
+    const int64_t total = M * N;
+    const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
+    k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, splitk, p.D, D, d_rs, d_cs);
     SPM_LAUNCH_CHECK();
   }
   if (sym_upper) {
@@ -705,7 +701,9 @@ int gemm_tc_noalloc(int64_t M, int64_t N, int64_t K, int npass, const TcOp* A, c
   else
     SPM_TRY((launch_bn<128>(A[0].mn_major, B[0].mn_major, ta, tb, p, grid, st)));
   if (splitk > 1) {
-    k_splitk_reduce<<<reduce_grid(M, N), 256, 0, st>>>((int)M, (int)N, splitk, scratch, D, ldd, 1);
+    const int64_t total = M * N;
+    const int blocks = (int)min64(cdiv(total, 256), 152 * 8);
+    k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, splitk, scratch, D, ldd, 1);
     SPM_LAUNCH_CHECK();
   }
   return SPM_OK;

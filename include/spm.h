@@ -419,7 +419,9 @@ int spm_nystrom_gauss(const spm_sketch* S, const void* X, int32_t dtype, int64_t
  * multiple of 8, base 16-byte aligned): a_mn = 0 -> stored M x K (K contiguous);
  * a_mn = 1 -> stored K x M.  Same for B with N.  splitk >= 1 splits K; partial
  * sums are reduced in a fixed order (deterministic).
- * Errors: SPM_EINVAL on bad sizes/alignment, SPM_ECUDA without an sm_103 device.
+ * Errors: SPM_EINVAL on bad sizes/alignment or when an operand or D is not
+ * device memory of the current device (the tensor maps cover only this GPU's
+ * memory), SPM_ECUDA without an sm_103 device.
  * The call does not synchronise; a bounded device wait that expires is recorded
  * in a per-device status word that spm_gemm_bf16_status reads. */
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,

@@ -972,6 +972,19 @@ int spm_trim_memory(void) {
 
 uint64_t spm_launch_count(void) { return (uint64_t)g_launches.load(); }
 
+// The tensor maps of a product cover device memory of the current device only:
+// p must be a device (or managed) allocation of that device.
+static bool on_current_device(const void* p) {
+  int dev = 0;
+  cudaPointerAttributes at{};
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
                   int64_t lda, int32_t a_mn, const void* const* B, int64_t ldb, int32_t b_mn,
                   float* D, int64_t ldd, int32_t splitk, void* stream) {
@@ -979,8 +992,9 @@ int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* co
     return SPM_EINVAL;
   if (!tc_available()) return SPM_ECUDA;
   TcOp a[3], b[3];
+  if (!on_current_device(D)) return SPM_EINVAL;
   for (int q = 0; q < npass; ++q) {
-    if (!A[q] || !B[q]) return SPM_EINVAL;
+    if (!A[q] || !B[q] || !on_current_device(A[q]) || !on_current_device(B[q])) return SPM_EINVAL;
     a[q] = TcOp{(const __nv_bfloat16*)A[q], lda, a_mn != 0};
     b[q] = TcOp{(const __nv_bfloat16*)B[q], ldb, b_mn != 0};
   }

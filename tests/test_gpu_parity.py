@@ -120,6 +120,21 @@ def test_gemm_bf16_layouts(spm, a_mn, b_mn, M, N, K):
     assert (D2.double() - ref).abs().max().item() <= 1e-4 * (K ** 0.5) * 4
 
 
+def test_gemm_bf16_rejects_operands_off_the_current_device(spm):
+    # the tensor maps cover only this GPU's memory: a host operand (pinned or
+    # pageable) or a host D is refused before anything is launched
+    M = N = K = 64
+    dev = torch.zeros(K, M, dtype=torch.bfloat16, device="cuda")
+    for host in (torch.zeros(K, M, dtype=torch.bfloat16).pin_memory(),
+                 torch.zeros(K, M, dtype=torch.bfloat16)):
+        with pytest.raises(spm.SpmError):
+            spm.gemm_bf16([host], [dev], M, N, K, a_mn=True, b_mn=True)
+        with pytest.raises(spm.SpmError):
+            spm.gemm_bf16([dev], [host], M, N, K, a_mn=True, b_mn=True)
+    D = spm.gemm_bf16([dev], [dev], M, N, K, a_mn=True, b_mn=True)
+    assert torch.count_nonzero(D).item() == 0
+
+
 def test_gemm_bf16_split_precision(spm):
     g = torch.Generator(device="cuda").manual_seed(5)
     X = torch.randn(700, 304, device="cuda", generator=g, dtype=torch.float64)

@@ -973,7 +973,7 @@ int spm_trim_memory(void) {
 uint64_t spm_launch_count(void) { return (uint64_t)g_launches.load(); }
 
 // The tensor maps of a product cover device memory of the current device only:
-// p must be a device (or managed) allocation of that device.
+// p must be a device allocation of that device, or managed memory.
 static bool on_current_device(const void* p) {
   int dev = 0;
   cudaPointerAttributes at{};
@@ -982,7 +982,8 @@ static bool on_current_device(const void* p) {
     cudaGetLastError();  // clear the error of an unknown pointer
     return false;
   }
-  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+  if (at.type == cudaMemoryTypeManaged) return true;  // migrates to the device that reads it
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 int spm_gemm_bf16(int64_t M, int64_t N, int64_t K, int32_t npass, const void* const* A,
